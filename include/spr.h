@@ -1,0 +1,259 @@
+/*
+ * spr.h -- C ABI of the GB300 speculative progressive isosurface raycaster.
+ *
+ * The method is the one of Usher, Dyken and Kumar, "Speculative Progressive
+ * Raycasting for Memory Constrained Isosurface Visualization of Massive
+ * Volumes" (arXiv 2309.10212): a wavefront of rays is advanced through a
+ * block-compressed volume one pass at a time; each pass (Fig. 2, Sec. 3, 4)
+ *   (a) advances every live ray through the two-level macrocell grid to its
+ *       next k blocks whose value range holds the isovalue (Sec. 3.3, 4.1),
+ *   (b) marks those blocks visible and their +x/+y/+z neighbours active
+ *       (Sec. 3.4), groups the ray-block entries by block (Sec. 3.6, 4.2),
+ *   (c) decompresses the active blocks that are not cached into a fixed
+ *       budget LRU cache (Sec. 3.5),
+ *   (d) intersects each entry's ray with the trilinear isosurface inside its
+ *       block (Sec. 3.7, 4.3) and keeps each ray's earliest hit (Sec. 4.4),
+ *   (e) compacts the rays still live for the next pass (Sec. 3, step f).
+ * k is a fixed speculation count or floor(w*h / N_Act) capped at k_max
+ * (Sec. 4).  Every step runs in CUDA kernels on one GPU; the host reads one
+ * small counter record per pass.
+ *
+ * Conventions
+ *   - Every function returns an int status: SPR_OK (0) or a negative
+ *     SPR_ERR_* code.  Nothing throws or exits across the ABI.  The text of
+ *     the most recent error of the calling thread is spr_last_error().
+ *   - Handles are opaque; one host thread uses a handle at a time.
+ *   - spr_stream is a cudaStream_t passed as void* (NULL: the legacy default
+ *     stream).  Work is ordered on that stream; functions that return
+ *     statistics synchronise it.
+ *   - "device" pointers are CUDA device memory of the current device; "host"
+ *     pointers are ordinary (or pinned) host memory.  Caller buffers are only
+ *     borrowed for the duration of the call unless stated otherwise.
+ *   - Device memory the library needs is taken from the allocator set with
+ *     spr_set_allocator (default: cudaMalloc/cudaFree); allocation failure is
+ *     SPR_ERR_OUT_OF_MEMORY.
+ *
+ * Geometry (Sec. 3.2, 3.7): voxel (x,y,z) sits at point (x,y,z); the domain is
+ * [0,Dx-1]x[0,Dy-1]x[0,Dz-1]; cell (x,y,z) is the unit cube with that lower
+ * corner and the field inside is the trilinear interpolant of its corners.
+ * The ray of pixel (i,j) (j = 0 the bottom row, pixel id i + W*j) is
+ * eye + t*d with d = (p00 + (i+0.5f)*du) + (j+0.5f)*dv evaluated per
+ * component in IEEE single precision without fused multiply-add; the hit is
+ * the first point along the ray where the interpolant equals the isovalue.
+ */
+#ifndef SPR_H
+#define SPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define SPR_OK                    0
+#define SPR_ERR_INVALID_ARG      -1  /* a bad pointer, size, camera or mode          */
+#define SPR_ERR_OUT_OF_MEMORY    -2  /* the allocator returned NULL                  */
+#define SPR_ERR_CACHE_TOO_SMALL  -3  /* cache budget below 8 slots (8 x 256 bytes)   */
+#define SPR_ERR_CUDA             -4  /* a CUDA runtime call failed                   */
+#define SPR_ERR_DEVICE_TIMEOUT   -5  /* a bounded device-side wait gave up           */
+#define SPR_ERR_NOT_CONVERGED    -6  /* max_passes reached with rays still live      */
+#define SPR_ERR_NOT_IMPLEMENTED  -7
+#define SPR_ERR_NO_DEVICE        -8  /* no CUDA device / wrong architecture          */
+#define SPR_ERR_DEVICE_ERROR     -9  /* a kernel reported an internal error flag     */
+
+typedef void *spr_stream;
+typedef struct spr_volume spr_volume;
+typedef struct spr_renderer spr_renderer;
+
+/* text of the calling thread's most recent error ("" if none) */
+const char *spr_last_error(void);
+/* fixed description of a status code */
+const char *spr_status_string(int status);
+/* library version, e.g. 10000 for 1.0.0 */
+int spr_version(void);
+
+/* ------------------------------------------------------------- allocator */
+/* Process-wide device allocator for all library-owned memory.  alloc returns
+ * a device pointer of at least `bytes` (256-byte aligned) or NULL; free
+ * releases it.  `stream` is the stream the memory is first used on.  Passing
+ * NULL for both restores cudaMalloc/cudaFree.  Set it while no handle is
+ * alive; memory is freed with the allocator that allocated it. */
+typedef void *(*spr_alloc_fn)(size_t bytes, spr_stream stream, void *ctx);
+typedef void (*spr_free_fn)(void *ptr, size_t bytes, spr_stream stream, void *ctx);
+int spr_set_allocator(spr_alloc_fn alloc, spr_free_fn free_fn, void *ctx);
+
+/* ------------------------------------------------------------------ codec */
+/*
+ * FRC4: the fixed-rate 4^3 block codec that stands in for the ZFP
+ * fixed-rate mode the paper decompresses on the GPU (Sec. 3.1, 3.5).  At rate
+ * R (1..32 bits per value) every block is 8*R bytes, block b (x-fastest over
+ * the nb = ceil(D/4) block grid) at byte 8*R*b.  A block is: a 1 bit "block
+ * is nonzero" (else all zero), 8 bits emax+127 (emax = largest frexp exponent,
+ * clamped to >= -100), then bit planes 29..0 of the negabinary, sequency-
+ * ordered coefficients of a two-level integer S-transform along x, y, z of
+ * q = round-half-even(x * 2^(24-emax)), each plane as refinement bits of the
+ * significant prefix followed by group tests, cut at the budget.  Bit k of a
+ * block is bit k&7 of byte k>>3.  Partial blocks repeat the last voxel.
+ */
+#define SPR_CODEC_FRC4 1
+
+/* Compress a device volume (x fastest, dims[0]*dims[1]*dims[2] values) into
+ * out (device, nb[0]*nb[1]*nb[2]*8*rate bytes).  u8 voxels are read as
+ * (float)u / 255.0f.  Non-finite input -> SPR_ERR_INVALID_ARG. */
+int spr_encode_f32(const float *vol, const int32_t dims[3], int rate, uint8_t *out,
+                   spr_stream stream);
+int spr_encode_u8(const uint8_t *vol, const int32_t dims[3], int rate, uint8_t *out,
+                  spr_stream stream);
+
+/* Decompress n blocks of a device block stream into out (device, n*64
+ * floats, block-major, value index x + 4y + 16z).  ids (device, n entries)
+ * selects the blocks; ids == NULL means blocks 0..n-1.  The block id must be
+ * below n_blocks (the stream's block count); larger ids are an error. */
+int spr_decode_blocks(const uint8_t *blocks, int64_t n_blocks, int rate, const uint32_t *ids,
+                      int64_t n, float *out, spr_stream stream);
+
+/* ----------------------------------------------------------------- volume */
+typedef struct {
+    int32_t dims[3];        /* voxels per axis, each in [2, 4096]              */
+    int32_t rate;           /* bits per value, 1..32                           */
+    int32_t codec;          /* SPR_CODEC_FRC4                                  */
+} spr_volume_desc;
+
+/* Create a volume from its compressed blocks (Sec. 3.1).  blocks points to
+ * nbytes = nb[0]*nb[1]*nb[2]*8*rate bytes, in device memory if
+ * blocks_on_device, else in host memory.  The library copies them, decodes
+ * every block once to get its value range, and builds the fine (per block)
+ * and coarse (per 4^3 blocks) macrocell grids, each range combined with the
+ * +x/+y/+z neighbours' (Sec. 3.1).  Ordered on `stream`; returns after the
+ * work is enqueued.  *out is owned by the caller (spr_destroy_volume). */
+int spr_create_volume(const spr_volume_desc *desc, const void *blocks, size_t nbytes,
+                      int blocks_on_device, spr_stream stream, spr_volume **out);
+int spr_destroy_volume(spr_volume *vol);
+
+/* Copy the volume's range grids to host memory: fine = nb blocks x (min,max),
+ * coarse = ceil(nb/4) cells x (min,max), float pairs (either may be NULL).
+ * Synchronises `stream`. */
+int spr_volume_ranges(const spr_volume *vol, float *fine_host, float *coarse_host,
+                      spr_stream stream);
+/* block-grid and coarse-grid sizes; either pointer may be NULL */
+int spr_volume_shape(const spr_volume *vol, int64_t nb[3], int64_t nc[3]);
+
+/* --------------------------------------------------------------- renderer */
+#define SPR_SPEC_FIXED    0   /* k = the given count every pass                */
+#define SPR_SPEC_ADAPTIVE 1   /* k = min(k_max, floor(w*h / N_Act)) (Sec. 4)   */
+#define SPR_K_LIMIT       4096
+
+typedef struct {
+    int32_t pass;           /* 1-based pass index since the last reset          */
+    int32_t k;              /* speculation count from the rule                  */
+    int32_t k_used;         /* after halving on cache overflow                  */
+    int32_t retries;        /* passes redone because the cache was too small    */
+    int64_t n_active;       /* live rays at pass start (N_Act)                  */
+    int64_t n_processed;    /* live rays taken this pass                        */
+    int64_t n_entries;      /* non-empty ray-block entries (speculated included)*/
+    int64_t n_visible;      /* unique visible blocks (I_BVis)                   */
+    int64_t n_requested;    /* unique active blocks: visible + neighbours       */
+    int64_t n_decoded;      /* cache misses = blocks decompressed               */
+    int64_t n_evicted;      /* misses that replaced a cached block              */
+    int64_t n_term_hit;     /* rays finished with a hit this pass               */
+    int64_t n_term_miss;    /* rays that left the volume this pass              */
+    int64_t n_active_after; /* live rays after the pass                         */
+    double  utilization;    /* n_entries / (w*h) (Table 2)                      */
+    float   ms;             /* device time of the pass (profiling on, else 0)   */
+    float   ms_stage[6];    /* traverse, group, cache, decode, intersect, resolve*/
+} spr_pass_stats;
+
+typedef struct {
+    int32_t passes;
+    int32_t converged;      /* 1 when no live ray is left                       */
+    int64_t blocks_decoded; /* over all passes                                  */
+    int64_t bytes_decoded;  /* blocks_decoded * 256                             */
+    int64_t entries;        /* ray-block tests over all passes                  */
+    int64_t evictions;
+    int64_t n_rays;         /* rays that entered the volume                     */
+    int64_t n_hits;
+    float   ms_total;       /* device time from ray generation to convergence   */
+    float   ms_raygen;
+} spr_render_stats;
+
+/* Framebuffer (device, owned by the renderer; valid until the next set_* or
+ * render call).  Pixel p = i + W*j. */
+typedef struct {
+    int32_t   width, height;
+    float    *depth;        /* t*|d| in voxels; +inf where no hit               */
+    uint32_t *rgba;         /* grey shade g as g|g<<8|g<<16|255<<24; 0 = no hit  */
+    uint32_t *block;        /* hit block id (x-fastest over nb) or 0xFFFFFFFF   */
+    uint64_t *cell;         /* hit cell x + Dx*(y + Dy*z) or ~0                 */
+    int32_t  *final_pass;   /* pass in which the pixel became final; 0 = never  */
+    uint8_t  *status;       /* 0 live, 1 hit, 2 left the volume / missed it     */
+} spr_framebuffer;
+
+/* Create a renderer of a width x height image for vol (which must outlive
+ * it).  Defaults: isovalue 0.5, adaptive speculation with k_max 64, cache
+ * budget 256 MiB, no camera (render calls fail until spr_set_camera). */
+int spr_create_renderer(spr_volume *vol, int width, int height, spr_renderer **out);
+int spr_destroy_renderer(spr_renderer *r);
+
+/* Camera (Sec. 3.2): float triples eye, p00, du, dv (see the geometry note
+ * above).  Each eye component must be a multiple of 1/256 with magnitude
+ * below 16384, and every component of p00, du, dv zero or of magnitude in
+ * [2^-40, 2^40]; otherwise SPR_ERR_INVALID_ARG.  With these bounds every
+ * plane offset X - eye is exact in single precision, which the exact
+ * traversal predicates rely on.  Restarts the render. */
+int spr_set_camera(spr_renderer *r, const float eye[3], const float p00[3], const float du[3],
+                   const float dv[3]);
+/* isovalue (finite); restarts the render (the cache contents are kept) */
+int spr_set_isovalue(spr_renderer *r, float iso);
+/* cache budget in bytes; slots = bytes / 256, at least 8, else
+ * SPR_ERR_CACHE_TOO_SMALL.  Empties the cache and restarts the render. */
+int spr_set_cache_budget(spr_renderer *r, size_t bytes);
+/* mode SPR_SPEC_FIXED with 1 <= k <= SPR_K_LIMIT, or SPR_SPEC_ADAPTIVE with
+ * 1 <= k_max <= SPR_K_LIMIT (k ignored).  Restarts the render. */
+int spr_set_speculation(spr_renderer *r, int mode, int k, int k_max);
+/* empty the block cache (the next pass decodes from scratch) */
+int spr_reset_cache(spr_renderer *r);
+/* per-pass CUDA-event timing of the stages (adds host synchronisation) */
+int spr_set_profiling(spr_renderer *r, int on);
+
+/* Run one pass (steps a-e above) on `stream`.  The first pass after a set_*
+ * call also generates the rays.  On a converged render it does nothing and
+ * reports n_active = 0.  Synchronises `stream` once (to read the pass's
+ * counters).  out may be NULL. */
+int spr_render_pass(spr_renderer *r, spr_stream stream, spr_pass_stats *out);
+
+/* Run passes until no ray is live or max_passes passes ran (then
+ * SPR_ERR_NOT_CONVERGED, with the partial image valid).  per_pass (may be
+ * NULL) receives up to max_passes records.  out may be NULL. */
+int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int max_passes,
+                              spr_render_stats *out, spr_pass_stats *per_pass);
+
+/* device pointers of the current framebuffer */
+int spr_get_framebuffer(spr_renderer *r, spr_framebuffer *out);
+
+/* Copy the framebuffer to host buffers of width*height entries each (any may
+ * be NULL); synchronises `stream`. */
+int spr_read_framebuffer(spr_renderer *r, spr_stream stream, float *depth, uint32_t *rgba,
+                         uint32_t *block, uint64_t *cell, int32_t *final_pass,
+                         uint8_t *status);
+
+/* --------------------------------------------------------------- scan */
+/* Exclusive prefix sum of n uint32 values (device in/out; in == out allowed),
+ * total written to *total (device, may be NULL), by a single-pass
+ * decoupled-lookback scan (the prefix sums of Sec. 3.6).  Its waits on
+ * predecessor tiles are bounded: a wait that gives up returns
+ * SPR_ERR_DEVICE_TIMEOUT (synchronises `stream`). */
+int spr_exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
+                           spr_stream stream);
+
+/* Test hook for the bounded wait: like spr_exclusive_scan_u32 but tile
+ * `withhold_tile` never publishes its sum, so its successors wait until the
+ * limit of `spin_limit` polls and report SPR_ERR_DEVICE_TIMEOUT. */
+int spr_debug_scan_withhold(const uint32_t *in, uint32_t *out, int64_t n,
+                            int64_t withhold_tile, int64_t spin_limit, spr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

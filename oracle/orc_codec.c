@@ -31,26 +31,30 @@ static int get_bit(bit_reader *r)
 }
 
 /* ---------------- the integer decorrelating transform -------------------- */
-/* Arithmetic right shift of a negative int is floor division by two with gcc
- * and clang (two's complement), which is what the transform needs. */
+/* Additions wrap modulo 2^32 (they never do for streams the encoder writes,
+ * but the decoder accepts any bits).  Arithmetic right shift of a negative
+ * int is floor division by two with gcc and clang (two's complement). */
+static int32_t add_w(int32_t a, int32_t b) { return (int32_t)((uint32_t)a + (uint32_t)b); }
+static int32_t sub_w(int32_t a, int32_t b) { return (int32_t)((uint32_t)a - (uint32_t)b); }
+
 void orc_fwd_lift4(int32_t v[4])
 {
     int32_t a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
-    int32_t d0 = a1 - a0, s0 = a0 + (d0 >> 1);
-    int32_t d1 = a3 - a2, s1 = a2 + (d1 >> 1);
-    int32_t dd = s1 - s0, ss = s0 + (dd >> 1);
+    int32_t d0 = sub_w(a1, a0), s0 = add_w(a0, d0 >> 1);
+    int32_t d1 = sub_w(a3, a2), s1 = add_w(a2, d1 >> 1);
+    int32_t dd = sub_w(s1, s0), ss = add_w(s0, dd >> 1);
     v[0] = ss; v[1] = dd; v[2] = d0; v[3] = d1;
 }
 
 void orc_inv_lift4(int32_t v[4])
 {
     int32_t ss = v[0], dd = v[1], d0 = v[2], d1 = v[3];
-    int32_t s0 = ss - (dd >> 1);
-    int32_t s1 = s0 + dd;
-    int32_t a0 = s0 - (d0 >> 1);
-    int32_t a1 = a0 + d0;
-    int32_t a2 = s1 - (d1 >> 1);
-    int32_t a3 = a2 + d1;
+    int32_t s0 = sub_w(ss, dd >> 1);
+    int32_t s1 = add_w(s0, dd);
+    int32_t a0 = sub_w(s0, d0 >> 1);
+    int32_t a1 = add_w(a0, d0);
+    int32_t a2 = sub_w(s1, d1 >> 1);
+    int32_t a3 = add_w(a2, d1);
     v[0] = a0; v[1] = a1; v[2] = a2; v[3] = a3;
 }
 

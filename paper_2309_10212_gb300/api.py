@@ -1,0 +1,324 @@
+"""Python binding of the C ABI (include/spr.h), same names as the C calls.
+
+Device buffers are torch CUDA tensors and streams are torch streams; the
+binding only marshals pointers and sizes.  Every computation runs in the CUDA
+library; without a built libspr.so or a CUDA device the calls raise."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (SPR_CODEC_FRC4, SPR_K_LIMIT, SPR_SPEC_ADAPTIVE, SPR_SPEC_FIXED,  # noqa: F401
+                   SprError, check, load)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise SprError(_lib.SPR_ERR_NO_DEVICE, "CUDA is not available")
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_ptr(t, dtype=None):
+    torch = _torch()
+    assert isinstance(t, torch.Tensor) and t.is_cuda, "expected a CUDA tensor"
+    assert t.is_contiguous(), "expected a contiguous tensor"
+    if dtype is not None:
+        assert t.dtype == dtype, "expected %s, got %s" % (dtype, t.dtype)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f3(v):
+    a = (ctypes.c_float * 3)()
+    a[:] = [float(x) for x in np.asarray(v, dtype=np.float32)]
+    return a
+
+
+def _i3(v):
+    a = (ctypes.c_int32 * 3)()
+    a[:] = [int(x) for x in v]
+    return a
+
+
+def nblocks(dims):
+    return tuple((int(d) + 3) // 4 for d in dims)
+
+
+def spr_version() -> int:
+    return load().spr_version()
+
+
+# ------------------------------------------------------------------ codec
+def spr_encode_u8(vol, rate: int, out=None, stream=None):
+    """Compress a CUDA uint8 volume of shape (Dz, Dy, Dx); returns the block
+    stream as a CUDA uint8 tensor."""
+    torch = _torch()
+    dims = (vol.shape[2], vol.shape[1], vol.shape[0])
+    nb = nblocks(dims)
+    if out is None:
+        out = torch.empty(nb[0] * nb[1] * nb[2] * 8 * rate, dtype=torch.uint8, device=vol.device)
+    check(load().spr_encode_u8(_dev_ptr(vol, torch.uint8), _i3(dims), rate, _dev_ptr(out),
+                               _stream(stream)))
+    return out
+
+
+def spr_encode_f32(vol, rate: int, out=None, stream=None):
+    torch = _torch()
+    dims = (vol.shape[2], vol.shape[1], vol.shape[0])
+    nb = nblocks(dims)
+    if out is None:
+        out = torch.empty(nb[0] * nb[1] * nb[2] * 8 * rate, dtype=torch.uint8, device=vol.device)
+    check(load().spr_encode_f32(_dev_ptr(vol, torch.float32), _i3(dims), rate, _dev_ptr(out),
+                                _stream(stream)))
+    return out
+
+
+def spr_decode_blocks(blocks, n_blocks: int, rate: int, ids=None, n=None, out=None,
+                      stream=None):
+    """Decompress blocks (all of them, or the CUDA uint32 `ids`) into a CUDA
+    float32 tensor of shape (n, 64)."""
+    torch = _torch()
+    if n is None:
+        n = n_blocks if ids is None else ids.numel()
+    if out is None:
+        out = torch.empty((n, 64), dtype=torch.float32, device=blocks.device)
+    idp = None if ids is None else _dev_ptr(ids, torch.int32)
+    check(load().spr_decode_blocks(_dev_ptr(blocks), int(n_blocks), rate, idp, int(n),
+                                   _dev_ptr(out, torch.float32), _stream(stream)))
+    return out
+
+
+def spr_exclusive_scan_u32(x, out=None, stream=None):
+    """Exclusive prefix sum of a CUDA int32 tensor (read as uint32); returns
+    (out, total)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty_like(x)
+    total = torch.zeros(1, dtype=torch.int32, device=x.device)
+    check(load().spr_exclusive_scan_u32(_dev_ptr(x), _dev_ptr(out), x.numel(), _dev_ptr(total),
+                                        _stream(stream)))
+    return out, total
+
+
+def spr_debug_scan_withhold(x, withhold_tile: int, spin_limit: int, out=None, stream=None):
+    """The bounded-wait test hook; returns the status instead of raising."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty_like(x)
+    return load().spr_debug_scan_withhold(_dev_ptr(x), _dev_ptr(out), x.numel(),
+                                          int(withhold_tile), int(spin_limit), _stream(stream))
+
+
+# ----------------------------------------------------------------- volume
+class Volume:
+    def __init__(self, handle, dims, rate):
+        self.handle = handle
+        self.dims = tuple(int(d) for d in dims)
+        self.rate = rate
+
+    @property
+    def nblocks(self):
+        return nblocks(self.dims)
+
+    def close(self):
+        if self.handle:
+            spr_destroy_volume(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spr_create_volume(dims, rate: int, blocks, stream=None) -> Volume:
+    """blocks: CUDA uint8 tensor (copied on the device) or numpy uint8 array
+    (copied from the host)."""
+    desc = _lib.VolumeDesc()
+    desc.dims[:] = [int(d) for d in dims]
+    desc.rate = rate
+    desc.codec = SPR_CODEC_FRC4
+    h = ctypes.c_void_p()
+    L = load()
+    if isinstance(blocks, np.ndarray):
+        b = np.ascontiguousarray(blocks, dtype=np.uint8)
+        _torch()
+        check(L.spr_create_volume(ctypes.byref(desc), b.ctypes.data_as(ctypes.c_void_p), b.nbytes,
+                                  0, _stream(stream), ctypes.byref(h)))
+    else:
+        check(L.spr_create_volume(ctypes.byref(desc), _dev_ptr(blocks), blocks.numel(), 1,
+                                  _stream(stream), ctypes.byref(h)))
+    return Volume(h, dims, rate)
+
+
+def spr_destroy_volume(vol: Volume):
+    if vol.handle:
+        check(load().spr_destroy_volume(vol.handle))
+        vol.handle = None
+
+
+def spr_volume_ranges(vol: Volume, stream=None):
+    """(fine, coarse) value ranges as float32 arrays of shape (n, 2)."""
+    nb = ctypes.c_int64 * 3
+    a, c = nb(), nb()
+    check(load().spr_volume_shape(vol.handle, a, c))
+    fine = np.zeros((a[0] * a[1] * a[2], 2), np.float32)
+    coarse = np.zeros((c[0] * c[1] * c[2], 2), np.float32)
+    check(load().spr_volume_ranges(vol.handle, fine.ctypes.data_as(ctypes.c_void_p),
+                                   coarse.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return fine, coarse
+
+
+# --------------------------------------------------------------- renderer
+class Renderer:
+    def __init__(self, handle, vol: Volume, W: int, H: int):
+        self.handle = handle
+        self.vol = vol
+        self.W, self.H = W, H
+
+    def close(self):
+        if self.handle:
+            spr_destroy_renderer(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spr_create_renderer(vol: Volume, W: int, H: int) -> Renderer:
+    h = ctypes.c_void_p()
+    check(load().spr_create_renderer(vol.handle, W, H, ctypes.byref(h)))
+    return Renderer(h, vol, W, H)
+
+
+def spr_destroy_renderer(r: Renderer):
+    if r.handle:
+        check(load().spr_destroy_renderer(r.handle))
+        r.handle = None
+
+
+def spr_set_camera(r: Renderer, eye, p00=None, du=None, dv=None):
+    """eye may be a dict with keys eye, p00, du, dv (as synth.cameras makes)."""
+    if isinstance(eye, dict):
+        eye, p00, du, dv = eye["eye"], eye["p00"], eye["du"], eye["dv"]
+    check(load().spr_set_camera(r.handle, _f3(eye), _f3(p00), _f3(du), _f3(dv)))
+
+
+def spr_set_isovalue(r: Renderer, iso: float):
+    check(load().spr_set_isovalue(r.handle, float(iso)))
+
+
+def spr_set_cache_budget(r: Renderer, nbytes: int):
+    check(load().spr_set_cache_budget(r.handle, int(nbytes)))
+
+
+def spr_set_speculation(r: Renderer, mode: int, k: int = 1, k_max: int = 64):
+    check(load().spr_set_speculation(r.handle, int(mode), int(k), int(k_max)))
+
+
+def spr_reset_cache(r: Renderer):
+    check(load().spr_reset_cache(r.handle))
+
+
+def spr_set_profiling(r: Renderer, on: bool):
+    check(load().spr_set_profiling(r.handle, 1 if on else 0))
+
+
+def spr_render_pass(r: Renderer, stream=None) -> dict:
+    st = _lib.PassStats()
+    check(load().spr_render_pass(r.handle, _stream(stream), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def spr_render_to_convergence(r: Renderer, max_passes: int = 10000, stream=None,
+                              allow_partial: bool = False):
+    """Returns (render stats, [pass stats])."""
+    rs = _lib.RenderStats()
+    per = (_lib.PassStats * max_passes)()
+    status = load().spr_render_to_convergence(r.handle, _stream(stream), int(max_passes),
+                                              ctypes.byref(rs), per)
+    if not (allow_partial and status == _lib.SPR_ERR_NOT_CONVERGED):
+        check(status)
+    return rs.as_dict(), [per[i].as_dict() for i in range(rs.passes)]
+
+
+def spr_get_framebuffer(r: Renderer) -> dict:
+    """Zero-copy CUDA tensors viewing the renderer's framebuffer."""
+    torch = _torch()
+    fb = _lib.Framebuffer()
+    check(load().spr_get_framebuffer(r.handle, ctypes.byref(fb)))
+    n = fb.width * fb.height
+
+    class _View:
+        def __init__(self, ptr, typestr):
+            self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                             "data": (ptr, False), "version": 2}
+    out = {}
+    for name, typestr in (("depth", "<f4"), ("rgba", "<u4"), ("block", "<u4"), ("cell", "<u8"),
+                          ("final_pass", "<i4"), ("status", "|u1")):
+        out[name] = torch.as_tensor(_View(getattr(fb, name), typestr), device="cuda")
+    return out
+
+
+def spr_read_framebuffer(r: Renderer, stream=None) -> dict:
+    """Host copies (numpy) of the framebuffer."""
+    n = r.W * r.H
+    out = dict(depth=np.empty(n, np.float32), rgba=np.empty(n, np.uint32),
+               block=np.empty(n, np.uint32), cell=np.empty(n, np.uint64),
+               final_pass=np.empty(n, np.int32), status=np.empty(n, np.uint8))
+    p = {k: v.ctypes.data_as(ctypes.c_void_p) for k, v in out.items()}
+    check(load().spr_read_framebuffer(r.handle, _stream(stream), p["depth"], p["rgba"],
+                                      p["block"], p["cell"], p["final_pass"], p["status"]))
+    return out
+
+
+# -------------------------------------------------------------- allocator
+_keep = []
+
+
+def spr_set_allocator(alloc=None, free=None):
+    """Install Python callables alloc(nbytes, stream) -> int pointer (0 on
+    failure) and free(ptr, nbytes, stream) as the library's device allocator;
+    no arguments restores cudaMalloc."""
+    if alloc is None:
+        check(load().spr_set_allocator(_lib.ALLOC_FN(), _lib.FREE_FN(), None))
+        _keep.clear()
+        return
+
+    def a(nbytes, stream, ctx):
+        try:
+            return int(alloc(int(nbytes), stream)) or None
+        except Exception:
+            return None
+
+    def f(ptr, nbytes, stream, ctx):
+        try:
+            free(int(ptr), int(nbytes), stream)
+        except Exception:
+            pass
+    cb = (_lib.ALLOC_FN(a), _lib.FREE_FN(f))
+    check(load().spr_set_allocator(cb[0], cb[1], None))
+    _keep[:] = [cb]
+
+
+def use_torch_allocator():
+    """Route the library's device memory through torch's caching allocator."""
+    torch = _torch()
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, stream=stream or 0)
+
+    def free(ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+    spr_set_allocator(alloc, free)

@@ -1,0 +1,377 @@
+// codec.cu -- FRC4 encode/decode kernels and volume creation (Sec. 3.1).
+//
+// create_volume decodes every block once to get its value range, then builds
+// the fine grid (one cell per block) and the coarse grid (one cell per 4^3
+// blocks), each cell's range combined with its +x/+y/+z neighbours' ranges.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "frc4.cuh"
+#include "kernels.cuh"
+#include "spr_common.cuh"
+
+namespace spr {
+
+VolGeom make_geom(const int32_t dims[3], int rate)
+{
+    VolGeom g{};
+    g.rate = rate;
+    g.nblocks = 1;
+    g.ncoarse = 1;
+    for (int a = 0; a < 3; ++a) {
+        g.dims[a] = dims[a];
+        g.nb[a] = (dims[a] + 3) / 4;
+        g.nc[a] = (g.nb[a] + 3) / 4;
+        g.tb[a] = (dims[a] - 1 + 3) / 4;
+        g.tc[a] = (g.tb[a] + 3) / 4;
+        g.nblocks *= g.nb[a];
+        g.ncoarse *= g.nc[a];
+    }
+    return g;
+}
+
+// ---------------------------------------------------------------- kernels
+__device__ __forceinline__ void load_order(uint8_t *order_s)
+{
+    if (threadIdx.x < 64) order_s[threadIdx.x] = frc4::kOrder.v[threadIdx.x];
+    __syncthreads();
+}
+
+// raw range of each block: min/max of its decoded in-domain voxels
+__global__ void __launch_bounds__(kDecThreads) range_kernel(const uint8_t *__restrict__ comp,
+                                                            VolGeom g, float2 *__restrict__ raw)
+{
+    __shared__ uint32_t col_s[64 * kColStride];
+    __shared__ uint8_t order_s[64];
+    load_order(order_s);
+    uint32_t *col = col_s + threadIdx.x;
+    const int64_t bytes = 8 * (int64_t)g.rate;
+    for (int64_t b = (int64_t)blockIdx.x * kDecThreads + threadIdx.x; b < g.nblocks;
+         b += (int64_t)gridDim.x * kDecThreads) {
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(comp + b * bytes);
+        int emax = 0;
+        float mn = 0.0f, mx = 0.0f;
+        if (frc4::decode_coeffs(w, g.rate, col, kColStride, order_s, &emax)) {
+            int64_t bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / ((int64_t)g.nb[0] * g.nb[1]);
+            int ex = min(4, (int)(g.dims[0] - 4 * bx));
+            int ey = min(4, (int)(g.dims[1] - 4 * by));
+            int ez = min(4, (int)(g.dims[2] - 4 * bz));
+            float v[64];
+            frc4::reconstruct(col, kColStride, emax, v);
+            mn = INFINITY;
+            mx = -INFINITY;
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+                bool in = (i & 3) < ex && ((i >> 2) & 3) < ey && (i >> 4) < ez;
+                if (in) {
+                    mn = fminf(mn, v[i]);
+                    mx = fmaxf(mx, v[i]);
+                }
+            }
+        }
+        raw[b] = make_float2(mn, mx);
+    }
+}
+
+// union of a cell's range with its +x/+y/+z face, edge and corner neighbours
+__global__ void plus_union_kernel(const float2 *__restrict__ in, int nx, int ny, int nz,
+                                  float2 *__restrict__ out)
+{
+    int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
+        float mn = INFINITY, mx = -INFINITY;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            int xx = x + (o & 1), yy = y + ((o >> 1) & 1), zz = z + (o >> 2);
+            if (xx < nx && yy < ny && zz < nz) {
+                float2 r = in[xx + (int64_t)nx * (yy + (int64_t)ny * zz)];
+                mn = fminf(mn, r.x);
+                mx = fmaxf(mx, r.y);
+            }
+        }
+        out[c] = make_float2(mn, mx);
+    }
+}
+
+// range of the 4^3 blocks of each coarse cell
+__global__ void coarse_raw_kernel(const float2 *__restrict__ raw, VolGeom g, float2 *__restrict__ craw)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncoarse;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int cx = (int)(c % g.nc[0]), cy = (int)((c / g.nc[0]) % g.nc[1]),
+            cz = (int)(c / ((int64_t)g.nc[0] * g.nc[1]));
+        float mn = INFINITY, mx = -INFINITY;
+        for (int z = 4 * cz; z < min(4 * cz + 4, g.nb[2]); ++z)
+            for (int y = 4 * cy; y < min(4 * cy + 4, g.nb[1]); ++y)
+                for (int x = 4 * cx; x < min(4 * cx + 4, g.nb[0]); ++x) {
+                    float2 r = raw[x + (int64_t)g.nb[0] * (y + (int64_t)g.nb[1] * z)];
+                    mn = fminf(mn, r.x);
+                    mx = fmaxf(mx, r.y);
+                }
+        craw[c] = make_float2(mn, mx);
+    }
+}
+
+// encode: one thread per block, edge-replicating partial blocks
+template <class T>
+__global__ void encode_kernel(const T *__restrict__ vol, VolGeom g, uint8_t *__restrict__ out,
+                              unsigned int *bad)
+{
+    const int64_t bytes = 8 * (int64_t)g.rate;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < g.nblocks;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        int64_t bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / ((int64_t)g.nb[0] * g.nb[1]);
+        float v[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+            int64_t x = min(4 * bx + (i & 3), (int64_t)g.dims[0] - 1);
+            int64_t y = min(4 * by + ((i >> 2) & 3), (int64_t)g.dims[1] - 1);
+            int64_t z = min(4 * bz + (i >> 4), (int64_t)g.dims[2] - 1);
+            T raw = vol[x + (int64_t)g.dims[0] * (y + (int64_t)g.dims[1] * z)];
+            if constexpr (sizeof(T) == 1)
+                v[i] = __fdiv_rn((float)raw, 255.0f);
+            else
+                v[i] = (float)raw;
+        }
+        uint32_t *w = reinterpret_cast<uint32_t *>(out + b * bytes);
+        if (!frc4::encode_block(v, g.rate, w)) atomicOr(bad, 1u);
+    }
+}
+
+// decode blocks ids[i] (or i) to out + dst[i]*64 (or i*64), a warp writing
+// its 32 blocks with coalesced stores
+__global__ void __launch_bounds__(kDecThreads) decode_list_kernel(
+    const uint8_t *__restrict__ comp, int64_t nblocks, int rate, const uint32_t *__restrict__ ids,
+    const uint32_t *__restrict__ dst_ids, int64_t n_host, const uint32_t *n_dev,
+    const uint32_t *skip, float *__restrict__ out, unsigned int *bad)
+{
+    __shared__ uint32_t col_s[64 * kColStride];
+    __shared__ uint8_t order_s[64];
+    if (skip && *skip) return;
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    load_order(order_s);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t *col = col_s + threadIdx.x;
+    const int64_t bytes = 8 * (int64_t)rate;
+    for (int64_t base = (int64_t)blockIdx.x * kDecThreads + wid * 32; base < n;
+         base += (int64_t)gridDim.x * kDecThreads) {
+        int64_t i = base + lane;
+        if (i < n) {
+            int64_t id = ids ? (int64_t)ids[i] : i;
+            float v[64];
+            int emax = 0;
+            bool nz = false;
+            if (id < nblocks) {
+                const uint32_t *w = reinterpret_cast<const uint32_t *>(comp + id * bytes);
+                nz = frc4::decode_coeffs(w, rate, col, kColStride, order_s, &emax);
+            } else {
+                atomicOr(bad, 1u);
+            }
+            if (nz) {
+                frc4::reconstruct(col, kColStride, emax, v);
+#pragma unroll
+                for (int k = 0; k < 64; ++k) col[k * kColStride] = __float_as_uint(v[k]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 64; ++k) col[k * kColStride] = 0u;
+            }
+        }
+        __syncwarp();
+        const int64_t m = n - base < 32 ? n - base : 32;
+        for (int t = 0; t < m; ++t) {
+            int64_t slot = dst_ids ? (int64_t)dst_ids[base + t] : base + t;
+            float *dst = out + slot * 64;
+            const uint32_t *src = col_s + wid * 32 + t;
+            dst[lane] = __uint_as_float(src[lane * kColStride]);
+            dst[lane + 32] = __uint_as_float(src[(lane + 32) * kColStride]);
+        }
+        __syncwarp();
+    }
+}
+
+int grid_for(int64_t n, int threads, int per_sm)
+{
+    int64_t g = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)device_sm_count() * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+static int check_dims_rate(const int32_t dims[3], int rate)
+{
+    if (!dims) return set_error(SPR_ERR_INVALID_ARG, "dims is NULL");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 2 || dims[a] > 4096)
+            return set_error(SPR_ERR_INVALID_ARG, "dims[%d] = %d outside [2, 4096]", a, dims[a]);
+    if (rate < 1 || rate > 32) return set_error(SPR_ERR_INVALID_ARG, "rate %d outside [1, 32]", rate);
+    return SPR_OK;
+}
+
+template <class T>
+static int encode_impl(const T *vol, const int32_t dims[3], int rate, uint8_t *out, spr_stream st)
+{
+    clear_error();
+    SPR_TRY(check_dims_rate(dims, rate));
+    if (!vol || !out) return set_error(SPR_ERR_INVALID_ARG, "NULL buffer");
+    cudaStream_t s = as_stream(st);
+    VolGeom g = make_geom(dims, rate);
+    DevBuf flag;
+    SPR_TRY(buf_alloc(flag, sizeof(unsigned int), s));
+    SPR_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(unsigned int), s));
+    encode_kernel<T><<<grid_for(g.nblocks, 128, 16), 128, 0, s>>>(vol, g, out, flag.as<unsigned int>());
+    SPR_CUDA_TRY(cudaGetLastError());
+    unsigned int bad = 0;
+    SPR_CUDA_TRY(cudaMemcpyAsync(&bad, flag.p, sizeof bad, cudaMemcpyDeviceToHost, s));
+    SPR_CUDA_TRY(cudaStreamSynchronize(s));
+    buf_free(flag, s);
+    if (bad) return set_error(SPR_ERR_INVALID_ARG, "volume holds non-finite values");
+    return SPR_OK;
+}
+
+int launch_decode_list(const uint8_t *comp, int64_t nblocks, int rate, const uint32_t *ids,
+                       const uint32_t *dst, int64_t n_host, const uint32_t *n_dev,
+                       const uint32_t *skip, float *out, unsigned int *bad, cudaStream_t s)
+{
+    if (n_host <= 0) return SPR_OK;
+    decode_list_kernel<<<grid_for(n_host, kDecThreads, 8), kDecThreads, 0, s>>>(
+        comp, nblocks, rate, ids, dst, n_host, n_dev, skip, out, bad);
+    SPR_CUDA_TRY(cudaGetLastError());
+    return SPR_OK;
+}
+
+}  // namespace spr
+
+using namespace spr;
+
+extern "C" int spr_encode_f32(const float *vol, const int32_t dims[3], int rate, uint8_t *out,
+                              spr_stream stream)
+{
+    return encode_impl<float>(vol, dims, rate, out, stream);
+}
+
+extern "C" int spr_encode_u8(const uint8_t *vol, const int32_t dims[3], int rate, uint8_t *out,
+                             spr_stream stream)
+{
+    return encode_impl<uint8_t>(vol, dims, rate, out, stream);
+}
+
+extern "C" int spr_decode_blocks(const uint8_t *blocks, int64_t n_blocks, int rate,
+                                 const uint32_t *ids, int64_t n, float *out, spr_stream stream)
+{
+    clear_error();
+    if (!blocks || !out || n < 0 || n_blocks < 1)
+        return set_error(SPR_ERR_INVALID_ARG, "bad decode arguments");
+    if (rate < 1 || rate > 32) return set_error(SPR_ERR_INVALID_ARG, "rate %d outside [1, 32]", rate);
+    if (!ids && n > n_blocks) return set_error(SPR_ERR_INVALID_ARG, "n exceeds the block count");
+    cudaStream_t s = as_stream(stream);
+    DevBuf flag;
+    SPR_TRY(buf_alloc(flag, sizeof(unsigned int), s));
+    SPR_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(unsigned int), s));
+    int rc = launch_decode_list(blocks, n_blocks, rate, ids, nullptr, n, nullptr, nullptr, out,
+                                flag.as<unsigned int>(), s);
+    unsigned int bad = 0;
+    if (rc == SPR_OK) {
+        cudaError_t e = cudaMemcpyAsync(&bad, flag.p, sizeof bad, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = set_error(SPR_ERR_CUDA, "decode: %s", cudaGetErrorString(e));
+    }
+    buf_free(flag, s);
+    if (rc == SPR_OK && bad) rc = set_error(SPR_ERR_INVALID_ARG, "a block id is out of range");
+    return rc;
+}
+
+extern "C" int spr_create_volume(const spr_volume_desc *desc, const void *blocks, size_t nbytes,
+                                 int blocks_on_device, spr_stream stream, spr_volume **out)
+{
+    clear_error();
+    if (!desc || !blocks || !out) return set_error(SPR_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    SPR_TRY(check_dims_rate(desc->dims, desc->rate));
+    if (desc->codec != SPR_CODEC_FRC4) return set_error(SPR_ERR_INVALID_ARG, "unknown codec %d", desc->codec);
+    VolGeom g = make_geom(desc->dims, desc->rate);
+    size_t need = (size_t)g.nblocks * 8 * (size_t)g.rate;
+    if (nbytes != need)
+        return set_error(SPR_ERR_INVALID_ARG, "expected %zu compressed bytes, got %zu", need, nbytes);
+    cudaStream_t s = as_stream(stream);
+    spr_volume *v = new (std::nothrow) spr_volume();
+    if (!v) return set_error(SPR_ERR_OUT_OF_MEMORY, "host allocation failed");
+    v->g = g;
+    DevBuf raw, craw;
+    int rc = SPR_OK;
+    auto fail = [&](int code) {
+        buf_free(raw, s);
+        buf_free(craw, s);
+        buf_free(v->comp, s);
+        buf_free(v->fine, s);
+        buf_free(v->coarse, s);
+        delete v;
+        return code;
+    };
+    if ((rc = buf_alloc(v->comp, need, s)) || (rc = buf_alloc(v->fine, sizeof(float2) * g.nblocks, s)) ||
+        (rc = buf_alloc(v->coarse, sizeof(float2) * g.ncoarse, s)) ||
+        (rc = buf_alloc(raw, sizeof(float2) * g.nblocks, s)) ||
+        (rc = buf_alloc(craw, sizeof(float2) * g.ncoarse, s)))
+        return fail(rc);
+    cudaError_t e = cudaMemcpyAsync(v->comp.p, blocks, need,
+                                    blocks_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(set_error(SPR_ERR_CUDA, "copy of blocks: %s", cudaGetErrorString(e)));
+    range_kernel<<<grid_for(g.nblocks, kDecThreads, 8), kDecThreads, 0, s>>>(v->comp.as<uint8_t>(), g,
+                                                                           raw.as<float2>());
+    plus_union_kernel<<<grid_for(g.nblocks, 256, 8), 256, 0, s>>>(raw.as<float2>(), g.nb[0], g.nb[1], g.nb[2],
+                                                                 v->fine.as<float2>());
+    coarse_raw_kernel<<<grid_for(g.ncoarse, 256, 8), 256, 0, s>>>(raw.as<float2>(), g, craw.as<float2>());
+    plus_union_kernel<<<grid_for(g.ncoarse, 256, 8), 256, 0, s>>>(craw.as<float2>(), g.nc[0], g.nc[1],
+                                                                 g.nc[2], v->coarse.as<float2>());
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(set_error(SPR_ERR_CUDA, "volume setup: %s", cudaGetErrorString(e)));
+    buf_free(raw, s);
+    buf_free(craw, s);
+    *out = v;
+    return SPR_OK;
+}
+
+extern "C" int spr_destroy_volume(spr_volume *v)
+{
+    clear_error();
+    if (!v) return SPR_OK;
+    cudaDeviceSynchronize();
+    buf_free(v->comp, nullptr);
+    buf_free(v->fine, nullptr);
+    buf_free(v->coarse, nullptr);
+    delete v;
+    return SPR_OK;
+}
+
+extern "C" int spr_volume_ranges(const spr_volume *v, float *fine_host, float *coarse_host,
+                                 spr_stream stream)
+{
+    clear_error();
+    if (!v) return set_error(SPR_ERR_INVALID_ARG, "NULL volume");
+    cudaStream_t s = as_stream(stream);
+    if (fine_host)
+        SPR_CUDA_TRY(cudaMemcpyAsync(fine_host, v->fine.p, sizeof(float2) * v->g.nblocks,
+                                     cudaMemcpyDeviceToHost, s));
+    if (coarse_host)
+        SPR_CUDA_TRY(cudaMemcpyAsync(coarse_host, v->coarse.p, sizeof(float2) * v->g.ncoarse,
+                                     cudaMemcpyDeviceToHost, s));
+    SPR_CUDA_TRY(cudaStreamSynchronize(s));
+    return SPR_OK;
+}
+
+extern "C" int spr_volume_shape(const spr_volume *v, int64_t nb[3], int64_t nc[3])
+{
+    clear_error();
+    if (!v) return set_error(SPR_ERR_INVALID_ARG, "NULL volume");
+    for (int a = 0; a < 3; ++a) {
+        if (nb) nb[a] = v->g.nb[a];
+        if (nc) nc[a] = v->g.nc[a];
+    }
+    return SPR_OK;
+}

@@ -1,0 +1,1484 @@
+// render.cu -- the per-pass wavefront of the speculative progressive
+// isosurface raycaster (Fig. 2, Sec. 3, 4) and the renderer part of the C ABI.
+//
+// One pass, all on the device, one host read of a small counter record:
+//   traverse   (Sec. 3.3, 4.1) each live ray resumes its two-level walk
+//              (coarse cells of 4^3 blocks, then blocks) and records its next
+//              k visible blocks in R_BID at i*k + j; the visible block and its
+//              +x/+y/+z neighbours are marked in two bitmaps (Sec. 3.4);
+//   group      (Sec. 3.6, 4.2) the bitmaps compact to sorted lists I_BVis and
+//              I_BAct; entries are counted per visible block, scanned into
+//              O_BRays and scattered so each block's entries are contiguous;
+//   cache      (Sec. 3.5) active blocks are looked up; misses take the least
+//              recently used slots not needed by this pass;
+//   decode     the misses are decompressed into their slots;
+//   intersect  (Sec. 3.7, 4.3) each entry's ray is clipped to its block and
+//              walked cell by cell; the first root of the trilinear cubic is
+//              packed into a 64-bit key and atomicMin'ed per ray (Sec. 4.4);
+//   resolve    hits and rays that left the volume are written out; the live
+//              rays are compacted, in order, for the next pass.
+// Traversal decisions use exact predicates (spr_common.cuh); intersection
+// runs in block-local single precision.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "kernels.cuh"
+#include "scan.cuh"
+#include "spr_common.cuh"
+
+namespace spr {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint64_t kNoKey = ~0ull;
+constexpr uint64_t kStep = 1;   // state flag: the saved block was already taken
+constexpr uint64_t kDone = 2;   // state flag: the walk left the volume
+
+// counter record, device resident, read by the host once per pass
+enum Ctr {
+    C_NVIS = 0,
+    C_NACT,
+    C_NENT,
+    C_NMISS,
+    C_NUNTOUCHED,
+    C_NLIVE,
+    C_OVERFLOW,
+    C_EVICT,
+    C_HIT,
+    C_MISSRAY,
+    C_SCANFLAGS,
+    C_BAD,
+    C_COUNT = 16
+};
+
+struct Cam {
+    float eye[3], p00[3], du[3], dv[3];
+};
+
+struct Geo {
+    VolGeom g;
+    const float2 *fine;
+    const float2 *coarse;
+    float iso;
+    Cam cam;
+    int W;
+};
+
+__device__ __forceinline__ bool holds(float2 r, float iso) { return r.x <= iso && iso <= r.y; }
+
+__device__ __forceinline__ uint64_t pack_state(const int b[3], uint64_t flags)
+{
+    return (uint64_t)(b[0] & 0xFFFF) | ((uint64_t)(b[1] & 0xFFFF) << 16) |
+           ((uint64_t)(b[2] & 0xFFFF) << 32) | (flags << 48);
+}
+
+// ---------------------------------------------------------- exact walking
+// step to the next block; false when the ray leaves the traversal grid
+__device__ bool block_step(const Ray &r, const VolGeom &g, int b[3])
+{
+    Tq tmin{0.f, 1.f};
+    int mask = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (r.sgn[a] == 0) continue;
+        float X = r.sgn[a] > 0 ? (float)min(4 * (b[a] + 1), g.dims[a] - 1) : (float)(4 * b[a]);
+        Tq t = plane_t(r, a, X);
+        int c = mask ? tcmp(t, tmin) : -1;
+        if (c < 0) {
+            tmin = t;
+            mask = 1 << a;
+        } else if (c == 0) {
+            mask |= 1 << a;
+        }
+    }
+    bool ok = mask != 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (mask >> a & 1) {
+            b[a] += r.sgn[a];
+            if (b[a] < 0 || b[a] >= g.tb[a]) ok = false;
+        }
+    return ok;
+}
+
+// leave the current coarse cell; the new block is the one containing the
+// ray just after the exit point
+__device__ bool coarse_skip(const Ray &r, const VolGeom &g, int b[3])
+{
+    int c[3] = {b[0] >> 2, b[1] >> 2, b[2] >> 2};
+    Tq tmin{0.f, 1.f};
+    int mask = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (r.sgn[a] == 0) continue;
+        float X = r.sgn[a] > 0 ? (float)min(16 * (c[a] + 1), g.dims[a] - 1) : (float)(16 * c[a]);
+        Tq t = plane_t(r, a, X);
+        int cmp = mask ? tcmp(t, tmin) : -1;
+        if (cmp < 0) {
+            tmin = t;
+            mask = 1 << a;
+        } else if (cmp == 0) {
+            mask |= 1 << a;
+        }
+    }
+    if (!mask) return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (mask >> a & 1) {
+            c[a] += r.sgn[a];
+            if (c[a] < 0 || c[a] >= g.tc[a]) return false;
+            b[a] = r.sgn[a] > 0 ? 4 * c[a] : min(4 * c[a] + 3, g.tb[a] - 1);
+        } else if (r.sgn[a] > 0) {
+            int hi = min(4 * c[a] + 3, g.tb[a] - 1);
+            while (b[a] + 1 <= hi && tcmp(plane_t(r, a, (float)(4 * (b[a] + 1))), tmin) <= 0) ++b[a];
+        } else if (r.sgn[a] < 0) {
+            while (b[a] - 1 >= 4 * c[a] && tcmp(plane_t(r, a, (float)(4 * b[a])), tmin) <= 0) --b[a];
+        }
+    }
+    return true;
+}
+
+// block index along axis a that contains p(T+)
+__device__ int locate_block(const Ray &r, int a, Tq T, int tb)
+{
+    if (r.sgn[a] == 0) {
+        float f = floorf(__fmul_rn(r.e[a], 0.25f));
+        f = fminf(fmaxf(f, 0.f), (float)(tb - 1));
+        return (int)f;
+    }
+    float p = fmaf(__fdiv_rn(T.n, T.ad), r.d[a], r.e[a]);
+    float q = fminf(fmaxf(__fmul_rn(p, 0.25f), -1.f), (float)tb);
+    int b;
+    if (r.sgn[a] > 0) {
+        b = min(max((int)floorf(q), 0), tb - 1);
+        while (b + 1 <= tb - 1 && tcmp(plane_t(r, a, (float)(4 * (b + 1))), T) <= 0) ++b;
+        while (b >= 1 && tcmp(plane_t(r, a, (float)(4 * b)), T) > 0) --b;
+    } else {
+        b = min(max((int)ceilf(q) - 1, 0), tb - 1);
+        while (b >= 1 && tcmp(plane_t(r, a, (float)(4 * b)), T) <= 0) --b;
+        while (b + 1 <= tb - 1 && tcmp(plane_t(r, a, (float)(4 * (b + 1))), T) > 0) ++b;
+    }
+    return b;
+}
+
+__device__ __forceinline__ void set_bit(uint32_t *bits, uint32_t b)
+{
+    uint32_t m = 1u << (b & 31);
+    uint32_t *w = bits + (b >> 5);
+    if (!(*w & m)) atomicOr(w, m);
+}
+
+__device__ __forceinline__ void warp_add(uint32_t *ctr, uint32_t v)
+{
+    unsigned m = __activemask();
+    uint32_t s = __reduce_add_sync(m, v);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(m) - 1) && s) atomicAdd(ctr, s);
+}
+
+// ------------------------------------------------------------- ray setup
+struct RaygenCount {
+    Geo P;
+    uint64_t *state;
+    uint8_t *status;
+    uint64_t *keys;
+    float *depth;
+    uint32_t *rgba, *block;
+    uint64_t *cell;
+    int32_t *final_pass;
+    __device__ bool enabled() const { return true; }
+    __device__ uint32_t operator()(int64_t p) const
+    {
+        keys[p] = kNoKey;
+        depth[p] = INFINITY;
+        rgba[p] = 0u;
+        block[p] = kNone;
+        cell[p] = kNoKey;
+        final_pass[p] = 0;
+        Ray r;
+        make_ray(r, P.cam.eye, P.cam.p00, P.cam.du, P.cam.dv, (int)(p % P.W), (int)(p / P.W));
+        const VolGeom &g = P.g;
+        Tq tin{0.f, 1.f}, tout{0.f, 1.f};
+        bool have_out = false;
+        for (int a = 0; a < 3; ++a) {
+            if (r.sgn[a] == 0) {
+                if (r.e[a] < 0.f || r.e[a] > (float)(g.dims[a] - 1)) {
+                    status[p] = 2;
+                    return 0;
+                }
+                continue;
+            }
+            float nearp = r.sgn[a] > 0 ? 0.f : (float)(g.dims[a] - 1);
+            float farp = r.sgn[a] > 0 ? (float)(g.dims[a] - 1) : 0.f;
+            Tq tn = plane_t(r, a, nearp), tf = plane_t(r, a, farp);
+            if (tcmp(tn, tin) > 0) tin = tn;
+            if (!have_out || tcmp(tf, tout) < 0) {
+                tout = tf;
+                have_out = true;
+            }
+        }
+        if (!have_out || tcmp(tin, tout) >= 0) {
+            status[p] = 2;
+            return 0;
+        }
+        int b[3];
+        for (int a = 0; a < 3; ++a) b[a] = locate_block(r, a, tin, g.tb[a]);
+        state[p] = pack_state(b, 0);
+        status[p] = 0;
+        return 1;
+    }
+};
+
+struct IndexEmit {
+    uint32_t *out;
+    __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
+    {
+        if (c) out[pre] = (uint32_t)i;
+    }
+};
+
+// ------------------------------------------------------------- traversal
+__global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__restrict__ live,
+                                                       uint32_t nproc, int kk,
+                                                       const uint64_t *__restrict__ state_in,
+                                                       uint64_t *__restrict__ state_out,
+                                                       uint32_t *__restrict__ rbid,
+                                                       uint32_t *vis_bits, uint32_t *act_bits)
+{
+    const VolGeom &g = P.g;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nproc;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t ray = live[i];
+        Ray r;
+        make_ray(r, P.cam.eye, P.cam.p00, P.cam.du, P.cam.dv, (int)(ray % P.W), (int)(ray / P.W));
+        const uint64_t st = state_in[ray];
+        int b[3] = {(int)(st & 0xFFFF), (int)((st >> 16) & 0xFFFF), (int)((st >> 32) & 0xFFFF)};
+        uint64_t flags = st >> 48;
+        uint32_t *out = rbid + (uint64_t)i * kk;
+        int cnt = 0;
+        bool alive = !(flags & kDone);
+        if (alive && (flags & kStep)) alive = block_step(r, g, b);
+        flags &= ~kStep;
+        while (alive) {
+            int64_t c = (b[0] >> 2) + (int64_t)g.nc[0] * ((b[1] >> 2) + (int64_t)g.nc[1] * (b[2] >> 2));
+            if (!holds(P.coarse[c], P.iso)) {
+                alive = coarse_skip(r, g, b);
+                continue;
+            }
+            uint32_t blin = (uint32_t)(b[0] + (int64_t)g.nb[0] * (b[1] + (int64_t)g.nb[1] * b[2]));
+            if (holds(P.fine[blin], P.iso)) {
+                out[cnt++] = blin;
+                set_bit(vis_bits, blin);
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    int x = b[0] + (o & 1), y = b[1] + ((o >> 1) & 1), z = b[2] + (o >> 2);
+                    if (x < g.nb[0] && y < g.nb[1] && z < g.nb[2])
+                        set_bit(act_bits, (uint32_t)(x + (int64_t)g.nb[0] * (y + (int64_t)g.nb[1] * z)));
+                }
+                if (cnt == kk) {
+                    flags |= kStep;
+                    break;
+                }
+            }
+            alive = block_step(r, g, b);
+        }
+        if (!alive) flags |= kDone;
+        for (int j = cnt; j < kk; ++j) out[j] = kNone;
+        state_out[ray] = pack_state(b, flags);
+    }
+}
+
+// --------------------------------------------------------------- grouping
+struct BitsCount {
+    const uint32_t *bits;
+    const uint32_t *skip;
+    __device__ bool enabled() const { return !skip || !*skip; }
+    __device__ uint32_t operator()(int64_t w) const { return __popc(bits[w]); }
+};
+
+struct BitsEmit {
+    const uint32_t *bits;
+    uint32_t *wpre;
+    uint32_t *list;
+    uint32_t *zero;  // optional: zero this array at each emitted position
+    __device__ void operator()(int64_t w, uint32_t pre, uint32_t c) const
+    {
+        wpre[w] = pre;
+        uint32_t x = bits[w];
+        while (x) {
+            int k = __ffs(x) - 1;
+            x &= x - 1;
+            list[pre] = (uint32_t)(w * 32 + k);
+            if (zero) zero[pre] = 0u;
+            ++pre;
+        }
+    }
+};
+
+__global__ void overflow_kernel(uint32_t *ctr, int64_t n_slots)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) ctr[C_OVERFLOW] = (int64_t)ctr[C_NACT] > n_slots ? 1u : 0u;
+}
+
+__device__ __forceinline__ uint32_t vis_rank(const uint32_t *bits, const uint32_t *wpre, uint32_t b)
+{
+    uint32_t w = b >> 5;
+    return wpre[w] + __popc(bits[w] & ((1u << (b & 31)) - 1u));
+}
+
+__global__ void count_entries_kernel(int64_t n, const uint32_t *__restrict__ rbid, const uint32_t *vis_bits,
+                                     const uint32_t *vis_wpre, uint32_t *nbrays, uint32_t *erank,
+                                     const uint32_t *ctr)
+{
+    if (ctr[C_OVERFLOW]) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t b = rbid[e];
+        if (b == kNone) continue;
+        erank[e] = atomicAdd(&nbrays[vis_rank(vis_bits, vis_wpre, b)], 1u);
+    }
+}
+
+struct ArrayCount {
+    const uint32_t *a;
+    const uint32_t *skip;
+    __device__ bool enabled() const { return !skip || !*skip; }
+    __device__ uint32_t operator()(int64_t i) const { return a[i]; }
+};
+
+struct ArrayEmit {
+    uint32_t *out;
+    __device__ void operator()(int64_t i, uint32_t pre, uint32_t) const { out[i] = pre; }
+};
+
+__global__ void scatter_entries_kernel(int64_t n, const uint32_t *__restrict__ rbid, const uint32_t *vis_bits,
+                                       const uint32_t *vis_wpre, const uint32_t *obrays,
+                                       const uint32_t *erank, uint32_t *E, const uint32_t *ctr)
+{
+    if (ctr[C_OVERFLOW]) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t b = rbid[e];
+        if (b == kNone) continue;
+        E[obrays[vis_rank(vis_bits, vis_wpre, b)] + erank[e]] = (uint32_t)e;
+    }
+}
+
+// ------------------------------------------------------------------ cache
+struct LookupCount {
+    const uint32_t *iact;
+    const uint32_t *blk_slot;
+    uint8_t *touched;
+    const uint32_t *skip;
+    __device__ bool enabled() const { return !*skip; }
+    __device__ uint32_t operator()(int64_t i) const
+    {
+        uint32_t s = blk_slot[iact[i]];
+        if (s != kNone) {
+            touched[s] = 1;
+            return 0u;
+        }
+        return 1u;
+    }
+};
+
+struct SelectEmit {
+    const uint32_t *src;
+    uint32_t *dst;
+    __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
+    {
+        if (c) dst[pre] = src[i];
+    }
+};
+
+struct VictimCount {
+    const uint32_t *lru;
+    const uint8_t *touched;
+    const uint32_t *skip;
+    __device__ bool enabled() const { return !*skip; }
+    __device__ uint32_t operator()(int64_t i) const { return touched[lru[i]] ? 0u : 1u; }
+};
+
+struct VictimEmit {
+    const uint32_t *lru;
+    const uint32_t *n_miss;
+    uint32_t *victim;
+    uint32_t *lru_next;
+    __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
+    {
+        if (!c) return;
+        uint32_t nm = *n_miss;
+        if (pre < nm) victim[pre] = lru[i];
+        else lru_next[pre - nm] = lru[i];
+    }
+};
+
+__global__ void assign_kernel(int64_t cap, const uint32_t *__restrict__ miss, const uint32_t *__restrict__ victim,
+                              uint32_t *blk_slot, uint32_t *slot_blk, uint8_t *touched, uint32_t *ctr)
+{
+    if (ctr[C_OVERFLOW]) return;
+    const int64_t n = ctr[C_NMISS];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t s = victim[i];
+        uint32_t old = slot_blk[s];
+        uint32_t ev = 0;
+        if (old != kNone) {
+            blk_slot[old] = kNone;
+            ev = 1;
+        }
+        uint32_t b = miss[i];
+        blk_slot[b] = s;
+        slot_blk[s] = b;
+        touched[s] = 1;
+        warp_add(&ctr[C_EVICT], ev);
+    }
+}
+
+struct TouchedCount {
+    const uint8_t *touched;
+    const uint32_t *skip;
+    __device__ bool enabled() const { return !*skip; }
+    __device__ uint32_t operator()(int64_t s) const { return touched[s] ? 1u : 0u; }
+};
+
+struct TouchedEmit {
+    uint8_t *touched;
+    const uint32_t *ctr;
+    uint32_t *lru_next;
+    __device__ void operator()(int64_t s, uint32_t pre, uint32_t c) const
+    {
+        if (!c) return;
+        lru_next[ctr[C_NUNTOUCHED] - ctr[C_NMISS] + pre] = (uint32_t)s;
+        touched[s] = 0;
+    }
+};
+
+__global__ void lru_init_kernel(uint32_t *lru, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        lru[i] = (uint32_t)i;
+}
+
+// -------------------------------------------------------------- intersect
+struct RT {
+    Geo P;
+    const float *cache;
+    const uint32_t *blk_slot;
+};
+
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+__device__ __forceinline__ float tri8(const float v[8], float x, float y, float z)
+{
+    float c00 = lerpf(v[0], v[1], x), c10 = lerpf(v[2], v[3], x);
+    float c01 = lerpf(v[4], v[5], x), c11 = lerpf(v[6], v[7], x);
+    return lerpf(lerpf(c00, c10, y), lerpf(c01, c11, y), z);
+}
+
+struct CellF {
+    float v[8];
+    float iso, u[3], d[3];
+    __device__ float operator()(float s) const
+    {
+        return tri8(v, fmaf(s, d[0], u[0]), fmaf(s, d[1], u[1]), fmaf(s, d[2], u[2])) - iso;
+    }
+};
+
+// roots of f'(s) = 3 c3 s^2 + 2 c2 s + c1 inside (0, L), ascending; the
+// coefficients are re-derived in double precision when the discriminant is
+// ill-conditioned
+__device__ int deriv_roots(const CellF &f, float L, float out[2])
+{
+    float c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const bool i = k & 1, j = (k >> 1) & 1, l = k >> 2;
+        float ax = i ? f.u[0] : 1.f - f.u[0], bx = i ? f.d[0] : -f.d[0];
+        float ay = j ? f.u[1] : 1.f - f.u[1], by = j ? f.d[1] : -f.d[1];
+        float az = l ? f.u[2] : 1.f - f.u[2], bz = l ? f.d[2] : -f.d[2];
+        c1 += f.v[k] * (bx * ay * az + ax * by * az + ax * ay * bz);
+        c2 += f.v[k] * (bx * by * az + bx * ay * bz + ax * by * bz);
+        c3 += f.v[k] * (bx * by * bz);
+    }
+    float a = 3.f * c3, b = 2.f * c2, c = c1;
+    float disc = b * b - 4.f * a * c;
+    float r[2];
+    int n = 0;
+    if (fabsf(disc) < 1e-5f * (b * b + fabsf(4.f * a * c))) {
+        double C1 = 0.0, C2 = 0.0, C3 = 0.0;
+        for (int k = 0; k < 8; ++k) {
+            const bool i = k & 1, j = (k >> 1) & 1, l = k >> 2;
+            double ax = i ? f.u[0] : 1.0 - f.u[0], bx = i ? f.d[0] : -(double)f.d[0];
+            double ay = j ? f.u[1] : 1.0 - f.u[1], by = j ? f.d[1] : -(double)f.d[1];
+            double az = l ? f.u[2] : 1.0 - f.u[2], bz = l ? f.d[2] : -(double)f.d[2];
+            C1 += f.v[k] * (bx * ay * az + ax * by * az + ax * ay * bz);
+            C2 += f.v[k] * (bx * by * az + bx * ay * bz + ax * by * bz);
+            C3 += f.v[k] * (bx * by * bz);
+        }
+        double A = 3.0 * C3, B = 2.0 * C2, CC = C1;
+        if (A == 0.0) {
+            if (B != 0.0) r[n++] = (float)(-CC / B);
+        } else {
+            double D = B * B - 4.0 * A * CC;
+            if (D >= 0.0) {
+                double q = -0.5 * (B + (B >= 0.0 ? sqrt(D) : -sqrt(D)));
+                if (q != 0.0) {
+                    r[n++] = (float)(q / A);
+                    r[n++] = (float)(CC / q);
+                } else {
+                    r[n++] = 0.f;
+                }
+            }
+        }
+    } else if (a == 0.f) {
+        if (b != 0.f) r[n++] = -c / b;
+    } else if (disc > 0.f) {
+        float q = -0.5f * (b + copysignf(sqrtf(disc), b));
+        if (q != 0.f) {
+            r[n++] = q / a;
+            r[n++] = c / q;
+        }
+    }
+    int m = 0;
+    for (int t = 0; t < n; ++t)
+        if (r[t] > 0.f && r[t] < L) out[m++] = r[t];
+    if (m == 2 && out[0] > out[1]) {
+        float t = out[0];
+        out[0] = out[1];
+        out[1] = t;
+    }
+    return m;
+}
+
+// first root of f on [0, L]: monotone pieces split at the roots of f', the
+// first piece that starts on a zero or changes sign, refined by Illinois
+// regula falsi
+__device__ bool first_root(const CellF &f, float L, float &s_hit)
+{
+    float pts[4];
+    float ext[2];
+    int ne = deriv_roots(f, L, ext);
+    int np = 0;
+    pts[np++] = 0.f;
+    for (int i = 0; i < ne; ++i) pts[np++] = ext[i];
+    pts[np++] = L;
+    float fa = f(0.f);
+    if (fa == 0.f) {
+        s_hit = 0.f;
+        return true;
+    }
+    for (int i = 1; i < np; ++i) {
+        float sa = pts[i - 1], sb = pts[i];
+        float fb = f(sb);
+        if (fb == 0.f) {
+            s_hit = sb;
+            return true;
+        }
+        if ((fb < 0.f) != (fa < 0.f)) {
+            float a = sa, b = sb, ya = fa, yb = fb;
+            int side = 0;
+            for (int it = 0; it < 60; ++it) {
+                float s = (a * yb - b * ya) / (yb - ya);
+                if (!(s > a && s < b)) s = 0.5f * (a + b);
+                float ys = f(s);
+                if (ys == 0.f) {
+                    a = b = s;
+                    break;
+                }
+                if ((ys < 0.f) == (ya < 0.f)) {
+                    a = s;
+                    ya = ys;
+                    if (side == -1) yb *= 0.5f;
+                    side = -1;
+                } else {
+                    b = s;
+                    yb = ys;
+                    if (side == 1) ya *= 0.5f;
+                    side = 1;
+                }
+                if (b - a <= 1e-7f * (1.f + b)) break;
+            }
+            s_hit = 0.5f * (a + b);
+            return true;
+        }
+        fa = fb;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t pick8(const uint32_t s[8], int k)
+{
+    uint32_t a = (k & 1) ? s[1] : s[0], b = (k & 1) ? s[3] : s[2];
+    uint32_t c = (k & 1) ? s[5] : s[4], d = (k & 1) ? s[7] : s[6];
+    uint32_t ab = (k & 2) ? b : a, cd = (k & 2) ? d : c;
+    return (k & 4) ? cd : ab;
+}
+
+// Intersect the ray with the isosurface inside block (bx,by,bz).  On a hit,
+// returns the 44 low bits of the resolve key: depth bits, local cell, grey.
+__device__ bool intersect_block(const RT &R, const Ray &r, int bx, int by, int bz, uint64_t &payload)
+{
+    const VolGeom &g = R.P.g;
+    const float iso = R.P.iso;
+    const int bq[3] = {bx, by, bz};
+    float o[3];
+    int ext[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = __fsub_rn(r.e[a], (float)(4 * bq[a]));   // exact
+        ext[a] = min(4, g.dims[a] - 1 - 4 * bq[a]);
+    }
+    // neighbour slots: own, +x, +y, +xy, +z, +xz, +yz, +xyz
+    uint32_t slots[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        int x = bx + (k & 1), y = by + ((k >> 1) & 1), z = bz + (k >> 2);
+        bool need = (!(k & 1) || ext[0] == 4) && (!(k & 2) || ext[1] == 4) && (!(k & 4) || ext[2] == 4);
+        slots[k] = (need && x < g.nb[0] && y < g.nb[1] && z < g.nb[2])
+                       ? R.blk_slot[x + (int64_t)g.nb[0] * (y + (int64_t)g.nb[1] * z)]
+                       : 0u;
+    }
+    // entry into the block: the latest near-plane crossing (exact; ties go to
+    // the higher axis, which is crossed last)
+    int ain = -1;
+    Tq tin{0.f, 1.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (r.sgn[a] == 0) continue;
+        float Pn = r.sgn[a] > 0 ? 0.f : (float)ext[a];
+        Tq t{r.sgn[a] > 0 ? __fsub_rn(Pn, o[a]) : __fsub_rn(o[a], Pn), r.ad[a]};
+        if (ain < 0 || tcmp(t, tin) >= 0) {
+            tin = t;
+            ain = a;
+        }
+    }
+    float q[3];
+    float th = 0.f, tl = 0.f;  // t at the block entry as a float pair
+    if (ain < 0 || tin.n <= 0.f) {
+        q[0] = o[0];
+        q[1] = o[1];
+        q[2] = o[2];
+    } else {
+        const float ad = r.ad[ain];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a == ain) {
+                q[a] = r.sgn[a] > 0 ? 0.f : (float)ext[a];
+                continue;
+            }
+            // q_a = o_a + t_in d_a = (o_a |d_in| + n_in d_a) / |d_in|, numerator
+            // formed with error-free products so that the cancellation is exact
+            float p1, e1, p2, e2, s, es;
+            two_prod(o[a], ad, p1, e1);
+            two_prod(tin.n, r.d[a], p2, e2);
+            two_sum(p1, p2, s, es);
+            float num = __fadd_rn(s, __fadd_rn(es, __fadd_rn(e1, e2)));
+            q[a] = fminf(fmaxf(__fdiv_rn(num, ad), 0.f), (float)ext[a]);
+        }
+        th = __fdiv_rn(tin.n, ad);
+        tl = __fdiv_rn(__fmaf_rn(-th, ad, tin.n), ad);
+    }
+    float inv[3];
+    float sexit = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        inv[a] = r.sgn[a] != 0 ? 1.f / r.ad[a] : 0.f;
+        if (r.sgn[a] == 0) continue;
+        float farp = r.sgn[a] > 0 ? (float)ext[a] : 0.f;
+        sexit = fminf(sexit, (farp - q[a]) * (float)r.sgn[a] * inv[a]);
+    }
+    if (!(sexit > 0.f)) return false;
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float fl = floorf(q[a]);
+        int ci = (int)fl;
+        if (r.sgn[a] < 0 && q[a] == fl) --ci;
+        c[a] = min(max(ci, 0), ext[a] - 1);
+    }
+    float s0 = 0.f;
+    for (int it = 0; it < 16; ++it) {
+        float s1 = sexit;
+        int mask = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (r.sgn[a] == 0) continue;
+            float plane = (float)(r.sgn[a] > 0 ? c[a] + 1 : c[a]);
+            float sa = (plane - q[a]) * (float)r.sgn[a] * inv[a];
+            if (sa < s1) {
+                s1 = sa;
+                mask = 1 << a;
+            } else if (sa == s1) {
+                mask |= 1 << a;
+            }
+        }
+        if (s1 > s0) {
+            CellF f;
+            int below = 0, above = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                int lx = c[0] + (k & 1), ly = c[1] + ((k >> 1) & 1), lz = c[2] + (k >> 2);
+                int nsel = (lx >> 2) | ((ly >> 2) << 1) | ((lz >> 2) << 2);
+                uint32_t slot = pick8(slots, nsel);
+                f.v[k] = __ldg(R.cache + (uint64_t)slot * 64 + (lx & 3) + 4 * (ly & 3) + 16 * (lz & 3));
+                below += f.v[k] < iso;
+                above += f.v[k] > iso;
+            }
+            if (below != 8 && above != 8) {
+                f.iso = iso;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    f.d[a] = r.d[a];
+                    f.u[a] = fmaf(s0, r.d[a], q[a] - (float)c[a]);
+                }
+                float sig;
+                if (first_root(f, s1 - s0, sig)) {
+                    // depth = (t_in + s) |d|, carried in float pairs
+                    float sx, ex, sy, ey, sz, ez, t1, e1, t2, e2;
+                    two_prod(r.d[0], r.d[0], sx, ex);
+                    two_prod(r.d[1], r.d[1], sy, ey);
+                    two_prod(r.d[2], r.d[2], sz, ez);
+                    two_sum(sx, sy, t1, e1);
+                    two_sum(t1, sz, t2, e2);
+                    float lo = ex + ey + ez + e1 + e2;
+                    float rt = sqrtf(t2);
+                    float rr, rre;
+                    two_prod(rt, rt, rr, rre);
+                    float corr = ((t2 - rr) - rre + lo) / (2.f * rt);
+                    float S = tl + (s0 + sig);
+                    float pp, pe;
+                    two_prod(th, rt, pp, pe);
+                    float depth = __fadd_rn(pp, pe + th * corr + S * (rt + corr));
+                    // shade: |n . d| with n the interpolant's gradient
+                    float ux = fmaf(sig, f.d[0], f.u[0]), uy = fmaf(sig, f.d[1], f.u[1]),
+                          uz = fmaf(sig, f.d[2], f.u[2]);
+                    const float *v = f.v;
+                    float gx = lerpf(lerpf(v[1] - v[0], v[3] - v[2], uy), lerpf(v[5] - v[4], v[7] - v[6], uy), uz);
+                    float gy = lerpf(lerpf(v[2] - v[0], v[3] - v[1], ux), lerpf(v[6] - v[4], v[7] - v[5], ux), uz);
+                    float gz = lerpf(lerpf(v[4] - v[0], v[5] - v[1], ux), lerpf(v[6] - v[2], v[7] - v[3], ux), uy);
+                    float gn = sqrtf(gx * gx + gy * gy + gz * gz);
+                    float cosv = gn > 0.f ? fabsf(gx * r.d[0] + gy * r.d[1] + gz * r.d[2]) / (gn * (rt + corr)) : 0.f;
+                    int grey = (int)floorf(255.f * (0.1f + 0.9f * fminf(cosv, 1.f)) + 0.5f);
+                    uint32_t lc = (uint32_t)(c[0] + 4 * c[1] + 16 * c[2]);
+                    payload = ((uint64_t)__float_as_uint(fmaxf(depth, 0.f)) << 20) | ((uint64_t)lc << 14) |
+                              ((uint64_t)grey << 6);
+                    return true;
+                }
+            }
+        }
+        if (!mask) break;
+        bool out = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (mask >> a & 1) {
+                c[a] += r.sgn[a];
+                if (c[a] < 0 || c[a] >= ext[a]) out = true;
+            }
+        if (out) break;
+        s0 = s1;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(128) intersect_kernel(RT R, int64_t cap, const uint32_t *__restrict__ E,
+                                                        const uint32_t *__restrict__ rbid,
+                                                        const uint32_t *__restrict__ live, int kk,
+                                                        unsigned long long *keys, const uint32_t *ctr)
+{
+    if (ctr[C_OVERFLOW]) return;
+    const int64_t n = ctr[C_NENT];
+    const VolGeom &g = R.P.g;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t e = E[idx];
+        uint32_t b = rbid[e];
+        uint32_t i = e / (uint32_t)kk, j = e - i * (uint32_t)kk;
+        uint32_t ray = live[i];
+        Ray r;
+        make_ray(r, R.P.cam.eye, R.P.cam.p00, R.P.cam.du, R.P.cam.dv, (int)(ray % R.P.W), (int)(ray / R.P.W));
+        int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((uint32_t)g.nb[0] * g.nb[1]));
+        uint64_t payload;
+        if (intersect_block(R, r, bx, by, bz, payload)) atomicMin(keys + ray, ((uint64_t)j << 52) | payload);
+    }
+}
+
+// ---------------------------------------------------------------- resolve
+struct ResolveCount {
+    const uint32_t *live;
+    uint32_t nproc;
+    int kk;
+    int pass;
+    int Dx, Dy;
+    VolGeom g;
+    unsigned long long *keys;
+    const uint32_t *rbid;
+    uint64_t *state_in;
+    const uint64_t *state_out;
+    uint8_t *status;
+    float *depth;
+    uint32_t *rgba, *block;
+    uint64_t *cell;
+    int32_t *final_pass;
+    uint32_t *ctr;
+    __device__ bool enabled() const { return !ctr[C_OVERFLOW]; }
+    __device__ uint32_t operator()(int64_t i) const
+    {
+        const uint32_t ray = live[i];
+        uint32_t alive = 1, hit = 0, gone = 0;
+        if (i < (int64_t)nproc) {
+            const unsigned long long key = keys[ray];
+            const uint64_t st = state_out[ray];
+            state_in[ray] = st;
+            if (key != kNoKey) {
+                uint32_t j = (uint32_t)(key >> 52);
+                uint32_t b = rbid[(uint64_t)i * kk + j];
+                uint32_t lc = (uint32_t)((key >> 14) & 63u), grey = (uint32_t)((key >> 6) & 255u);
+                int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]),
+                    bz = (int)(b / ((uint32_t)g.nb[0] * g.nb[1]));
+                uint64_t cx = 4 * bx + (lc & 3), cy = 4 * by + ((lc >> 2) & 3), cz = 4 * bz + (lc >> 4);
+                depth[ray] = __uint_as_float((uint32_t)((key >> 20) & 0xFFFFFFFFull));
+                rgba[ray] = grey | (grey << 8) | (grey << 16) | (255u << 24);
+                block[ray] = b;
+                cell[ray] = cx + (uint64_t)Dx * (cy + (uint64_t)Dy * cz);
+                final_pass[ray] = pass;
+                status[ray] = 1;
+                keys[ray] = kNoKey;
+                alive = 0;
+                hit = 1;
+            } else if ((st >> 48) & kDone) {
+                final_pass[ray] = pass;
+                status[ray] = 2;
+                alive = 0;
+                gone = 1;
+            }
+        }
+        unsigned m = __activemask();
+        uint32_t nh = __popc(__ballot_sync(m, hit)), ng = __popc(__ballot_sync(m, gone));
+        if ((threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) {
+            if (nh) atomicAdd(&ctr[C_HIT], nh);
+            if (ng) atomicAdd(&ctr[C_MISSRAY], ng);
+        }
+        return alive;
+    }
+};
+
+// -------------------------------------------------------------- utilities
+template <class CF, class EF>
+int run_compact(DevBuf &status, DevBuf &ticket, uint32_t *flags, int64_t n_cap, const uint32_t *n_dev,
+                CF cf, EF ef, uint32_t *total, cudaStream_t s, int64_t spin = kDefaultSpinLimit,
+                int64_t withhold = -1)
+{
+    int64_t tiles = std::max<int64_t>(1, scan_tiles(n_cap));
+    if ((size_t)tiles * sizeof(unsigned long long) > status.bytes)
+        return set_error(SPR_ERR_INVALID_ARG, "scan of %lld items exceeds its scratch", (long long)n_cap);
+    SPR_CUDA_TRY(cudaMemsetAsync(status.p, 0, (size_t)tiles * sizeof(unsigned long long), s));
+    SPR_CUDA_TRY(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned int), s));
+    ScanCtl ctl{status.as<unsigned long long>(), ticket.as<unsigned int>(), flags, spin, withhold};
+    compact_kernel<CF, EF><<<(unsigned)tiles, kScanThreads, 0, s>>>(n_cap, n_dev, ctl, cf, ef, total);
+    SPR_CUDA_TRY(cudaGetLastError());
+    return SPR_OK;
+}
+
+}  // namespace spr
+
+using namespace spr;
+
+// ================================================================= renderer
+struct spr_renderer {
+    spr_volume *vol = nullptr;
+    int W = 0, H = 0;
+    int64_t npix = 0;
+    Cam cam{};
+    bool has_cam = false;
+    float iso = 0.5f;
+    int spec_mode = SPR_SPEC_ADAPTIVE, k_fixed = 1, k_max = 64;
+    int64_t n_slots = 0;
+    bool profiling = false;
+
+    bool need_raygen = true;
+    bool cache_dirty = true;
+    int pass = 0;
+    uint32_t n_live = 0;
+    uint32_t n_enter = 0;
+    float ms_raygen = 0.f;
+
+    DevBuf state_in, state_out, status, live[2], keys;
+    DevBuf fb_depth, fb_rgba, fb_block, fb_cell, fb_final;
+    DevBuf rbid, erank, E;
+    int64_t cap_entries = 0;
+    DevBuf vis_bits, act_bits, vis_wpre, act_wpre, ivis, iact, nbrays, obrays;
+    int64_t nwords = 0, cap_act = 0;
+    DevBuf cache, blk_slot, slot_blk, lru[2], touched, miss, victim;
+    int cur_lru = 0, cur_live = 0;
+    DevBuf scan_status, scan_ticket, ctr;
+    uint32_t *h_ctr = nullptr;
+    cudaEvent_t ev[8] = {};
+};
+
+namespace {
+
+void free_all(spr_renderer *r)
+{
+    cudaDeviceSynchronize();
+    DevBuf *bufs[] = {&r->state_in, &r->state_out, &r->status, &r->live[0], &r->live[1], &r->keys,
+                      &r->fb_depth, &r->fb_rgba, &r->fb_block, &r->fb_cell, &r->fb_final, &r->rbid,
+                      &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre, &r->act_wpre,
+                      &r->ivis, &r->iact, &r->nbrays, &r->obrays, &r->cache, &r->blk_slot,
+                      &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
+                      &r->scan_status, &r->scan_ticket, &r->ctr};
+    for (DevBuf *b : bufs) buf_free(*b, nullptr);
+    if (r->h_ctr) cudaFreeHost(r->h_ctr);
+    r->h_ctr = nullptr;
+    for (auto &e : r->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+int64_t entries_needed(const spr_renderer *r)
+{
+    int64_t k = r->spec_mode == SPR_SPEC_FIXED ? r->k_fixed : 1;
+    return std::max<int64_t>(1, r->npix * k);
+}
+
+int ensure_entry_buffers(spr_renderer *r, cudaStream_t s)
+{
+    int64_t cap = entries_needed(r);
+    if (cap > 0x7FFFFFFFll)
+        return set_error(SPR_ERR_INVALID_ARG, "width*height*k = %lld exceeds 2^31 entries", (long long)cap);
+    if (cap <= r->cap_entries) return SPR_OK;
+    SPR_TRY(buf_reserve(r->rbid, sizeof(uint32_t) * cap, s));
+    SPR_TRY(buf_reserve(r->erank, sizeof(uint32_t) * cap, s));
+    SPR_TRY(buf_reserve(r->E, sizeof(uint32_t) * cap, s));
+    SPR_TRY(buf_reserve(r->ivis, sizeof(uint32_t) * cap, s));
+    SPR_TRY(buf_reserve(r->nbrays, sizeof(uint32_t) * (cap + 1), s));
+    SPR_TRY(buf_reserve(r->obrays, sizeof(uint32_t) * (cap + 1), s));
+    int64_t act = std::min<int64_t>(r->vol->g.nblocks, 8 * cap);
+    SPR_TRY(buf_reserve(r->iact, sizeof(uint32_t) * act, s));
+    SPR_TRY(buf_reserve(r->miss, sizeof(uint32_t) * act, s));
+    SPR_TRY(buf_reserve(r->victim, sizeof(uint32_t) * act, s));
+    r->cap_act = act;
+    r->cap_entries = cap;
+    return SPR_OK;
+}
+
+int ensure_scan_scratch(spr_renderer *r, cudaStream_t s)
+{
+    int64_t biggest = std::max({r->npix, r->n_slots, r->nwords, r->cap_entries, r->cap_act, (int64_t)1});
+    return buf_reserve(r->scan_status, sizeof(unsigned long long) * (scan_tiles(biggest) + 1), s);
+}
+
+int reset_cache(spr_renderer *r, cudaStream_t s)
+{
+    const VolGeom &g = r->vol->g;
+    SPR_CUDA_TRY(cudaMemsetAsync(r->blk_slot.p, 0xFF, sizeof(uint32_t) * g.nblocks, s));
+    SPR_CUDA_TRY(cudaMemsetAsync(r->slot_blk.p, 0xFF, sizeof(uint32_t) * r->n_slots, s));
+    SPR_CUDA_TRY(cudaMemsetAsync(r->touched.p, 0, r->n_slots, s));
+    lru_init_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, s>>>(r->lru[0].as<uint32_t>(), r->n_slots);
+    SPR_CUDA_TRY(cudaGetLastError());
+    r->cur_lru = 0;
+    r->cache_dirty = false;
+    return SPR_OK;
+}
+
+Geo make_geo(const spr_renderer *r)
+{
+    Geo P;
+    P.g = r->vol->g;
+    P.fine = r->vol->fine.as<float2>();
+    P.coarse = r->vol->coarse.as<float2>();
+    P.iso = r->iso;
+    P.cam = r->cam;
+    P.W = r->W;
+    return P;
+}
+
+int raygen(spr_renderer *r, cudaStream_t s)
+{
+    uint32_t *ctr = r->ctr.as<uint32_t>();
+    SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
+    RaygenCount cf{make_geo(r),           r->state_in.as<uint64_t>(), r->status.as<uint8_t>(),
+                   r->keys.as<uint64_t>(), r->fb_depth.as<float>(),   r->fb_rgba.as<uint32_t>(),
+                   r->fb_block.as<uint32_t>(), r->fb_cell.as<uint64_t>(), r->fb_final.as<int32_t>()};
+    r->cur_live = 0;
+    IndexEmit ef{r->live[0].as<uint32_t>()};
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, ctr + C_SCANFLAGS, r->npix, nullptr, cf, ef,
+                        ctr + C_NLIVE, s));
+    SPR_CUDA_TRY(cudaMemcpyAsync(r->h_ctr, ctr, sizeof(uint32_t) * C_COUNT, cudaMemcpyDeviceToHost, s));
+    SPR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (r->h_ctr[C_SCANFLAGS]) return set_error(SPR_ERR_DEVICE_TIMEOUT, "ray compaction timed out");
+    r->n_live = r->h_ctr[C_NLIVE];
+    r->n_enter = r->n_live;
+    r->pass = 0;
+    r->need_raygen = false;
+    return SPR_OK;
+}
+
+// one attempt of a pass with kk and nproc; counters land in h_ctr
+int pass_attempt(spr_renderer *r, cudaStream_t s, int kk, uint32_t nproc, float *stage_ms)
+{
+    const VolGeom &g = r->vol->g;
+    uint32_t *ctr = r->ctr.as<uint32_t>();
+    uint32_t *flags = ctr + C_SCANFLAGS;
+    const bool prof = r->profiling;
+    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
+    SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
+    SPR_CUDA_TRY(cudaMemsetAsync(r->vis_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
+    SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
+    const uint32_t *live = r->live[r->cur_live].as<uint32_t>();
+    uint32_t *live_next = r->live[1 - r->cur_live].as<uint32_t>();
+    const int64_t n_ent = (int64_t)nproc * kk;
+
+    // (a) traversal with speculation, marking visible and active blocks
+    traverse_kernel<<<grid_for(nproc, 128, 16), 128, 0, s>>>(
+        make_geo(r), live, nproc, kk, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
+        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>());
+    SPR_CUDA_TRY(cudaGetLastError());
+    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
+
+    // (b) compact the marks; group the entries by visible block
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->nwords, nullptr,
+                        BitsCount{r->vis_bits.as<uint32_t>(), nullptr},
+                        BitsEmit{r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(), r->ivis.as<uint32_t>(),
+                                 r->nbrays.as<uint32_t>()},
+                        ctr + C_NVIS, s));
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->nwords, nullptr,
+                        BitsCount{r->act_bits.as<uint32_t>(), nullptr},
+                        BitsEmit{r->act_bits.as<uint32_t>(), r->act_wpre.as<uint32_t>(), r->iact.as<uint32_t>(),
+                                 nullptr},
+                        ctr + C_NACT, s));
+    overflow_kernel<<<1, 32, 0, s>>>(ctr, r->n_slots);
+    count_entries_kernel<<<grid_for(n_ent, 256, 16), 256, 0, s>>>(
+        n_ent, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
+        r->nbrays.as<uint32_t>(), r->erank.as<uint32_t>(), ctr);
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->cap_entries, ctr + C_NVIS,
+                        ArrayCount{r->nbrays.as<uint32_t>(), ctr + C_OVERFLOW},
+                        ArrayEmit{r->obrays.as<uint32_t>()}, ctr + C_NENT, s));
+    scatter_entries_kernel<<<grid_for(n_ent, 256, 16), 256, 0, s>>>(
+        n_ent, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
+        r->obrays.as<uint32_t>(), r->erank.as<uint32_t>(), r->E.as<uint32_t>(), ctr);
+    SPR_CUDA_TRY(cudaGetLastError());
+    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[2], s));
+
+    // (c) cache: look up, pick least recently used victims, assign
+    uint32_t *lru = r->lru[r->cur_lru].as<uint32_t>(), *lru_next = r->lru[1 - r->cur_lru].as<uint32_t>();
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->cap_act, ctr + C_NACT,
+                        LookupCount{r->iact.as<uint32_t>(), r->blk_slot.as<uint32_t>(), r->touched.as<uint8_t>(),
+                                    ctr + C_OVERFLOW},
+                        SelectEmit{r->iact.as<uint32_t>(), r->miss.as<uint32_t>()}, ctr + C_NMISS, s));
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, nullptr,
+                        VictimCount{lru, r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
+                        VictimEmit{lru, ctr + C_NMISS, r->victim.as<uint32_t>(), lru_next}, ctr + C_NUNTOUCHED,
+                        s));
+    assign_kernel<<<grid_for(r->cap_act, 256, 8), 256, 0, s>>>(r->cap_act, r->miss.as<uint32_t>(),
+                                                              r->victim.as<uint32_t>(), r->blk_slot.as<uint32_t>(),
+                                                              r->slot_blk.as<uint32_t>(), r->touched.as<uint8_t>(), ctr);
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, nullptr,
+                        TouchedCount{r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
+                        TouchedEmit{r->touched.as<uint8_t>(), ctr, lru_next}, nullptr, s));
+    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[3], s));
+
+    // (d) decode the misses into their slots
+    SPR_TRY(launch_decode_list(r->vol->comp.as<uint8_t>(), g.nblocks, g.rate, r->miss.as<uint32_t>(),
+                               r->victim.as<uint32_t>(), r->cap_act, ctr + C_NMISS, ctr + C_OVERFLOW,
+                               r->cache.as<float>(), ctr + C_BAD, s));
+    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[4], s));
+
+    // (e) intersect the entries, block by block
+    RT R{make_geo(r), r->cache.as<float>(), r->blk_slot.as<uint32_t>()};
+    intersect_kernel<<<grid_for(n_ent, 128, 16), 128, 0, s>>>(R, n_ent, r->E.as<uint32_t>(), r->rbid.as<uint32_t>(),
+                                                             live, kk, r->keys.as<unsigned long long>(), ctr);
+    SPR_CUDA_TRY(cudaGetLastError());
+    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[5], s));
+
+    // (f) resolve hits and exits, compact the live rays in order
+    ResolveCount rc{live,
+                    nproc,
+                    kk,
+                    r->pass + 1,
+                    g.dims[0],
+                    g.dims[1],
+                    g,
+                    r->keys.as<unsigned long long>(),
+                    r->rbid.as<uint32_t>(),
+                    r->state_in.as<uint64_t>(),
+                    r->state_out.as<uint64_t>(),
+                    r->status.as<uint8_t>(),
+                    r->fb_depth.as<float>(),
+                    r->fb_rgba.as<uint32_t>(),
+                    r->fb_block.as<uint32_t>(),
+                    r->fb_cell.as<uint64_t>(),
+                    r->fb_final.as<int32_t>(),
+                    ctr};
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_live, nullptr, rc, SelectEmit{live, live_next},
+                        ctr + C_NLIVE, s));
+    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[6], s));
+    SPR_CUDA_TRY(cudaMemcpyAsync(r->h_ctr, ctr, sizeof(uint32_t) * C_COUNT, cudaMemcpyDeviceToHost, s));
+    SPR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (prof) {
+        for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&stage_ms[k], r->ev[k], r->ev[k + 1]);
+    }
+    if (r->h_ctr[C_SCANFLAGS]) return set_error(SPR_ERR_DEVICE_TIMEOUT, "a decoupled look-back wait timed out");
+    if (r->h_ctr[C_BAD]) return set_error(SPR_ERR_DEVICE_ERROR, "a kernel flagged an out-of-range block id");
+    return SPR_OK;
+}
+
+int check_ready(spr_renderer *r)
+{
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    if (!r->has_cam) return set_error(SPR_ERR_INVALID_ARG, "no camera set");
+    if (r->n_slots < 8) return set_error(SPR_ERR_CACHE_TOO_SMALL, "cache budget below 8 slots");
+    return SPR_OK;
+}
+
+int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
+{
+    SPR_TRY(check_ready(r));
+    SPR_TRY(ensure_entry_buffers(r, s));
+    SPR_TRY(ensure_scan_scratch(r, s));
+    if (r->cache_dirty) SPR_TRY(reset_cache(r, s));
+    if (r->need_raygen) {
+        if (r->profiling) SPR_CUDA_TRY(cudaEventRecord(r->ev[7], s));
+        SPR_TRY(raygen(r, s));
+        if (r->profiling) {
+            SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
+            SPR_CUDA_TRY(cudaEventSynchronize(r->ev[0]));
+            cudaEventElapsedTime(&r->ms_raygen, r->ev[7], r->ev[0]);
+        }
+    }
+    spr_pass_stats st;
+    memset(&st, 0, sizeof st);
+    st.n_active = r->n_live;
+    st.pass = r->pass;
+    if (r->n_live == 0) {
+        if (out) *out = st;
+        return SPR_OK;
+    }
+    int k = r->spec_mode == SPR_SPEC_FIXED
+                ? r->k_fixed
+                : (int)std::max<int64_t>(1, std::min<int64_t>(r->k_max, r->npix / r->n_live));
+    int kk = k;
+    uint32_t nproc = r->n_live;
+    int retries = 0;
+    float stage_ms[6] = {0, 0, 0, 0, 0, 0};
+    for (;;) {
+        SPR_TRY(pass_attempt(r, s, kk, nproc, stage_ms));
+        if (!r->h_ctr[C_OVERFLOW]) break;
+        ++retries;
+        if (kk > 1) kk /= 2;
+        else nproc = nproc > 1 ? nproc / 2 : 1;
+    }
+    const uint32_t *h = r->h_ctr;
+    r->cur_lru = 1 - r->cur_lru;
+    r->cur_live = 1 - r->cur_live;
+    r->pass += 1;
+    st.pass = r->pass;
+    st.k = k;
+    st.k_used = kk;
+    st.retries = retries;
+    st.n_processed = nproc;
+    st.n_entries = h[C_NENT];
+    st.n_visible = h[C_NVIS];
+    st.n_requested = h[C_NACT];
+    st.n_decoded = h[C_NMISS];
+    st.n_evicted = h[C_EVICT];
+    st.n_term_hit = h[C_HIT];
+    st.n_term_miss = h[C_MISSRAY];
+    st.n_active_after = h[C_NLIVE];
+    st.utilization = (double)st.n_entries / (double)r->npix;
+    float tot = 0.f;
+    for (int i = 0; i < 6; ++i) {
+        st.ms_stage[i] = stage_ms[i];
+        tot += stage_ms[i];
+    }
+    st.ms = tot;
+    r->n_live = h[C_NLIVE];
+    if (out) *out = st;
+    return SPR_OK;
+}
+
+}  // namespace
+
+extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_renderer **out)
+{
+    clear_error();
+    if (!vol || !out || width < 1 || height < 1) return set_error(SPR_ERR_INVALID_ARG, "bad renderer arguments");
+    *out = nullptr;
+    if ((int64_t)width * height > (int64_t)1 << 28) return set_error(SPR_ERR_INVALID_ARG, "image too large");
+    spr_renderer *r = new (std::nothrow) spr_renderer();
+    if (!r) return set_error(SPR_ERR_OUT_OF_MEMORY, "host allocation failed");
+    r->vol = vol;
+    r->W = width;
+    r->H = height;
+    r->npix = (int64_t)width * height;
+    r->nwords = (vol->g.nblocks + 31) / 32;
+    r->n_slots = (int64_t)(256u << 20) / 256;
+    cudaStream_t s = nullptr;
+    const int64_t np = r->npix;
+    int rc = SPR_OK;
+    if ((rc = buf_alloc(r->state_in, 8 * np, s)) || (rc = buf_alloc(r->state_out, 8 * np, s)) ||
+        (rc = buf_alloc(r->status, np, s)) || (rc = buf_alloc(r->live[0], 4 * np, s)) ||
+        (rc = buf_alloc(r->live[1], 4 * np, s)) || (rc = buf_alloc(r->keys, 8 * np, s)) ||
+        (rc = buf_alloc(r->fb_depth, 4 * np, s)) || (rc = buf_alloc(r->fb_rgba, 4 * np, s)) ||
+        (rc = buf_alloc(r->fb_block, 4 * np, s)) || (rc = buf_alloc(r->fb_cell, 8 * np, s)) ||
+        (rc = buf_alloc(r->fb_final, 4 * np, s)) || (rc = buf_alloc(r->vis_bits, 4 * r->nwords, s)) ||
+        (rc = buf_alloc(r->act_bits, 4 * r->nwords, s)) || (rc = buf_alloc(r->vis_wpre, 4 * r->nwords, s)) ||
+        (rc = buf_alloc(r->act_wpre, 4 * r->nwords, s)) ||
+        (rc = buf_alloc(r->blk_slot, 4 * vol->g.nblocks, s)) || (rc = buf_alloc(r->scan_ticket, 64, s)) ||
+        (rc = buf_alloc(r->ctr, sizeof(uint32_t) * C_COUNT, s))) {
+        free_all(r);
+        delete r;
+        return rc;
+    }
+    if (cudaMallocHost((void **)&r->h_ctr, sizeof(uint32_t) * C_COUNT) != cudaSuccess) {
+        free_all(r);
+        delete r;
+        return set_error(SPR_ERR_OUT_OF_MEMORY, "pinned host allocation failed");
+    }
+    for (auto &e : r->ev) cudaEventCreate(&e);
+    int64_t slots = r->n_slots;
+    r->n_slots = 0;
+    if ((rc = spr_set_cache_budget(r, (size_t)slots * 256))) {
+        free_all(r);
+        delete r;
+        return rc;
+    }
+    *out = r;
+    return SPR_OK;
+}
+
+extern "C" int spr_destroy_renderer(spr_renderer *r)
+{
+    clear_error();
+    if (!r) return SPR_OK;
+    free_all(r);
+    delete r;
+    return SPR_OK;
+}
+
+static bool basis_ok(float x)
+{
+    float a = fabsf(x);
+    return std::isfinite(x) && (a == 0.f || (a >= 0x1p-40f && a <= 0x1p40f));
+}
+
+extern "C" int spr_set_camera(spr_renderer *r, const float eye[3], const float p00[3], const float du[3],
+                              const float dv[3])
+{
+    clear_error();
+    if (!r || !eye || !p00 || !du || !dv) return set_error(SPR_ERR_INVALID_ARG, "NULL camera argument");
+    for (int a = 0; a < 3; ++a) {
+        double e = eye[a];
+        if (!std::isfinite(eye[a]) || std::fabs(e) >= 16384.0 || e * 256.0 != std::floor(e * 256.0))
+            return set_error(SPR_ERR_INVALID_ARG,
+                             "eye[%d] = %.9g must be a multiple of 1/256 below 16384 in magnitude", a, e);
+        if (!basis_ok(p00[a]) || !basis_ok(du[a]) || !basis_ok(dv[a]))
+            return set_error(SPR_ERR_INVALID_ARG, "camera basis component %d outside {0} or [2^-40, 2^40]", a);
+    }
+    for (int a = 0; a < 3; ++a) {
+        r->cam.eye[a] = eye[a];
+        r->cam.p00[a] = p00[a];
+        r->cam.du[a] = du[a];
+        r->cam.dv[a] = dv[a];
+    }
+    r->has_cam = true;
+    r->need_raygen = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_set_isovalue(spr_renderer *r, float iso)
+{
+    clear_error();
+    if (!r || !std::isfinite(iso)) return set_error(SPR_ERR_INVALID_ARG, "bad isovalue");
+    r->iso = iso;
+    r->need_raygen = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_set_cache_budget(spr_renderer *r, size_t bytes)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    int64_t slots = (int64_t)(bytes / 256);
+    if (slots < 8) return set_error(SPR_ERR_CACHE_TOO_SMALL, "cache budget of %zu bytes is below 8 slots", bytes);
+    if (slots > 0x7FFFFFFFll) return set_error(SPR_ERR_INVALID_ARG, "cache budget too large");
+    cudaStream_t s = nullptr;
+    cudaDeviceSynchronize();
+    buf_free(r->cache, s);
+    buf_free(r->slot_blk, s);
+    buf_free(r->lru[0], s);
+    buf_free(r->lru[1], s);
+    buf_free(r->touched, s);
+    r->n_slots = 0;
+    int rc;
+    if ((rc = buf_alloc(r->cache, (size_t)slots * 256, s)) || (rc = buf_alloc(r->slot_blk, 4 * slots, s)) ||
+        (rc = buf_alloc(r->lru[0], 4 * slots, s)) || (rc = buf_alloc(r->lru[1], 4 * slots, s)) ||
+        (rc = buf_alloc(r->touched, (size_t)slots, s)))
+        return rc;
+    r->n_slots = slots;
+    r->cache_dirty = true;
+    r->need_raygen = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_set_speculation(spr_renderer *r, int mode, int k, int k_max)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    if (mode == SPR_SPEC_FIXED) {
+        if (k < 1 || k > SPR_K_LIMIT) return set_error(SPR_ERR_INVALID_ARG, "k = %d outside [1, %d]", k, SPR_K_LIMIT);
+        if (r->npix * (int64_t)k > 0x7FFFFFFFll)
+            return set_error(SPR_ERR_INVALID_ARG, "width*height*k exceeds 2^31 entries");
+        r->k_fixed = k;
+    } else if (mode == SPR_SPEC_ADAPTIVE) {
+        if (k_max < 1 || k_max > SPR_K_LIMIT)
+            return set_error(SPR_ERR_INVALID_ARG, "k_max = %d outside [1, %d]", k_max, SPR_K_LIMIT);
+        r->k_max = k_max;
+    } else {
+        return set_error(SPR_ERR_INVALID_ARG, "unknown speculation mode %d", mode);
+    }
+    r->spec_mode = mode;
+    r->need_raygen = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_reset_cache(spr_renderer *r)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    r->cache_dirty = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_set_profiling(spr_renderer *r, int on)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    r->profiling = on != 0;
+    return SPR_OK;
+}
+
+extern "C" int spr_render_pass(spr_renderer *r, spr_stream stream, spr_pass_stats *out)
+{
+    clear_error();
+    return do_pass(r, as_stream(stream), out);
+}
+
+extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int max_passes,
+                                         spr_render_stats *out, spr_pass_stats *per_pass)
+{
+    clear_error();
+    SPR_TRY(check_ready(r));
+    if (max_passes < 1) return set_error(SPR_ERR_INVALID_ARG, "max_passes must be positive");
+    cudaStream_t s = as_stream(stream);
+    spr_render_stats rs;
+    memset(&rs, 0, sizeof rs);
+    bool fresh = r->need_raygen;
+    int passes = 0;
+    float ms = 0.f;
+    while (passes < max_passes) {
+        spr_pass_stats st;
+        SPR_TRY(do_pass(r, s, &st));
+        if (st.n_active == 0) break;
+        if (per_pass) per_pass[passes] = st;
+        ++passes;
+        rs.blocks_decoded += st.n_decoded;
+        rs.entries += st.n_entries;
+        rs.evictions += st.n_evicted;
+        rs.n_hits += st.n_term_hit;
+        ms += st.ms;
+        if (r->n_live == 0) break;
+    }
+    rs.passes = passes;
+    rs.n_rays = r->n_enter;
+    rs.converged = r->n_live == 0;
+    rs.bytes_decoded = rs.blocks_decoded * 256;
+    rs.ms_raygen = fresh ? r->ms_raygen : 0.f;
+    rs.ms_total = ms + rs.ms_raygen;
+    if (out) *out = rs;
+    if (!rs.converged) return set_error(SPR_ERR_NOT_CONVERGED, "%d passes left rays live", passes);
+    return SPR_OK;
+}
+
+extern "C" int spr_get_framebuffer(spr_renderer *r, spr_framebuffer *out)
+{
+    clear_error();
+    if (!r || !out) return set_error(SPR_ERR_INVALID_ARG, "NULL argument");
+    out->width = r->W;
+    out->height = r->H;
+    out->depth = r->fb_depth.as<float>();
+    out->rgba = r->fb_rgba.as<uint32_t>();
+    out->block = r->fb_block.as<uint32_t>();
+    out->cell = r->fb_cell.as<uint64_t>();
+    out->final_pass = r->fb_final.as<int32_t>();
+    out->status = r->status.as<uint8_t>();
+    return SPR_OK;
+}
+
+extern "C" int spr_read_framebuffer(spr_renderer *r, spr_stream stream, float *depth, uint32_t *rgba,
+                                    uint32_t *block, uint64_t *cell, int32_t *final_pass, uint8_t *status)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    cudaStream_t s = as_stream(stream);
+    const size_t n = (size_t)r->npix;
+    if (depth) SPR_CUDA_TRY(cudaMemcpyAsync(depth, r->fb_depth.p, 4 * n, cudaMemcpyDeviceToHost, s));
+    if (rgba) SPR_CUDA_TRY(cudaMemcpyAsync(rgba, r->fb_rgba.p, 4 * n, cudaMemcpyDeviceToHost, s));
+    if (block) SPR_CUDA_TRY(cudaMemcpyAsync(block, r->fb_block.p, 4 * n, cudaMemcpyDeviceToHost, s));
+    if (cell) SPR_CUDA_TRY(cudaMemcpyAsync(cell, r->fb_cell.p, 8 * n, cudaMemcpyDeviceToHost, s));
+    if (final_pass) SPR_CUDA_TRY(cudaMemcpyAsync(final_pass, r->fb_final.p, 4 * n, cudaMemcpyDeviceToHost, s));
+    if (status) SPR_CUDA_TRY(cudaMemcpyAsync(status, r->status.p, n, cudaMemcpyDeviceToHost, s));
+    SPR_CUDA_TRY(cudaStreamSynchronize(s));
+    return SPR_OK;
+}
+
+// ------------------------------------------------------------------- scan
+namespace {
+int scan_impl(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total, int64_t withhold, int64_t spin,
+              cudaStream_t s)
+{
+    if (n < 0 || (n > 0 && (!in || !out))) return set_error(SPR_ERR_INVALID_ARG, "bad scan arguments");
+    if (n > 0xFFFFFFFFll) return set_error(SPR_ERR_INVALID_ARG, "scan longer than 2^32");
+    DevBuf status, ticket, flags;
+    int rc = SPR_OK;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(s);
+        buf_free(status, s);
+        buf_free(ticket, s);
+        buf_free(flags, s);
+    };
+    if ((rc = buf_alloc(status, sizeof(unsigned long long) * (scan_tiles(n) + 1), s)) ||
+        (rc = buf_alloc(ticket, 64, s)) || (rc = buf_alloc(flags, 64, s))) {
+        cleanup();
+        return rc;
+    }
+    if (cudaMemsetAsync(flags.p, 0, 64, s) != cudaSuccess) {
+        cleanup();
+        return set_error(SPR_ERR_CUDA, "memset failed");
+    }
+    rc = run_compact(status, ticket, flags.as<uint32_t>(), n, nullptr, ArrayCount{in, nullptr}, ArrayEmit{out},
+                     total, s, spin, withhold);
+    uint32_t f = 0;
+    if (rc == SPR_OK) {
+        cudaError_t e = cudaMemcpyAsync(&f, flags.p, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = set_error(SPR_ERR_CUDA, "scan: %s", cudaGetErrorString(e));
+    }
+    cleanup();
+    if (rc == SPR_OK && f) rc = set_error(SPR_ERR_DEVICE_TIMEOUT, "a look-back wait gave up after its poll limit");
+    return rc;
+}
+}  // namespace
+
+extern "C" int spr_exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
+                                      spr_stream stream)
+{
+    clear_error();
+    return scan_impl(in, out, n, total, -1, kDefaultSpinLimit, as_stream(stream));
+}
+
+extern "C" int spr_debug_scan_withhold(const uint32_t *in, uint32_t *out, int64_t n, int64_t withhold_tile,
+                                       int64_t spin_limit, spr_stream stream)
+{
+    clear_error();
+    if (spin_limit < 1) return set_error(SPR_ERR_INVALID_ARG, "spin_limit must be positive");
+    return scan_impl(in, out, n, nullptr, withhold_tile, spin_limit, as_stream(stream));
+}

@@ -1,0 +1,147 @@
+// scan.cuh -- single-pass stream compaction / prefix sum with decoupled
+// look-back (Merrill and Garland), the primitive behind the compactions and
+// prefix sums of Sec. 3.6 and 4.2.
+//
+// One kernel computes, for elements i in [0, n), a count c(i) and calls
+// emit(i, prefix, c(i)) with the exclusive prefix sum of the counts.  Tiles
+// take their index from an atomic ticket, so every tile a thread waits on is
+// already running or done.  Each tile publishes its aggregate, then its
+// inclusive prefix, in one 64-bit word: bits 63..62 = status (1 aggregate,
+// 2 inclusive), bits 31..0 = value.  Waits are bounded: after `spin_limit`
+// polls (with nanosleep back-off) a tile sets the timeout flag and gives up,
+// and every other waiting tile stops as soon as it sees the flag.
+#pragma once
+
+#include <stdint.h>
+
+namespace spr {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int64_t kDefaultSpinLimit = int64_t(1) << 22;
+
+struct ScanCtl {
+    unsigned long long *status;  // one word per tile, zeroed before launch
+    unsigned int *ticket;        // zeroed before launch
+    unsigned int *flags;         // bit 0: a wait timed out
+    int64_t spin_limit;
+    int64_t withhold;            // test hook: this tile never publishes (-1: none)
+};
+
+constexpr unsigned long long kAgg = 1ull << 62;
+constexpr unsigned long long kInc = 2ull << 62;
+
+__device__ __forceinline__ void publish(unsigned long long *w, unsigned long long v)
+{
+    atomicExch(w, v);
+}
+
+__device__ __forceinline__ unsigned long long poll(const unsigned long long *w)
+{
+    return *(const volatile unsigned long long *)w;
+}
+
+// n is read from *n_dev when n_dev is non-null (counts produced on the
+// device), else n_host is used.  total (optional) receives the sum.
+template <class CountF, class EmitF>
+__global__ void __launch_bounds__(kScanThreads)
+    compact_kernel(int64_t n_host, const uint32_t *n_dev, ScanCtl ctl, CountF count, EmitF emit,
+                   uint32_t *total)
+{
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_prefix;
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(ctl.ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    if (!count.enabled()) return;
+    const int64_t base = tile * kScanTile;
+    if (base >= n) {  // nobody waits on tiles past the end
+        if (tile == 0 && tid == 0 && total) *total = 0u;
+        return;
+    }
+
+    uint32_t c[kScanItems];
+    uint32_t local = 0;
+    const int64_t first = base + (int64_t)tid * kScanItems;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = first + k;
+        c[k] = i < n ? count(i) : 0u;
+        local += c[k];
+    }
+    // block-wide exclusive scan of the per-thread sums
+    uint32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < kScanThreads / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
+    }
+    __syncthreads();
+    uint32_t excl = s_warp[wid] + incl - local;
+    // the tile total is the last thread's inclusive sum
+    __shared__ uint32_t s_total;
+    if (tid == kScanThreads - 1) s_total = excl + local;
+    __syncthreads();
+    const uint32_t total_tile = s_total;
+
+    if (tid == 0) {
+        uint32_t prefix = 0;
+        const bool publish_ok = tile != ctl.withhold;
+        if (tile == 0) {
+            if (publish_ok) publish(&ctl.status[0], kInc | total_tile);
+        } else {
+            if (publish_ok) publish(&ctl.status[tile], kAgg | total_tile);
+            int64_t pred = tile - 1;
+            int64_t polls = 0;
+            unsigned ns = 32;
+            while (pred >= 0) {
+                unsigned long long w = poll(&ctl.status[pred]);
+                unsigned long long st = w & (3ull << 62);
+                if (st == 0) {
+                    if (++polls > ctl.spin_limit) {
+                        atomicOr(ctl.flags, 1u);
+                        break;
+                    }
+                    if ((polls & 63) == 0 && (*(volatile unsigned int *)ctl.flags & 1u)) break;
+                    __nanosleep(ns);
+                    if (ns < 1024) ns <<= 1;
+                    continue;
+                }
+                prefix += (uint32_t)(w & 0xFFFFFFFFull);
+                if (st == kInc) break;
+                --pred;
+            }
+            if (publish_ok) publish(&ctl.status[tile], kInc | (uint32_t)(prefix + total_tile));
+        }
+        s_prefix = prefix;
+        if (total && base + kScanTile >= n) *total = prefix + total_tile;
+    }
+    __syncthreads();
+    uint32_t run = s_prefix + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = first + k;
+        if (i < n) emit(i, run, c[k]);
+        run += c[k];
+    }
+}
+
+inline int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+}  // namespace spr
