@@ -245,9 +245,13 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
                                                        const uint64_t *__restrict__ state_in,
                                                        uint64_t *__restrict__ state_out,
                                                        uint32_t *__restrict__ rbid,
-                                                       uint32_t *vis_bits, uint32_t *act_bits)
+                                                       uint32_t *vis_bits, uint32_t *act_bits,
+                                                       uint32_t *ctr)
 {
     const VolGeom &g = P.g;
+    // every step moves at least one block index monotonically, so a walk
+    // never takes more steps than this; exceeding it is an internal error
+    const int max_steps = 2 * (g.tb[0] + g.tb[1] + g.tb[2]) + 8;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nproc;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t ray = live[i];
@@ -261,7 +265,13 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
         bool alive = !(flags & kDone);
         if (alive && (flags & kStep)) alive = block_step(r, g, b);
         flags &= ~kStep;
+        int steps = 0;
         while (alive) {
+            if (++steps > max_steps) {
+                atomicOr(&ctr[C_BAD], 2u);
+                alive = false;
+                break;
+            }
             int64_t c = (b[0] >> 2) + (int64_t)g.nc[0] * ((b[1] >> 2) + (int64_t)g.nc[1] * (b[2] >> 2));
             if (!holds(P.coarse[c], P.iso)) {
                 alive = coarse_skip(r, g, b);
@@ -1030,7 +1040,7 @@ int pass_attempt(spr_renderer *r, cudaStream_t s, int kk, uint32_t nproc, float 
     // (a) traversal with speculation, marking visible and active blocks
     traverse_kernel<<<grid_for(nproc, 128, 16), 128, 0, s>>>(
         make_geo(r), live, nproc, kk, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
-        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>());
+        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr);
     SPR_CUDA_TRY(cudaGetLastError());
     if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
 
@@ -1117,7 +1127,8 @@ int pass_attempt(spr_renderer *r, cudaStream_t s, int kk, uint32_t nproc, float 
         for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&stage_ms[k], r->ev[k], r->ev[k + 1]);
     }
     if (r->h_ctr[C_SCANFLAGS]) return set_error(SPR_ERR_DEVICE_TIMEOUT, "a decoupled look-back wait timed out");
-    if (r->h_ctr[C_BAD]) return set_error(SPR_ERR_DEVICE_ERROR, "a kernel flagged an out-of-range block id");
+    if (r->h_ctr[C_BAD] & 1u) return set_error(SPR_ERR_DEVICE_ERROR, "a kernel flagged an out-of-range block id");
+    if (r->h_ctr[C_BAD] & 2u) return set_error(SPR_ERR_DEVICE_ERROR, "a traversal exceeded its step bound");
     return SPR_OK;
 }
 
