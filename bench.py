@@ -1,0 +1,464 @@
+#!/usr/bin/env python
+"""Benchmark: time to final image of the speculative progressive isosurface
+raycaster (arXiv 2309.10212) on one GB300, with the CPU oracle beside it.
+
+A step is one whole render -- ray generation and every pass (traverse with
+speculation, entry grouping, LRU cache, decode, intersect, resolve) until no
+ray is live -- of one camera pose from a cold block cache, on a volume that is
+already resident in device memory.  Poses cycle through the workload's orbit.
+
+Workloads (synthetic stand-ins for the paper's data sets, see synth/):
+  medium (default)  512^3 u8 Gaussian blobs + 10% noise, 2 bits/value, iso 0.3,
+                    1280x720, 16-pose orbit, cache 10% of the decoded size,
+                    adaptive speculation capped at 16
+  paper             2048x2048x1920 u8 mixing layer, 2 bits/value, iso 0.5,
+                    1280x720, one pose, 4 GB cache, adaptive speculation (cap 64)
+  small             64^3 float value noise, 8 bits/value, iso 0.5, 256x256,
+                    cache 25% of the blocks, fixed k = 4
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms to final image & per pass at 1280×720; decoded GB/s vs HBM peak; blocks decoded"
+
+WORKLOADS = {
+    "medium": dict(dims=(512, 512, 512), rate=2, iso=0.3, W=1280, H=720, poses=16,
+                   cache_bytes=int(0.10 * 512 ** 3 * 4), spec="adaptive", k=16,
+                   name="medium: 512^3 u8 Gaussian blobs + 10% noise, 2 bits/value, iso 0.3, "
+                        "1280x720, 16-pose orbit, cache 10% of decoded size, adaptive k<=16"),
+    "paper": dict(dims=(2048, 2048, 1920), rate=2, iso=0.5, W=1280, H=720, poses=1,
+                  cache_bytes=4 << 30, spec="adaptive", k=64,
+                  name="paper-scale: 2048x2048x1920 u8 mixing layer, 2 bits/value, iso 0.5, "
+                       "1280x720, cache 4 GB, adaptive k<=64"),
+    "small": dict(dims=(64, 64, 64), rate=8, iso=0.5, W=256, H=256, poses=1,
+                  cache_bytes=1024 * 256, spec="fixed", k=4,
+                  name="small: 64^3 value noise, 8 bits/value, iso 0.5, 256x256, "
+                       "cache 25% of blocks, k=4"),
+}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=d["hbm_gbs"], sm_max_mhz=d.get("sm_max_mhz", 2070.0), src="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, src="fallback")
+
+
+def pose(wl, i):
+    import synth
+    if wl["dims"] == (64, 64, 64):
+        return synth.cameras.small_pose(wl["dims"], wl["W"], wl["H"])
+    if wl["poses"] == 1 and wl["dims"][0] == 2048:
+        return synth.cameras.paper_pose(wl["dims"], wl["W"], wl["H"])
+    return synth.cameras.medium_pose(i % wl["poses"], wl["dims"], wl["W"], wl["H"])
+
+
+def make_volume_u8_or_f32(wl, device):
+    """The raw (uncompressed) volume as a torch tensor on `device`."""
+    import synth
+    dims = wl["dims"]
+    if dims == (64, 64, 64):
+        return synth.volumes.value_noise(dims, seed=1, device=device)
+    if dims[0] == 2048:
+        return None  # generated slab by slab
+    return synth.volumes.gaussian_blobs(dims, seed=2, device=device)
+
+
+def compressed_on_device(wl, spr, torch):
+    """Generate the workload's volume on the GPU and compress it with the
+    library's encoder; returns the block stream (device)."""
+    import synth
+    dims, rate = wl["dims"], wl["rate"]
+    if dims[0] == 2048:
+        Dx, Dy, Dz = dims
+        nb = ((Dx + 3) // 4, (Dy + 3) // 4, (Dz + 3) // 4)
+        out = torch.empty(nb[0] * nb[1] * nb[2] * 8 * rate, dtype=torch.uint8, device="cuda")
+        params = synth.volumes.mixing_layer_params(3, scale=Dz / 1920.0)
+        slab = 64
+        per_slab = nb[0] * nb[1] * (slab // 4) * 8 * rate
+        for i, z0 in enumerate(range(0, Dz, slab)):
+            z1 = min(Dz, z0 + slab)
+            u8 = synth.volumes.mixing_layer_slab(dims, z0, z1, params, z_mid=Dz / 2.0,
+                                                 device="cuda")
+            n = nb[0] * nb[1] * ((z1 - z0 + 3) // 4) * 8 * rate
+            spr.spr_encode_u8(u8, rate, out=out[i * per_slab:i * per_slab + n])
+        return out
+    vol = make_volume_u8_or_f32(wl, "cuda")
+    if vol.dtype == torch.uint8:
+        return spr.spr_encode_u8(vol, rate)
+    return spr.spr_encode_f32(vol, rate)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                          "--query-gpu=" + self.QUERY, "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx = max(mx, float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                  "sw_power_cap"], parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(wl, pose_index, rows_every, nthreads, comp_host=None):
+    """Time the CPU oracle on every `rows_every`-th pixel row of one pose:
+    decode the whole volume once, then ray cast the sample.  Returns
+    (extrapolated ms per image, details)."""
+    import numpy as np
+
+    import oracle
+    dims, rate = wl["dims"], wl["rate"]
+    if comp_host is None:
+        import synth
+        dev = "cpu"
+        vol = make_volume_u8_or_f32(wl, dev)
+        vol = vol.numpy() if hasattr(vol, "numpy") else vol
+        comp_host = oracle.encode_volume(vol, dims, rate)
+    t0 = time.perf_counter()
+    dec = oracle.decode_volume(comp_host, dims, rate)
+    _, fine, _ = oracle.ranges(dec, dims)
+    t_dec = time.perf_counter() - t0
+    ov = oracle.Volume(dec, dims, fine)
+    W, H = wl["W"], wl["H"]
+    rows = np.arange(0, H, rows_every)
+    pixels = (rows[:, None] * W + np.arange(W)[None, :]).reshape(-1)
+    cam = pose(wl, pose_index)
+    t0 = time.perf_counter()
+    oracle.render(ov, cam, W, H, wl["iso"], pixels=pixels, nthreads=nthreads)
+    t_ray = time.perf_counter() - t0
+    ms = 1e3 * (t_dec + t_ray * (W * H) / pixels.size)
+    return ms, dict(decode_s=t_dec, raycast_s=t_ray, pixels=int(pixels.size))
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    nthreads = os.cpu_count() or 1
+    dims = wl["dims"]
+    if dims[0] == 2048:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the CPU oracle holds the decoded volume in host memory; the "
+                          "2048x2048x1920 volume (30 GB of floats) is measured on the medium "
+                          "workload instead"}))
+        return 0
+    vol = make_volume_u8_or_f32(wl, "cpu")
+    vol = vol.numpy() if hasattr(vol, "numpy") else vol
+    comp = oracle.encode_volume(vol, dims, wl["rate"])
+    rows_every = 48 if wl["W"] >= 1280 else 8
+    times = []
+    for step in range(args.warmup + args.steps):
+        ms, det = oracle_sample(wl, step, rows_every, nthreads, comp)
+        if step >= args.warmup:
+            times.append(ms)
+    value = statistics.mean(times)
+    sample = ("oracle (C, FP64, %d threads): full decode + ray casting of every %dth pixel row "
+              "(%d pixels), extrapolated to the whole %dx%d image" %
+              (nthreads, rows_every, det["pixels"], wl["W"], wl["H"]))
+    print(json.dumps({
+        "metric": METRIC, "value": round(value, 3), "unit": "ms", "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(value, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"]},
+        "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": nthreads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="spr", choices=["spr", "reference"])
+    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--dump", default="", help="write per-pass details to this JSON file")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2309_10212_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    import paper_2309_10212_gb300 as spr
+    from paper_2309_10212_gb300 import _lib
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        comp = compressed_on_device(wl, spr, torch)
+        vol = spr.spr_create_volume(wl["dims"], wl["rate"], comp, stream=stream)
+        r = spr.spr_create_renderer(vol, wl["W"], wl["H"])
+        spr.spr_set_cache_budget(r, wl["cache_bytes"])
+        if wl["spec"] == "fixed":
+            spr.spr_set_speculation(r, spr.SPR_SPEC_FIXED, k=wl["k"])
+        else:
+            spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=wl["k"])
+        spr.spr_set_isovalue(r, wl["iso"])
+        spr.spr_set_profiling(r, True)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+
+        def step(i):
+            spr.spr_reset_cache(r)
+            spr.spr_set_camera(r, pose(wl, rank * 1000 + i))
+            return spr.spr_render_to_convergence(r, 100000, stream=stream)
+
+        for i in range(args.warmup):
+            flush.fill_(i & 255)
+            step(i)
+        torch.cuda.synchronize()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        stats = []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.fill_((i + 7) & 255)          # L2 flush, outside the timed region
+                ev0[i].record(stream)
+                rs, passes = step(args.warmup + i)
+                ev1[i].record(stream)
+                stats.append((rs, passes))
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        ms_image = statistics.mean(step_ms)
+        if dist:
+            t = torch.tensor([ms_image], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_image = float(t.item())
+
+        # per-stage device times (CUDA events inside the library, same stream)
+        stage_names = ["traverse", "group", "cache", "decode", "intersect", "resolve"]
+        stage = {n: 0.0 for n in stage_names}
+        n_pass = 0
+        blocks = 0
+        launches = 0
+        decode_launch_ms, decode_bytes = [], []
+        for rs, passes in stats:
+            n_pass += rs["passes"]
+            blocks += rs["blocks_decoded"]
+            launches += rs["kernel_launches"]
+            for p in passes:
+                for k, n in enumerate(stage_names):
+                    stage[n] += p["ms_stage"][k]
+                if p["n_decoded"]:
+                    decode_launch_ms.append(p["ms_stage"][3])
+                    decode_bytes.append(p["n_decoded"] * (8 * wl["rate"] + 256))
+        total_stage = sum(stage.values()) or 1.0
+        pk = peaks()
+        # the kernel-level stages with one kernel each: traverse, decode, intersect
+        one_kernel = {"traverse": "traverse_kernel", "decode": "decode_list_kernel",
+                      "intersect": "intersect_kernel"}
+        dom = max(one_kernel, key=lambda n: stage[n])
+        dec_ms = sum(decode_launch_ms)
+        dec_gbs = (sum(decode_bytes) / 1e9) / (dec_ms / 1e3) if dec_ms > 0 else 0.0
+        roofline = None
+        if dom == "decode" and dec_ms > 0:
+            roofline = {"kernel": one_kernel[dom], "bound": "hbm",
+                        "achieved": round(dec_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": round(dec_gbs / pk["hbm_gbs"], 4), "traffic": None,
+                        "peak_source": pk["src"]}
+        else:
+            # traversal and intersection are latency/ALU bound; report their
+            # algorithmic HBM bytes against the copy peak
+            per_pass = [p for _, ps in stats for p in ps]
+            if dom == "traverse":
+                bytes_ = sum(p["n_processed"] * (4 + 8 + 8) + p["n_processed"] * p["k_used"] * 4
+                             for p in per_pass)
+            else:
+                bytes_ = sum(p["n_entries"] * (4 + 4 + 4 + 8 + 32 + 256) for p in per_pass)
+            ms_ = stage[dom]
+            ach = (bytes_ / 1e9) / (ms_ / 1e3) if ms_ > 0 else 0.0
+            roofline = {"kernel": one_kernel[dom], "bound": "hbm", "achieved": round(ach, 1),
+                        "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None,
+                        "peak_source": pk["src"]}
+        roofline["share"] = round(stage[dom] / total_stage, 3)
+
+        # end to end through the C ABI with host buffers: camera in, image out
+        n = wl["W"] * wl["H"]
+        host = {k: torch.empty(n * s, dtype=torch.uint8, pin_memory=True)
+                for k, s in (("depth", 4), ("rgba", 4), ("block", 4), ("cell", 8),
+                             ("final", 4), ("status", 1))}
+        L = _lib.load()
+        e2e = []
+        h2d = 4 * 12 + 4
+        d2h = sum(t.numel() for t in host.values())
+        pass_reads = []
+        spr.spr_set_profiling(r, False)
+        for i in range(args.e2e_steps):
+            flush.fill_(i & 255)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            spr.spr_reset_cache(r)
+            cam = pose(wl, i)
+            spr.spr_set_camera(r, cam)
+            spr.spr_set_isovalue(r, wl["iso"])
+            rs, _ = spr.spr_render_to_convergence(r, 100000, stream=stream)
+            _lib.check(L.spr_read_framebuffer(r.handle, ctypes.c_void_p(stream.cuda_stream),
+                                              *[ctypes.c_void_p(host[k].data_ptr()) for k in
+                                                ("depth", "rgba", "block", "cell", "final",
+                                                 "status")]))
+            e2e.append(1e3 * (time.perf_counter() - t0))
+            pass_reads.append(rs["passes"] + 1)
+        e2e_ms = statistics.mean(e2e)
+        d2h_total = d2h + 64 * statistics.mean(pass_reads)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and wl["dims"][0] != 2048:
+        try:
+            import oracle
+            oracle.build()
+            comp_host = comp.cpu().numpy()
+            nthreads = os.cpu_count() or 1
+            ms_cpu, det = oracle_sample(wl, 0, 24 if wl["W"] >= 1280 else 4, nthreads, comp_host)
+            cpu = {"value": round(ms_cpu, 1), "unit": "ms", "cores": nthreads, "kind": "oracle",
+                   "sample": "C oracle (FP64, OpenMP %d threads): decode of all blocks (%.1f s) + "
+                             "ray casting of %d pixels (%.1f s) of pose 0, extrapolated to the "
+                             "full image" % (nthreads, det["decode_s"], det["pixels"],
+                                             det["raycast_s"])}
+        except Exception as exc:  # noqa: BLE001
+            cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": "failed: %s" % exc}
+    elif rank == 0:
+        cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "not run: the oracle holds the 30 GB decoded volume in host memory"}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC,
+            "value": round(ms_image, 4),
+            "unit": "ms",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_image, 4),
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "dims": list(wl["dims"]), "rate": wl["rate"],
+                       "image": [wl["W"], wl["H"]], "iso": wl["iso"],
+                       "cache_bytes": wl["cache_bytes"],
+                       "speculation": "%s k%s%d" % (wl["spec"], "<=" if wl["spec"] == "adaptive"
+                                                    else "=", wl["k"]),
+                       "cold_cache_per_step": True,
+                       "l2": "256 MB buffer written between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "ms_per_pass": round(ms_image * len(stats) / max(1, n_pass), 4),
+            "passes_per_image": round(n_pass / len(stats), 2),
+            "blocks_decoded_per_image": round(blocks / len(stats), 1),
+            "decoded_gbs": round(dec_gbs, 1),
+            "images_per_s": round(1e3 / ms_image * world, 2),
+            "stage_ms_per_image": {k: round(v / len(stats), 4) for k, v in stage.items()},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": int(d2h_total)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+        if args.dump:
+            json.dump({"line": line, "steps": [{"render": rs, "passes": ps} for rs, ps in stats]},
+                      open(args.dump, "w"), indent=1)
+    r.close()
+    vol.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -176,6 +176,7 @@ typedef struct {
     int64_t n_hits;
     float   ms_total;       /* device time from ray generation to convergence   */
     float   ms_raygen;
+    int64_t kernel_launches;/* kernels the library launched for this render     */
 } spr_render_stats;
 
 /* Framebuffer (device, owned by the renderer; valid until the next set_* or

@@ -61,7 +61,8 @@ class RenderStats(ctypes.Structure):
                 ("blocks_decoded", ctypes.c_int64), ("bytes_decoded", ctypes.c_int64),
                 ("entries", ctypes.c_int64), ("evictions", ctypes.c_int64),
                 ("n_rays", ctypes.c_int64), ("n_hits", ctypes.c_int64),
-                ("ms_total", ctypes.c_float), ("ms_raygen", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("ms_raygen", ctypes.c_float),
+                ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

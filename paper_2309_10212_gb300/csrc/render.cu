@@ -873,6 +873,12 @@ struct ResolveCount {
 };
 
 // -------------------------------------------------------------- utilities
+thread_local int64_t *g_launch_counter = nullptr;
+inline void count_launch(int n = 1)
+{
+    if (g_launch_counter) *g_launch_counter += n;
+}
+
 template <class CF, class EF>
 int run_compact(DevBuf &status, DevBuf &ticket, uint32_t *flags, int64_t n_cap, const uint32_t *n_dev,
                 CF cf, EF ef, uint32_t *total, cudaStream_t s, int64_t spin = kDefaultSpinLimit,
@@ -885,6 +891,7 @@ int run_compact(DevBuf &status, DevBuf &ticket, uint32_t *flags, int64_t n_cap, 
     SPR_CUDA_TRY(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned int), s));
     ScanCtl ctl{status.as<unsigned long long>(), ticket.as<unsigned int>(), flags, spin, withhold};
     compact_kernel<CF, EF><<<(unsigned)tiles, kScanThreads, 0, s>>>(n_cap, n_dev, ctl, cf, ef, total);
+    count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     return SPR_OK;
 }
@@ -920,6 +927,7 @@ struct spr_renderer {
     int64_t nwords = 0, cap_act = 0;
     DevBuf cache, blk_slot, slot_blk, lru[2], touched, miss, victim;
     int cur_lru = 0, cur_live = 0;
+    int64_t launches = 0;   // kernels launched since the last render started
     DevBuf scan_status, scan_ticket, ctr;
     uint32_t *h_ctr = nullptr;
     cudaEvent_t ev[8] = {};
@@ -983,6 +991,7 @@ int reset_cache(spr_renderer *r, cudaStream_t s)
     SPR_CUDA_TRY(cudaMemsetAsync(r->slot_blk.p, 0xFF, sizeof(uint32_t) * r->n_slots, s));
     SPR_CUDA_TRY(cudaMemsetAsync(r->touched.p, 0, r->n_slots, s));
     lru_init_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, s>>>(r->lru[0].as<uint32_t>(), r->n_slots);
+    count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     r->cur_lru = 0;
     r->cache_dirty = false;
@@ -1041,6 +1050,7 @@ int pass_attempt(spr_renderer *r, cudaStream_t s, int kk, uint32_t nproc, float 
     traverse_kernel<<<grid_for(nproc, 128, 16), 128, 0, s>>>(
         make_geo(r), live, nproc, kk, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
         r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr);
+    count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
 
@@ -1056,6 +1066,7 @@ int pass_attempt(spr_renderer *r, cudaStream_t s, int kk, uint32_t nproc, float 
                                  nullptr},
                         ctr + C_NACT, s));
     overflow_kernel<<<1, 32, 0, s>>>(ctr, r->n_slots);
+    count_launch(3);  // overflow check, entry count, entry scatter
     count_entries_kernel<<<grid_for(n_ent, 256, 16), 256, 0, s>>>(
         n_ent, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
         r->nbrays.as<uint32_t>(), r->erank.as<uint32_t>(), ctr);
@@ -1081,6 +1092,7 @@ int pass_attempt(spr_renderer *r, cudaStream_t s, int kk, uint32_t nproc, float 
     assign_kernel<<<grid_for(r->cap_act, 256, 8), 256, 0, s>>>(r->cap_act, r->miss.as<uint32_t>(),
                                                               r->victim.as<uint32_t>(), r->blk_slot.as<uint32_t>(),
                                                               r->slot_blk.as<uint32_t>(), r->touched.as<uint8_t>(), ctr);
+    count_launch();
     SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, nullptr,
                         TouchedCount{r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
                         TouchedEmit{r->touched.as<uint8_t>(), ctr, lru_next}, nullptr, s));
@@ -1090,12 +1102,14 @@ int pass_attempt(spr_renderer *r, cudaStream_t s, int kk, uint32_t nproc, float 
     SPR_TRY(launch_decode_list(r->vol->comp.as<uint8_t>(), g.nblocks, g.rate, r->miss.as<uint32_t>(),
                                r->victim.as<uint32_t>(), r->cap_act, ctr + C_NMISS, ctr + C_OVERFLOW,
                                r->cache.as<float>(), ctr + C_BAD, s));
+    count_launch();
     if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[4], s));
 
     // (e) intersect the entries, block by block
     RT R{make_geo(r), r->cache.as<float>(), r->blk_slot.as<uint32_t>()};
     intersect_kernel<<<grid_for(n_ent, 128, 16), 128, 0, s>>>(R, n_ent, r->E.as<uint32_t>(), r->rbid.as<uint32_t>(),
                                                              live, kk, r->keys.as<unsigned long long>(), ctr);
+    count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[5], s));
 
@@ -1143,6 +1157,11 @@ int check_ready(spr_renderer *r)
 int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
 {
     SPR_TRY(check_ready(r));
+    if (r->need_raygen) r->launches = 0;
+    struct Scope {
+        Scope(int64_t *p) { g_launch_counter = p; }
+        ~Scope() { g_launch_counter = nullptr; }
+    } scope(&r->launches);
     SPR_TRY(ensure_entry_buffers(r, s));
     SPR_TRY(ensure_scan_scratch(r, s));
     if (r->cache_dirty) SPR_TRY(reset_cache(r, s));
@@ -1404,6 +1423,7 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
     rs.bytes_decoded = rs.blocks_decoded * 256;
     rs.ms_raygen = fresh ? r->ms_raygen : 0.f;
     rs.ms_total = ms + rs.ms_raygen;
+    rs.kernel_launches = r->launches;
     if (out) *out = rs;
     if (!rs.converged) return set_error(SPR_ERR_NOT_CONVERGED, "%d passes left rays live", passes);
     return SPR_OK;

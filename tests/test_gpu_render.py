@@ -135,7 +135,8 @@ def test_small_workload_k1_k4_and_cache(spr, orc):
             check_counters(st, passes)
             assert np.array_equal(fb["final_pass"], final)
     for key in results[0]:
-        assert np.array_equal(results[0][key], results[1][key]), key
+        if key != "final_pass":          # the pass a pixel finishes in depends on k
+            assert np.array_equal(results[0][key], results[1][key]), key
 
 
 def check_counters(st, passes):
