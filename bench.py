@@ -120,7 +120,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
                                           "--query-gpu=" + self.QUERY, "--format=csv,noheader",
-                                          "-lms", "200"], stdout=self.f,
+                                          "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -207,7 +207,7 @@ def run_reference(args, wl):
     vol = make_volume_u8_or_f32(wl, "cpu")
     vol = vol.numpy() if hasattr(vol, "numpy") else vol
     comp = oracle.encode_volume(vol, dims, wl["rate"])
-    rows_every = 48 if wl["W"] >= 1280 else 8
+    rows_every = 4 if wl["W"] >= 1280 else 2
     times = []
     for step in range(args.warmup + args.steps):
         ms, det = oracle_sample(wl, step, rows_every, nthreads, comp)
@@ -234,7 +234,7 @@ def run_reference(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--steps", type=int, default=128)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="spr", choices=["spr", "reference"])
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS))
@@ -400,12 +400,11 @@ def main():
             oracle.build()
             comp_host = comp.cpu().numpy()
             nthreads = os.cpu_count() or 1
-            ms_cpu, det = oracle_sample(wl, 0, 24 if wl["W"] >= 1280 else 4, nthreads, comp_host)
+            ms_cpu, det = oracle_sample(wl, 0, 1, nthreads, comp_host)
             cpu = {"value": round(ms_cpu, 1), "unit": "ms", "cores": nthreads, "kind": "oracle",
-                   "sample": "C oracle (FP64, OpenMP %d threads): decode of all blocks (%.1f s) + "
-                             "ray casting of %d pixels (%.1f s) of pose 0, extrapolated to the "
-                             "full image" % (nthreads, det["decode_s"], det["pixels"],
-                                             det["raycast_s"])}
+                   "sample": "C oracle (FP64, OpenMP %d threads): decode of all blocks (%.2f s) + "
+                             "ray casting of all %d pixels (%.2f s) of pose 0" %
+                             (nthreads, det["decode_s"], det["pixels"], det["raycast_s"])}
         except Exception as exc:  # noqa: BLE001
             cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "failed: %s" % exc}

@@ -34,27 +34,18 @@ VolGeom make_geom(const int32_t dims[3], int rate)
 }
 
 // ---------------------------------------------------------------- kernels
-__device__ __forceinline__ void load_order(uint8_t *order_s)
-{
-    if (threadIdx.x < 64) order_s[threadIdx.x] = frc4::kOrder.v[threadIdx.x];
-    __syncthreads();
-}
-
 // raw range of each block: min/max of its decoded in-domain voxels
 __global__ void __launch_bounds__(kDecThreads) range_kernel(const uint8_t *__restrict__ comp,
                                                             VolGeom g, float2 *__restrict__ raw)
 {
     __shared__ uint32_t col_s[64 * kColStride];
-    __shared__ uint8_t order_s[64];
-    load_order(order_s);
     uint32_t *col = col_s + threadIdx.x;
     const int64_t bytes = 8 * (int64_t)g.rate;
     for (int64_t b = (int64_t)blockIdx.x * kDecThreads + threadIdx.x; b < g.nblocks;
          b += (int64_t)gridDim.x * kDecThreads) {
-        const uint32_t *w = reinterpret_cast<const uint32_t *>(comp + b * bytes);
         int emax = 0;
         float mn = 0.0f, mx = 0.0f;
-        if (frc4::decode_coeffs(w, g.rate, col, kColStride, order_s, &emax)) {
+        if (frc4::decode_block_coeffs(comp + b * bytes, g.rate, col, kColStride, &emax)) {
             int64_t bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / ((int64_t)g.nb[0] * g.nb[1]);
             int ex = min(4, (int)(g.dims[0] - 4 * bx));
             int ey = min(4, (int)(g.dims[1] - 4 * by));
@@ -151,10 +142,8 @@ __global__ void __launch_bounds__(kDecThreads) decode_list_kernel(
     const uint32_t *skip, float *__restrict__ out, unsigned int *bad)
 {
     __shared__ uint32_t col_s[64 * kColStride];
-    __shared__ uint8_t order_s[64];
     if (skip && *skip) return;
     const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
-    load_order(order_s);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t *col = col_s + threadIdx.x;
     const int64_t bytes = 8 * (int64_t)rate;
@@ -167,8 +156,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_list_kernel(
             int emax = 0;
             bool nz = false;
             if (id < nblocks) {
-                const uint32_t *w = reinterpret_cast<const uint32_t *>(comp + id * bytes);
-                nz = frc4::decode_coeffs(w, rate, col, kColStride, order_s, &emax);
+                nz = frc4::decode_block_coeffs(comp + id * bytes, rate, col, kColStride, &emax);
             } else {
                 atomicOr(bad, 1u);
             }

@@ -33,28 +33,56 @@ __host__ __device__ constexpr Order make_order()
         }
     return o;
 }
-static __constant__ Order kOrder = make_order();
 
-// bits [pos, pos+n) of a block's little-endian word stream, n <= 32
-__device__ __forceinline__ uint32_t read_bits(const uint32_t *w, int nwords, int pos, int n)
+// Bit sources: bits [pos, pos+n) of a block's little-endian stream, n <= 32.
+// Reads past the end of the stream return zeros.
+struct MemBits {   // any rate: 32-bit words read through the read-only path
+    const uint32_t *w;
+    int nwords;
+    __device__ __forceinline__ uint32_t operator()(int pos, int n) const
+    {
+        int wi = pos >> 5;
+        uint32_t lo = __ldg(w + wi);
+        uint32_t hi = (wi + 1 < nwords) ? __ldg(w + wi + 1) : 0u;
+        uint32_t v = __funnelshift_r(lo, hi, pos & 31);
+        return n >= 32 ? v : (v & ((1u << n) - 1u));
+    }
+};
+
+struct RegBits {   // rate <= 2: the whole 64- or 128-bit stream in registers
+    uint64_t lo, hi;
+    __device__ __forceinline__ uint32_t operator()(int pos, int n) const
+    {
+        uint64_t v = pos < 64 ? (pos == 0 ? lo : (lo >> pos) | (hi << (64 - pos))) : (hi >> (pos - 64));
+        uint32_t x = (uint32_t)v;
+        return n >= 32 ? x : (x & ((1u << n) - 1u));
+    }
+};
+
+__device__ __forceinline__ RegBits load_reg_bits(const uint8_t *blk, int rate)
 {
-    int wi = pos >> 5;
-    uint32_t lo = __ldg(w + wi);
-    uint32_t hi = (wi + 1 < nwords) ? __ldg(w + wi + 1) : 0u;
-    uint32_t v = __funnelshift_r(lo, hi, pos & 31);
-    return n >= 32 ? v : (v & ((1u << n) - 1u));
+    RegBits b;
+    if (rate == 2) {
+        uint4 q = __ldg(reinterpret_cast<const uint4 *>(blk));
+        b.lo = (uint64_t)q.x | ((uint64_t)q.y << 32);
+        b.hi = (uint64_t)q.z | ((uint64_t)q.w << 32);
+    } else {
+        uint2 q = __ldg(reinterpret_cast<const uint2 *>(blk));
+        b.lo = (uint64_t)q.x | ((uint64_t)q.y << 32);
+        b.hi = 0;
+    }
+    return b;
 }
 
-// Parse one block.  col[i * stride] receives the negabinary coefficient of
-// block position i.  Returns false for an all-zero block; *emax otherwise.
-// order_s is the sequency order in shared memory.
-__device__ __forceinline__ bool decode_coeffs(const uint32_t *w, int rate, uint32_t *col,
-                                              int stride, const uint8_t *order_s, int *emax)
+// Parse one block.  col[k * stride] receives the negabinary value of the k-th
+// coefficient in sequency order.  Returns false for an all-zero block.
+template <class Bits>
+__device__ __forceinline__ bool decode_coeffs(const Bits &bits_at, int rate, uint32_t *col, int stride,
+                                              int *emax)
 {
-    const int nwords = 2 * rate;
 #pragma unroll
     for (int i = 0; i < 64; ++i) col[i * stride] = 0u;
-    uint32_t h = read_bits(w, nwords, 0, 9);
+    uint32_t h = bits_at(0, 9);
     if (!(h & 1u)) return false;
     int e = (int)((h >> 1) & 0xFFu) - 127;
     *emax = e < -100 ? -100 : e;
@@ -64,18 +92,18 @@ __device__ __forceinline__ bool decode_coeffs(const uint32_t *w, int rate, uint3
         int m = n < budget ? n : budget;
         for (int base = 0; base < m; base += 32) {
             int cnt = m - base < 32 ? m - base : 32;
-            uint32_t bits = read_bits(w, nwords, pos + base, cnt);
+            uint32_t bits = bits_at(pos + base, cnt);
             while (bits) {
                 int i = __ffs(bits) - 1;
                 bits &= bits - 1;
-                col[order_s[base + i] * stride] |= 1u << p;
+                col[(base + i) * stride] |= 1u << p;
             }
         }
         pos += m;
         budget -= m;
         // group tests and significance runs
         while (n < 64 && budget > 0) {
-            uint32_t g = read_bits(w, nwords, pos, 1);
+            uint32_t g = bits_at(pos, 1);
             ++pos;
             --budget;
             if (!g) break;
@@ -84,7 +112,7 @@ __device__ __forceinline__ bool decode_coeffs(const uint32_t *w, int rate, uint3
             bool found = false;
             while (used < lim) {
                 int cnt = lim - used < 32 ? lim - used : 32;
-                uint32_t bits = read_bits(w, nwords, pos + used, cnt);
+                uint32_t bits = bits_at(pos + used, cnt);
                 if (bits) {
                     used += __ffs(bits);
                     found = true;
@@ -95,10 +123,18 @@ __device__ __forceinline__ bool decode_coeffs(const uint32_t *w, int rate, uint3
             pos += used;
             budget -= used;
             n += used;
-            if (found) col[order_s[n - 1] * stride] |= 1u << p;
+            if (found) col[(n - 1) * stride] |= 1u << p;
         }
     }
     return true;
+}
+
+// decode block `blk` (8*rate bytes, 16-byte aligned when rate == 2)
+__device__ __forceinline__ bool decode_block_coeffs(const uint8_t *blk, int rate, uint32_t *col, int stride,
+                                                    int *emax)
+{
+    if (rate <= 2) return decode_coeffs(load_reg_bits(blk, rate), rate, col, stride, emax);
+    return decode_coeffs(MemBits{reinterpret_cast<const uint32_t *>(blk), 2 * rate}, rate, col, stride, emax);
 }
 
 // two-level inverse lifting on one 4-vector, wrap-around integer arithmetic
@@ -140,12 +176,14 @@ __device__ __forceinline__ uint32_t to_negabinary(int32_t x)
 // exact power of two as float, e in [-126, 127]
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
-// Coefficients in col (block positions, negabinary) -> 64 floats in v.
+// Coefficients in col (sequency order, negabinary) -> 64 floats in v.  The
+// order table is a compile-time constant, so c[] is indexed statically.
 __device__ __forceinline__ void reconstruct(const uint32_t *col, int stride, int emax, float v[64])
 {
+    constexpr Order ord = make_order();
     int32_t c[64];
 #pragma unroll
-    for (int i = 0; i < 64; ++i) c[i] = from_negabinary(col[i * stride]);
+    for (int k = 0; k < 64; ++k) c[ord.v[k]] = from_negabinary(col[k * stride]);
 #pragma unroll
     for (int y = 0; y < 4; ++y)
 #pragma unroll

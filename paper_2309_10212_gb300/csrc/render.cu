@@ -58,6 +58,14 @@ struct Cam {
     float eye[3], p00[3], du[3], dv[3];
 };
 
+// occupancy of the three skipping levels for the current isovalue: one bit
+// per block (fine), per 4^3 blocks (coarse) and per 16^3 blocks (super)
+struct Occ {
+    const uint32_t *fine, *coarse, *super;
+    int ns[3];   // super grid over the coarse grid: ceil(nc / 4)
+    int ts[3];   // super cells the traversal can visit: ceil(tc / 4)
+};
+
 struct Geo {
     VolGeom g;
     const float2 *fine;
@@ -65,7 +73,13 @@ struct Geo {
     float iso;
     Cam cam;
     int W;
+    Occ occ;
 };
+
+__device__ __forceinline__ bool test_bit(const uint32_t *bits, int64_t i)
+{
+    return (__ldg(bits + (i >> 5)) >> (i & 31)) & 1u;
+}
 
 __device__ __forceinline__ bool holds(float2 r, float iso) { return r.x <= iso && iso <= r.y; }
 
@@ -104,17 +118,38 @@ __device__ bool block_step(const Ray &r, const VolGeom &g, int b[3])
     return ok;
 }
 
-// leave the current coarse cell; the new block is the one containing the
-// ray just after the exit point
-__device__ bool coarse_skip(const Ray &r, const VolGeom &g, int b[3])
+// block index along axis a containing p(T+), known to lie in [lo, hi]: a
+// single-precision estimate corrected by exact plane tests
+__device__ int locate_in(const Ray &r, int a, Tq T, int lo, int hi)
 {
-    int c[3] = {b[0] >> 2, b[1] >> 2, b[2] >> 2};
+    float p = fmaf(__fdiv_rn(T.n, T.ad), r.d[a], r.e[a]);
+    float q = fminf(fmaxf(__fmul_rn(p, 0.25f), (float)lo - 1.f), (float)hi + 1.f);
+    int b;
+    if (r.sgn[a] > 0) {
+        b = min(max((int)floorf(q), lo), hi);
+        while (b + 1 <= hi && tcmp(plane_t(r, a, (float)(4 * (b + 1))), T) <= 0) ++b;
+        while (b - 1 >= lo && tcmp(plane_t(r, a, (float)(4 * b)), T) > 0) --b;
+    } else {
+        b = min(max((int)ceilf(q) - 1, lo), hi);
+        while (b - 1 >= lo && tcmp(plane_t(r, a, (float)(4 * b)), T) <= 0) --b;
+        while (b + 1 <= hi && tcmp(plane_t(r, a, (float)(4 * (b + 1))), T) > 0) ++b;
+    }
+    return b;
+}
+
+// Leave the current level cell (sb blocks per side: 4 for coarse cells, 16
+// for super cells; tl cells per axis).  The new block is the one containing
+// the ray just after the exit point; false when the ray leaves the volume.
+__device__ bool skip_level(const Ray &r, const VolGeom &g, int b[3], int sb, const int tl[3])
+{
+    const int L = 4 * sb;   // voxels per level cell
+    int c[3] = {b[0] / sb, b[1] / sb, b[2] / sb};
     Tq tmin{0.f, 1.f};
     int mask = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (r.sgn[a] == 0) continue;
-        float X = r.sgn[a] > 0 ? (float)min(16 * (c[a] + 1), g.dims[a] - 1) : (float)(16 * c[a]);
+        float X = r.sgn[a] > 0 ? (float)min(L * (c[a] + 1), g.dims[a] - 1) : (float)(L * c[a]);
         Tq t = plane_t(r, a, X);
         int cmp = mask ? tcmp(t, tmin) : -1;
         if (cmp < 0) {
@@ -129,13 +164,13 @@ __device__ bool coarse_skip(const Ray &r, const VolGeom &g, int b[3])
     for (int a = 0; a < 3; ++a) {
         if (mask >> a & 1) {
             c[a] += r.sgn[a];
-            if (c[a] < 0 || c[a] >= g.tc[a]) return false;
-            b[a] = r.sgn[a] > 0 ? 4 * c[a] : min(4 * c[a] + 3, g.tb[a] - 1);
+            if (c[a] < 0 || c[a] >= tl[a]) return false;
+            b[a] = r.sgn[a] > 0 ? sb * c[a] : min(sb * c[a] + sb - 1, g.tb[a] - 1);
         } else if (r.sgn[a] > 0) {
-            int hi = min(4 * c[a] + 3, g.tb[a] - 1);
-            while (b[a] + 1 <= hi && tcmp(plane_t(r, a, (float)(4 * (b[a] + 1))), tmin) <= 0) ++b[a];
+            // the ray moves up inside this level cell: b only grows
+            b[a] = locate_in(r, a, tmin, b[a], min(sb * c[a] + sb - 1, g.tb[a] - 1));
         } else if (r.sgn[a] < 0) {
-            while (b[a] - 1 >= 4 * c[a] && tcmp(plane_t(r, a, (float)(4 * b[a])), tmin) <= 0) --b[a];
+            b[a] = locate_in(r, a, tmin, sb * c[a], b[a]);
         }
     }
     return true;
@@ -176,6 +211,45 @@ __device__ __forceinline__ void warp_add(uint32_t *ctr, uint32_t v)
     unsigned m = __activemask();
     uint32_t s = __reduce_add_sync(m, v);
     if ((threadIdx.x & 31) == (unsigned)(__ffs(m) - 1) && s) atomicAdd(ctr, s);
+}
+
+// ------------------------------------------------------------- occupancy
+// bit i = (iso lies in range i), 32 ranges per word
+__global__ void occupancy_kernel(const float2 *__restrict__ ranges, int64_t n, float iso,
+                                 uint32_t *__restrict__ bits)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (n + 31) / 32;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int64_t i = w * 32 + lane;
+        bool on = i < n && holds(ranges[i], iso);
+        unsigned m = __ballot_sync(0xFFFFFFFFu, on);
+        if (lane == 0) bits[w] = m;
+    }
+}
+
+// a super cell (4^3 coarse cells) is occupied when any of its coarse cells is
+__global__ void super_kernel(const uint32_t *__restrict__ coarse_bits, VolGeom g, Occ o,
+                             uint32_t *__restrict__ bits)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t n = (int64_t)o.ns[0] * o.ns[1] * o.ns[2];
+    const int64_t nw = (n + 31) / 32;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int64_t i = w * 32 + lane;
+        bool on = false;
+        if (i < n) {
+            int sx = (int)(i % o.ns[0]), sy = (int)((i / o.ns[0]) % o.ns[1]), sz = (int)(i / ((int64_t)o.ns[0] * o.ns[1]));
+            for (int z = 4 * sz; z < min(4 * sz + 4, g.nc[2]) && !on; ++z)
+                for (int y = 4 * sy; y < min(4 * sy + 4, g.nc[1]) && !on; ++y)
+                    for (int x = 4 * sx; x < min(4 * sx + 4, g.nc[0]) && !on; ++x)
+                        on = test_bit(coarse_bits, x + (int64_t)g.nc[0] * (y + (int64_t)g.nc[1] * z));
+        }
+        unsigned m = __ballot_sync(0xFFFFFFFFu, on);
+        if (lane == 0) bits[w] = m;
+    }
 }
 
 // ------------------------------------------------------------- ray setup
@@ -272,13 +346,18 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
                 alive = false;
                 break;
             }
+            int64_t sc = (b[0] >> 4) + (int64_t)P.occ.ns[0] * ((b[1] >> 4) + (int64_t)P.occ.ns[1] * (b[2] >> 4));
+            if (!test_bit(P.occ.super, sc)) {
+                alive = skip_level(r, g, b, 16, P.occ.ts);
+                continue;
+            }
             int64_t c = (b[0] >> 2) + (int64_t)g.nc[0] * ((b[1] >> 2) + (int64_t)g.nc[1] * (b[2] >> 2));
-            if (!holds(P.coarse[c], P.iso)) {
-                alive = coarse_skip(r, g, b);
+            if (!test_bit(P.occ.coarse, c)) {
+                alive = skip_level(r, g, b, 4, g.tc);
                 continue;
             }
             uint32_t blin = (uint32_t)(b[0] + (int64_t)g.nb[0] * (b[1] + (int64_t)g.nb[1] * b[2]));
-            if (holds(P.fine[blin], P.iso)) {
+            if (test_bit(P.occ.fine, blin)) {
                 out[cnt++] = blin;
                 set_bit(vis_bits, blin);
 #pragma unroll
@@ -928,6 +1007,9 @@ struct spr_renderer {
     DevBuf cache, blk_slot, slot_blk, lru[2], touched, miss, victim;
     int cur_lru = 0, cur_live = 0;
     int64_t launches = 0;   // kernels launched since the last render started
+    DevBuf occ_fine, occ_coarse, occ_super;
+    Occ occ{};
+    float occ_iso = NAN;
     DevBuf scan_status, scan_ticket, ctr;
     uint32_t *h_ctr = nullptr;
     cudaEvent_t ev[8] = {};
@@ -943,7 +1025,8 @@ void free_all(spr_renderer *r)
                       &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre, &r->act_wpre,
                       &r->ivis, &r->iact, &r->nbrays, &r->obrays, &r->cache, &r->blk_slot,
                       &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
-                      &r->scan_status, &r->scan_ticket, &r->ctr};
+                      &r->scan_status, &r->scan_ticket, &r->ctr, &r->occ_fine, &r->occ_coarse,
+                      &r->occ_super};
     for (DevBuf *b : bufs) buf_free(*b, nullptr);
     if (r->h_ctr) cudaFreeHost(r->h_ctr);
     r->h_ctr = nullptr;
@@ -1007,11 +1090,31 @@ Geo make_geo(const spr_renderer *r)
     P.iso = r->iso;
     P.cam = r->cam;
     P.W = r->W;
+    P.occ = r->occ;
     return P;
+}
+
+// occupancy bitmaps for the current isovalue (recomputed when it changes)
+int update_occupancy(spr_renderer *r, cudaStream_t s)
+{
+    if (r->occ_iso == r->iso) return SPR_OK;
+    const VolGeom &g = r->vol->g;
+    int64_t ns = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
+    occupancy_kernel<<<grid_for(g.nblocks, 256, 8), 256, 0, s>>>(r->vol->fine.as<float2>(), g.nblocks, r->iso,
+                                                                r->occ_fine.as<uint32_t>());
+    occupancy_kernel<<<grid_for(g.ncoarse, 256, 8), 256, 0, s>>>(r->vol->coarse.as<float2>(), g.ncoarse, r->iso,
+                                                                r->occ_coarse.as<uint32_t>());
+    super_kernel<<<grid_for(ns, 256, 8), 256, 0, s>>>(r->occ_coarse.as<uint32_t>(), g, r->occ,
+                                                      r->occ_super.as<uint32_t>());
+    count_launch(3);
+    SPR_CUDA_TRY(cudaGetLastError());
+    r->occ_iso = r->iso;
+    return SPR_OK;
 }
 
 int raygen(spr_renderer *r, cudaStream_t s)
 {
+    SPR_TRY(update_occupancy(r, s));
     uint32_t *ctr = r->ctr.as<uint32_t>();
     SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
     RaygenCount cf{make_geo(r),           r->state_in.as<uint64_t>(), r->status.as<uint8_t>(),
@@ -1264,6 +1367,23 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         return set_error(SPR_ERR_OUT_OF_MEMORY, "pinned host allocation failed");
     }
     for (auto &e : r->ev) cudaEventCreate(&e);
+    for (int a = 0; a < 3; ++a) {
+        r->occ.ns[a] = (vol->g.nc[a] + 3) / 4;
+        r->occ.ts[a] = (vol->g.tc[a] + 3) / 4;
+    }
+    {
+        int64_t ns = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
+        if ((rc = buf_alloc(r->occ_fine, 4 * ((vol->g.nblocks + 31) / 32), s)) ||
+            (rc = buf_alloc(r->occ_coarse, 4 * ((vol->g.ncoarse + 31) / 32), s)) ||
+            (rc = buf_alloc(r->occ_super, 4 * ((ns + 31) / 32), s))) {
+            free_all(r);
+            delete r;
+            return rc;
+        }
+        r->occ.fine = r->occ_fine.as<uint32_t>();
+        r->occ.coarse = r->occ_coarse.as<uint32_t>();
+        r->occ.super = r->occ_super.as<uint32_t>();
+    }
     int64_t slots = r->n_slots;
     r->n_slots = 0;
     if ((rc = spr_set_cache_budget(r, (size_t)slots * 256))) {
