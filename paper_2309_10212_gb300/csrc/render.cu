@@ -60,8 +60,13 @@ struct Cam {
 
 // occupancy of the three skipping levels for the current isovalue: one bit
 // per block (fine), per 4^3 blocks (coarse) and per 16^3 blocks (super)
+// Brick masks: fmask[c] has bit x+4y+16z set when block 4c+(x,y,z) of coarse
+// cell c holds the isovalue in its fine range; smask[s] has bit x+4y+16z set
+// when coarse cell 4s+(x,y,z) of super cell s has a nonzero fmask.  A walk
+// loads one word when it enters a coarse or super cell and then steps through
+// that cell's blocks without touching memory.
 struct Occ {
-    const uint32_t *fine, *coarse, *super;
+    const unsigned long long *fmask, *smask;
     int ns[3];   // super grid over the coarse grid: ceil(nc / 4)
     int ts[3];   // super cells the traversal can visit: ceil(tc / 4)
 };
@@ -76,10 +81,7 @@ struct Geo {
     Occ occ;
 };
 
-__device__ __forceinline__ bool test_bit(const uint32_t *bits, int64_t i)
-{
-    return (__ldg(bits + (i >> 5)) >> (i & 31)) & 1u;
-}
+
 
 __device__ __forceinline__ bool holds(float2 r, float iso) { return r.x <= iso && iso <= r.y; }
 
@@ -201,9 +203,7 @@ __device__ int locate_block(const Ray &r, int a, Tq T, int tb)
 
 __device__ __forceinline__ void set_bit(uint32_t *bits, uint32_t b)
 {
-    uint32_t m = 1u << (b & 31);
-    uint32_t *w = bits + (b >> 5);
-    if (!(*w & m)) atomicOr(w, m);
+    atomicOr(bits + (b >> 5), 1u << (b & 31));   // result unused: a reduction
 }
 
 __device__ __forceinline__ void warp_add(uint32_t *ctr, uint32_t v)
@@ -214,41 +214,39 @@ __device__ __forceinline__ void warp_add(uint32_t *ctr, uint32_t v)
 }
 
 // ------------------------------------------------------------- occupancy
-// bit i = (iso lies in range i), 32 ranges per word
-__global__ void occupancy_kernel(const float2 *__restrict__ ranges, int64_t n, float iso,
-                                 uint32_t *__restrict__ bits)
+// one thread per coarse cell: the bits of its 4^3 blocks
+__global__ void fmask_kernel(const float2 *__restrict__ fine, VolGeom g, float iso,
+                             unsigned long long *__restrict__ fmask)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (n + 31) / 32;
-    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
-         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        int64_t i = w * 32 + lane;
-        bool on = i < n && holds(ranges[i], iso);
-        unsigned m = __ballot_sync(0xFFFFFFFFu, on);
-        if (lane == 0) bits[w] = m;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncoarse;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int cx = (int)(c % g.nc[0]), cy = (int)((c / g.nc[0]) % g.nc[1]), cz = (int)(c / ((int64_t)g.nc[0] * g.nc[1]));
+        unsigned long long m = 0ull;
+        for (int k = 0; k < 64; ++k) {
+            int x = 4 * cx + (k & 3), y = 4 * cy + ((k >> 2) & 3), z = 4 * cz + (k >> 4);
+            if (x < g.nb[0] && y < g.nb[1] && z < g.nb[2] &&
+                holds(fine[x + (int64_t)g.nb[0] * (y + (int64_t)g.nb[1] * z)], iso))
+                m |= 1ull << k;
+        }
+        fmask[c] = m;
     }
 }
 
-// a super cell (4^3 coarse cells) is occupied when any of its coarse cells is
-__global__ void super_kernel(const uint32_t *__restrict__ coarse_bits, VolGeom g, Occ o,
-                             uint32_t *__restrict__ bits)
+// one thread per super cell: which of its 4^3 coarse cells hold any block
+__global__ void smask_kernel(const unsigned long long *__restrict__ fmask, VolGeom g, Occ o,
+                             unsigned long long *__restrict__ smask)
 {
-    const int lane = threadIdx.x & 31;
     const int64_t n = (int64_t)o.ns[0] * o.ns[1] * o.ns[2];
-    const int64_t nw = (n + 31) / 32;
-    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
-         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        int64_t i = w * 32 + lane;
-        bool on = false;
-        if (i < n) {
-            int sx = (int)(i % o.ns[0]), sy = (int)((i / o.ns[0]) % o.ns[1]), sz = (int)(i / ((int64_t)o.ns[0] * o.ns[1]));
-            for (int z = 4 * sz; z < min(4 * sz + 4, g.nc[2]) && !on; ++z)
-                for (int y = 4 * sy; y < min(4 * sy + 4, g.nc[1]) && !on; ++y)
-                    for (int x = 4 * sx; x < min(4 * sx + 4, g.nc[0]) && !on; ++x)
-                        on = test_bit(coarse_bits, x + (int64_t)g.nc[0] * (y + (int64_t)g.nc[1] * z));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int sx = (int)(i % o.ns[0]), sy = (int)((i / o.ns[0]) % o.ns[1]), sz = (int)(i / ((int64_t)o.ns[0] * o.ns[1]));
+        unsigned long long m = 0ull;
+        for (int k = 0; k < 64; ++k) {
+            int x = 4 * sx + (k & 3), y = 4 * sy + ((k >> 2) & 3), z = 4 * sz + (k >> 4);
+            if (x < g.nc[0] && y < g.nc[1] && z < g.nc[2] &&
+                fmask[x + (int64_t)g.nc[0] * (y + (int64_t)g.nc[1] * z)])
+                m |= 1ull << k;
         }
-        unsigned m = __ballot_sync(0xFFFFFFFFu, on);
-        if (lane == 0) bits[w] = m;
+        smask[i] = m;
     }
 }
 
@@ -340,6 +338,8 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
         if (alive && (flags & kStep)) alive = block_step(r, g, b);
         flags &= ~kStep;
         int steps = 0;
+        int64_t cur_s = -1, cur_c = -1;
+        unsigned long long smask = 0ull, fmask = 0ull;
         while (alive) {
             if (++steps > max_steps) {
                 atomicOr(&ctr[C_BAD], 2u);
@@ -347,17 +347,21 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
                 break;
             }
             int64_t sc = (b[0] >> 4) + (int64_t)P.occ.ns[0] * ((b[1] >> 4) + (int64_t)P.occ.ns[1] * (b[2] >> 4));
-            if (!test_bit(P.occ.super, sc)) {
-                alive = skip_level(r, g, b, 16, P.occ.ts);
+            if (sc != cur_s) {
+                smask = __ldg(P.occ.smask + sc);
+                cur_s = sc;
+            }
+            if (!((smask >> (((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) & 1ull)) {
+                alive = skip_level(r, g, b, smask ? 4 : 16, smask ? g.tc : P.occ.ts);
                 continue;
             }
             int64_t c = (b[0] >> 2) + (int64_t)g.nc[0] * ((b[1] >> 2) + (int64_t)g.nc[1] * (b[2] >> 2));
-            if (!test_bit(P.occ.coarse, c)) {
-                alive = skip_level(r, g, b, 4, g.tc);
-                continue;
+            if (c != cur_c) {
+                fmask = __ldg(P.occ.fmask + c);
+                cur_c = c;
             }
             uint32_t blin = (uint32_t)(b[0] + (int64_t)g.nb[0] * (b[1] + (int64_t)g.nb[1] * b[2]));
-            if (test_bit(P.occ.fine, blin)) {
+            if ((fmask >> ((b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) & 1ull) {
                 out[cnt++] = blin;
                 set_bit(vis_bits, blin);
 #pragma unroll
@@ -1007,7 +1011,7 @@ struct spr_renderer {
     DevBuf cache, blk_slot, slot_blk, lru[2], touched, miss, victim;
     int cur_lru = 0, cur_live = 0;
     int64_t launches = 0;   // kernels launched since the last render started
-    DevBuf occ_fine, occ_coarse, occ_super;
+    DevBuf occ_fine, occ_super;   // brick masks per coarse cell and per super cell
     Occ occ{};
     float occ_iso = NAN;
     DevBuf scan_status, scan_ticket, ctr;
@@ -1025,7 +1029,7 @@ void free_all(spr_renderer *r)
                       &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre, &r->act_wpre,
                       &r->ivis, &r->iact, &r->nbrays, &r->obrays, &r->cache, &r->blk_slot,
                       &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
-                      &r->scan_status, &r->scan_ticket, &r->ctr, &r->occ_fine, &r->occ_coarse,
+                      &r->scan_status, &r->scan_ticket, &r->ctr, &r->occ_fine,
                       &r->occ_super};
     for (DevBuf *b : bufs) buf_free(*b, nullptr);
     if (r->h_ctr) cudaFreeHost(r->h_ctr);
@@ -1100,13 +1104,11 @@ int update_occupancy(spr_renderer *r, cudaStream_t s)
     if (r->occ_iso == r->iso) return SPR_OK;
     const VolGeom &g = r->vol->g;
     int64_t ns = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
-    occupancy_kernel<<<grid_for(g.nblocks, 256, 8), 256, 0, s>>>(r->vol->fine.as<float2>(), g.nblocks, r->iso,
-                                                                r->occ_fine.as<uint32_t>());
-    occupancy_kernel<<<grid_for(g.ncoarse, 256, 8), 256, 0, s>>>(r->vol->coarse.as<float2>(), g.ncoarse, r->iso,
-                                                                r->occ_coarse.as<uint32_t>());
-    super_kernel<<<grid_for(ns, 256, 8), 256, 0, s>>>(r->occ_coarse.as<uint32_t>(), g, r->occ,
-                                                      r->occ_super.as<uint32_t>());
-    count_launch(3);
+    fmask_kernel<<<grid_for(g.ncoarse, 128, 16), 128, 0, s>>>(r->vol->fine.as<float2>(), g, r->iso,
+                                                              r->occ_fine.as<unsigned long long>());
+    smask_kernel<<<grid_for(ns, 128, 16), 128, 0, s>>>(r->occ_fine.as<unsigned long long>(), g, r->occ,
+                                                       r->occ_super.as<unsigned long long>());
+    count_launch(2);
     SPR_CUDA_TRY(cudaGetLastError());
     r->occ_iso = r->iso;
     return SPR_OK;
@@ -1373,16 +1375,13 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
     }
     {
         int64_t ns = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
-        if ((rc = buf_alloc(r->occ_fine, 4 * ((vol->g.nblocks + 31) / 32), s)) ||
-            (rc = buf_alloc(r->occ_coarse, 4 * ((vol->g.ncoarse + 31) / 32), s)) ||
-            (rc = buf_alloc(r->occ_super, 4 * ((ns + 31) / 32), s))) {
+        if ((rc = buf_alloc(r->occ_fine, 8 * vol->g.ncoarse, s)) || (rc = buf_alloc(r->occ_super, 8 * ns, s))) {
             free_all(r);
             delete r;
             return rc;
         }
-        r->occ.fine = r->occ_fine.as<uint32_t>();
-        r->occ.coarse = r->occ_coarse.as<uint32_t>();
-        r->occ.super = r->occ_super.as<uint32_t>();
+        r->occ.fmask = r->occ_fine.as<unsigned long long>();
+        r->occ.smask = r->occ_super.as<unsigned long long>();
     }
     int64_t slots = r->n_slots;
     r->n_slots = 0;
