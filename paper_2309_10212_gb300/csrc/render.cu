@@ -92,49 +92,107 @@ __device__ __forceinline__ uint64_t pack_state(const int b[3], uint64_t flags)
 }
 
 // ---------------------------------------------------------- exact walking
-// step to the next block; false when the ray leaves the traversal grid
-__device__ bool block_step(const Ray &r, const VolGeom &g, int b[3])
+// A walk through the block grid.  Per axis it keeps the exact signed offset N
+// of the next block plane (so t = N / |d|) and t itself rounded to single
+// precision (relative error below 2 ulps).  The next crossing is decided on
+// the rounded t; when two axes lie within 5e-7 of each other, which contains
+// every case where rounding could swap them, the exact comparison decides.
+struct Walk {
+    Ray r;
+    float inv[3];   // 1 / |d_a|
+    int b[3];       // current block
+    float N[3], t[3];
+};
+
+__device__ __forceinline__ void set_axis(Walk &w, const VolGeom &g, int a)
 {
-    Tq tmin{0.f, 1.f};
-    int mask = 0;
+    if (w.r.sgn[a] == 0) {
+        w.N[a] = 0.f;
+        w.t[a] = INFINITY;
+        return;
+    }
+    float X = w.r.sgn[a] > 0 ? (float)min(4 * (w.b[a] + 1), g.dims[a] - 1) : (float)(4 * w.b[a]);
+    float n = __fsub_rn(X, w.r.e[a]);
+    w.N[a] = w.r.sgn[a] > 0 ? n : -n;
+    w.t[a] = __fmul_rn(w.N[a], w.inv[a]);
+}
+
+__device__ __forceinline__ void walk_init(Walk &w, const VolGeom &g)
+{
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (r.sgn[a] == 0) continue;
-        float X = r.sgn[a] > 0 ? (float)min(4 * (b[a] + 1), g.dims[a] - 1) : (float)(4 * b[a]);
-        Tq t = plane_t(r, a, X);
-        int c = mask ? tcmp(t, tmin) : -1;
-        if (c < 0) {
-            tmin = t;
-            mask = 1 << a;
-        } else if (c == 0) {
-            mask |= 1 << a;
-        }
+        w.inv[a] = w.r.sgn[a] ? __frcp_rn(w.r.ad[a]) : 0.f;
+        set_axis(w, g, a);
     }
+}
+
+// the set of axes whose plane (offsets N, rounded times t) is crossed first
+__device__ __forceinline__ int first_axes(const float t[3], const float N[3], const float ad[3])
+{
+    float m = fminf(fminf(t[0], t[1]), t[2]);
+    float thr = m + fabsf(m) * 5e-7f;
+    int mask = (t[0] <= thr) | ((t[1] <= thr) << 1) | ((t[2] <= thr) << 2);
+    if (__popc(mask) > 1) {
+        int out = 0;
+        Tq best{0.f, 1.f};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!(mask >> a & 1)) continue;
+            Tq ta{N[a], ad[a]};
+            int c = out ? tcmp(ta, best) : -1;
+            if (c < 0) {
+                best = ta;
+                out = 1 << a;
+            } else if (c == 0) {
+                out |= 1 << a;
+            }
+        }
+        mask = out;
+    }
+    return mask;
+}
+
+// step to the next block; false when the walk leaves the traversal grid
+__device__ __forceinline__ bool walk_step(Walk &w, const VolGeom &g)
+{
+    int mask = first_axes(w.t, w.N, w.r.ad);
     bool ok = mask != 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         if (mask >> a & 1) {
-            b[a] += r.sgn[a];
-            if (b[a] < 0 || b[a] >= g.tb[a]) ok = false;
+            w.b[a] += w.r.sgn[a];
+            if (w.b[a] < 0 || w.b[a] >= g.tb[a]) ok = false;
+            else set_axis(w, g, a);
         }
     return ok;
 }
 
-// block index along axis a containing p(T+), known to lie in [lo, hi]: a
-// single-precision estimate corrected by exact plane tests
-__device__ int locate_in(const Ray &r, int a, Tq T, int lo, int hi)
+// sign(t_X - T) for a plane X on axis a, filtered on the rounded times
+__device__ __forceinline__ int cmp_plane(const Walk &w, int a, float X, Tq T, float Tv)
 {
-    float p = fmaf(__fdiv_rn(T.n, T.ad), r.d[a], r.e[a]);
+    float n = __fsub_rn(X, w.r.e[a]);
+    Tq tx{w.r.sgn[a] > 0 ? n : -n, w.r.ad[a]};
+    float tv = __fmul_rn(tx.n, w.inv[a]);
+    float d = tv - Tv, tol = (fabsf(tv) + fabsf(Tv)) * 3e-7f;
+    if (d > tol) return 1;
+    if (d < -tol) return -1;
+    return exact_sign_diff(tx.n, T.ad, T.n, tx.ad);
+}
+
+// block index along axis a containing p(T+), known to lie in [lo, hi]
+__device__ __forceinline__ int locate_in(const Walk &w, int a, Tq T, float Tv, int lo, int hi)
+{
+    float p = fmaf(Tv, w.r.d[a], w.r.e[a]);
     float q = fminf(fmaxf(__fmul_rn(p, 0.25f), (float)lo - 1.f), (float)hi + 1.f);
     int b;
-    if (r.sgn[a] > 0) {
+    if (w.r.sgn[a] > 0) {
         b = min(max((int)floorf(q), lo), hi);
-        while (b + 1 <= hi && tcmp(plane_t(r, a, (float)(4 * (b + 1))), T) <= 0) ++b;
-        while (b - 1 >= lo && tcmp(plane_t(r, a, (float)(4 * b)), T) > 0) --b;
+        while (b + 1 <= hi && cmp_plane(w, a, (float)(4 * (b + 1)), T, Tv) <= 0) ++b;
+        while (b - 1 >= lo && cmp_plane(w, a, (float)(4 * b), T, Tv) > 0) --b;
     } else {
         b = min(max((int)ceilf(q) - 1, lo), hi);
-        while (b - 1 >= lo && tcmp(plane_t(r, a, (float)(4 * b)), T) <= 0) --b;
-        while (b + 1 <= hi && tcmp(plane_t(r, a, (float)(4 * (b + 1))), T) > 0) ++b;
+        while (b - 1 >= lo && cmp_plane(w, a, (float)(4 * b), T, Tv) <= 0) --b;
+        while (b + 1 <= hi && cmp_plane(w, a, (float)(4 * (b + 1)), T, Tv) > 0) ++b;
     }
     return b;
 }
@@ -142,39 +200,53 @@ __device__ int locate_in(const Ray &r, int a, Tq T, int lo, int hi)
 // Leave the current level cell (sb blocks per side: 4 for coarse cells, 16
 // for super cells; tl cells per axis).  The new block is the one containing
 // the ray just after the exit point; false when the ray leaves the volume.
-__device__ bool skip_level(const Ray &r, const VolGeom &g, int b[3], int sb, const int tl[3])
+__device__ __forceinline__ bool skip_level(Walk &w, const VolGeom &g, int sb, const int tl[3])
 {
-    const int L = 4 * sb;   // voxels per level cell
-    int c[3] = {b[0] / sb, b[1] / sb, b[2] / sb};
-    Tq tmin{0.f, 1.f};
-    int mask = 0;
+    const int L = 4 * sb;
+    int c[3];
+    float NL[3], TL[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (r.sgn[a] == 0) continue;
-        float X = r.sgn[a] > 0 ? (float)min(L * (c[a] + 1), g.dims[a] - 1) : (float)(L * c[a]);
-        Tq t = plane_t(r, a, X);
-        int cmp = mask ? tcmp(t, tmin) : -1;
-        if (cmp < 0) {
-            tmin = t;
-            mask = 1 << a;
-        } else if (cmp == 0) {
-            mask |= 1 << a;
+        c[a] = w.b[a] / sb;
+        if (w.r.sgn[a] == 0) {
+            NL[a] = 0.f;
+            TL[a] = INFINITY;
+            continue;
         }
+        float X = w.r.sgn[a] > 0 ? (float)min(L * (c[a] + 1), g.dims[a] - 1) : (float)(L * c[a]);
+        float n = __fsub_rn(X, w.r.e[a]);
+        NL[a] = w.r.sgn[a] > 0 ? n : -n;
+        TL[a] = __fmul_rn(NL[a], w.inv[a]);
     }
+    int mask = first_axes(TL, NL, w.r.ad);
     if (!mask) return false;
+    // the exit time, taken from the lowest axis of the set (static indexing)
+    Tq T;
+    float Tv;
+    if (mask & 1) {
+        T = Tq{NL[0], w.r.ad[0]};
+        Tv = TL[0];
+    } else if (mask & 2) {
+        T = Tq{NL[1], w.r.ad[1]};
+        Tv = TL[1];
+    } else {
+        T = Tq{NL[2], w.r.ad[2]};
+        Tv = TL[2];
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (mask >> a & 1) {
-            c[a] += r.sgn[a];
+            c[a] += w.r.sgn[a];
             if (c[a] < 0 || c[a] >= tl[a]) return false;
-            b[a] = r.sgn[a] > 0 ? sb * c[a] : min(sb * c[a] + sb - 1, g.tb[a] - 1);
-        } else if (r.sgn[a] > 0) {
-            // the ray moves up inside this level cell: b only grows
-            b[a] = locate_in(r, a, tmin, b[a], min(sb * c[a] + sb - 1, g.tb[a] - 1));
-        } else if (r.sgn[a] < 0) {
-            b[a] = locate_in(r, a, tmin, sb * c[a], b[a]);
+            w.b[a] = w.r.sgn[a] > 0 ? sb * c[a] : min(sb * c[a] + sb - 1, g.tb[a] - 1);
+        } else if (w.r.sgn[a] > 0) {
+            w.b[a] = locate_in(w, a, T, Tv, w.b[a], min(sb * c[a] + sb - 1, g.tb[a] - 1));
+        } else if (w.r.sgn[a] < 0) {
+            w.b[a] = locate_in(w, a, T, Tv, sb * c[a], w.b[a]);
         }
     }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) set_axis(w, g, a);
     return true;
 }
 
@@ -324,21 +396,28 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
     // every step moves at least one block index monotonically, so a walk
     // never takes more steps than this; exceeding it is an internal error
     const int max_steps = 2 * (g.tb[0] + g.tb[1] + g.tb[2]) + 8;
+    const uint32_t nb0 = g.nb[0], nb1 = g.nb[1], nc0 = g.nc[0], nc1 = g.nc[1];
+    const uint32_t ns0 = P.occ.ns[0], ns1 = P.occ.ns[1];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nproc;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t ray = live[i];
-        Ray r;
-        make_ray(r, P.cam.eye, P.cam.p00, P.cam.du, P.cam.dv, (int)(ray % P.W), (int)(ray / P.W));
+        Walk w;
+        make_ray(w.r, P.cam.eye, P.cam.p00, P.cam.du, P.cam.dv, (int)(ray % P.W), (int)(ray / P.W));
         const uint64_t st = state_in[ray];
-        int b[3] = {(int)(st & 0xFFFF), (int)((st >> 16) & 0xFFFF), (int)((st >> 32) & 0xFFFF)};
+        w.b[0] = (int)(st & 0xFFFF);
+        w.b[1] = (int)((st >> 16) & 0xFFFF);
+        w.b[2] = (int)((st >> 32) & 0xFFFF);
         uint64_t flags = st >> 48;
         uint32_t *out = rbid + (uint64_t)i * kk;
         int cnt = 0;
         bool alive = !(flags & kDone);
-        if (alive && (flags & kStep)) alive = block_step(r, g, b);
+        if (alive) {
+            walk_init(w, g);
+            if (flags & kStep) alive = walk_step(w, g);
+        }
         flags &= ~kStep;
         int steps = 0;
-        int64_t cur_s = -1, cur_c = -1;
+        uint32_t cur_s = 0xFFFFFFFFu, cur_c = 0xFFFFFFFFu;
         unsigned long long smask = 0ull, fmask = 0ull;
         while (alive) {
             if (++steps > max_steps) {
@@ -346,40 +425,41 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
                 alive = false;
                 break;
             }
-            int64_t sc = (b[0] >> 4) + (int64_t)P.occ.ns[0] * ((b[1] >> 4) + (int64_t)P.occ.ns[1] * (b[2] >> 4));
+            const int *b = w.b;
+            uint32_t sc = (uint32_t)(b[0] >> 4) + ns0 * ((uint32_t)(b[1] >> 4) + ns1 * (uint32_t)(b[2] >> 4));
             if (sc != cur_s) {
                 smask = __ldg(P.occ.smask + sc);
                 cur_s = sc;
             }
             if (!((smask >> (((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) & 1ull)) {
-                alive = skip_level(r, g, b, smask ? 4 : 16, smask ? g.tc : P.occ.ts);
+                alive = skip_level(w, g, smask ? 4 : 16, smask ? g.tc : P.occ.ts);
                 continue;
             }
-            int64_t c = (b[0] >> 2) + (int64_t)g.nc[0] * ((b[1] >> 2) + (int64_t)g.nc[1] * (b[2] >> 2));
+            uint32_t c = (uint32_t)(b[0] >> 2) + nc0 * ((uint32_t)(b[1] >> 2) + nc1 * (uint32_t)(b[2] >> 2));
             if (c != cur_c) {
                 fmask = __ldg(P.occ.fmask + c);
                 cur_c = c;
             }
-            uint32_t blin = (uint32_t)(b[0] + (int64_t)g.nb[0] * (b[1] + (int64_t)g.nb[1] * b[2]));
             if ((fmask >> ((b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) & 1ull) {
+                uint32_t blin = (uint32_t)b[0] + nb0 * ((uint32_t)b[1] + nb1 * (uint32_t)b[2]);
                 out[cnt++] = blin;
                 set_bit(vis_bits, blin);
 #pragma unroll
                 for (int o = 0; o < 8; ++o) {
                     int x = b[0] + (o & 1), y = b[1] + ((o >> 1) & 1), z = b[2] + (o >> 2);
                     if (x < g.nb[0] && y < g.nb[1] && z < g.nb[2])
-                        set_bit(act_bits, (uint32_t)(x + (int64_t)g.nb[0] * (y + (int64_t)g.nb[1] * z)));
+                        set_bit(act_bits, (uint32_t)x + nb0 * ((uint32_t)y + nb1 * (uint32_t)z));
                 }
                 if (cnt == kk) {
                     flags |= kStep;
                     break;
                 }
             }
-            alive = block_step(r, g, b);
+            alive = walk_step(w, g);
         }
         if (!alive) flags |= kDone;
         for (int j = cnt; j < kk; ++j) out[j] = kNone;
-        state_out[ray] = pack_state(b, flags);
+        state_out[ray] = pack_state(w.b, flags);
     }
 }
 
