@@ -54,6 +54,26 @@ enum Ctr {
     C_COUNT = 16
 };
 
+// The pass loop's state lives on the device, so that a pass (and a whole
+// render, as one graph launch) needs no host round trip: begin_pass_kernel
+// applies the speculation rule, end_pass_kernel records the pass, swaps the
+// double-buffered lists, or halves k / the ray window when the pass overflowed
+// the cache, and decides whether another pass runs.
+struct PassState {
+    uint32_t n_live;      // live rays at the start of the pass in progress
+    uint32_t k, kk, nproc;  // rule's k, k of this attempt, live rays taken
+    uint32_t pass;        // passes completed since ray generation
+    uint32_t parity;      // bit 0: live list in use, bit 1: LRU list in use
+    uint32_t retries;     // overflowed attempts of the pass in progress
+    uint32_t open;        // 1 when an overflowed pass waits for its retry
+    uint32_t max_passes;  // stop after this many passes
+    uint32_t run;         // 1 while passes should continue
+    uint32_t error;       // bit 0: wait timeout, bits 1..: kernel error flags
+    uint32_t spec_mode, k_fixed, k_max;
+    uint32_t npix;
+    uint32_t n_enter;     // rays that entered the volume at ray generation
+};
+
 struct Cam {
     float eye[3], p00[3], du[3], dv[3];
 };
@@ -71,12 +91,14 @@ struct Occ {
     int ts[3];   // super cells the traversal can visit: ceil(tc / 4)
 };
 
+// camera and isovalue live in device memory (read at kernel start), so that a
+// captured pass graph stays valid when they change
 struct Geo {
     VolGeom g;
     const float2 *fine;
     const float2 *coarse;
-    float iso;
-    Cam cam;
+    const Cam *camd;
+    const float *isod;
     int W;
     Occ occ;
 };
@@ -342,7 +364,8 @@ struct RaygenCount {
         cell[p] = kNoKey;
         final_pass[p] = 0;
         Ray r;
-        make_ray(r, P.cam.eye, P.cam.p00, P.cam.du, P.cam.dv, (int)(p % P.W), (int)(p / P.W));
+        const Cam &cam = *P.camd;
+        make_ray(r, cam.eye, cam.p00, cam.du, cam.dv, (int)(p % P.W), (int)(p / P.W));
         const VolGeom &g = P.g;
         Tq tin{0.f, 1.f}, tout{0.f, 1.f};
         bool have_out = false;
@@ -384,8 +407,9 @@ struct IndexEmit {
 };
 
 // ------------------------------------------------------------- traversal
-__global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__restrict__ live,
-                                                       uint32_t nproc, int kk,
+__global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__restrict__ live0,
+                                                       const uint32_t *__restrict__ live1,
+                                                       const PassState *__restrict__ ps,
                                                        const uint64_t *__restrict__ state_in,
                                                        uint64_t *__restrict__ state_out,
                                                        uint32_t *__restrict__ rbid,
@@ -393,6 +417,10 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
                                                        uint32_t *ctr)
 {
     const VolGeom &g = P.g;
+    const uint32_t nproc = ps->nproc;
+    const int kk = (int)ps->kk;
+    const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
+    const Cam cam = *P.camd;
     // every step moves at least one block index monotonically, so a walk
     // never takes more steps than this; exceeding it is an internal error
     const int max_steps = 2 * (g.tb[0] + g.tb[1] + g.tb[2]) + 8;
@@ -402,7 +430,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t ray = live[i];
         Walk w;
-        make_ray(w.r, P.cam.eye, P.cam.p00, P.cam.du, P.cam.dv, (int)(ray % P.W), (int)(ray / P.W));
+        make_ray(w.r, cam.eye, cam.p00, cam.du, cam.dv, (int)(ray % P.W), (int)(ray / P.W));
         const uint64_t st = state_in[ray];
         w.b[0] = (int)(st & 0xFFFF);
         w.b[1] = (int)((st >> 16) & 0xFFFF);
@@ -501,11 +529,12 @@ __device__ __forceinline__ uint32_t vis_rank(const uint32_t *bits, const uint32_
     return wpre[w] + __popc(bits[w] & ((1u << (b & 31)) - 1u));
 }
 
-__global__ void count_entries_kernel(int64_t n, const uint32_t *__restrict__ rbid, const uint32_t *vis_bits,
+__global__ void count_entries_kernel(const PassState *ps, const uint32_t *__restrict__ rbid, const uint32_t *vis_bits,
                                      const uint32_t *vis_wpre, uint32_t *nbrays, uint32_t *erank,
                                      const uint32_t *ctr)
 {
     if (ctr[C_OVERFLOW]) return;
+    const int64_t n = (int64_t)ps->nproc * ps->kk;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         uint32_t b = rbid[e];
         if (b == kNone) continue;
@@ -525,11 +554,12 @@ struct ArrayEmit {
     __device__ void operator()(int64_t i, uint32_t pre, uint32_t) const { out[i] = pre; }
 };
 
-__global__ void scatter_entries_kernel(int64_t n, const uint32_t *__restrict__ rbid, const uint32_t *vis_bits,
+__global__ void scatter_entries_kernel(const PassState *ps, const uint32_t *__restrict__ rbid, const uint32_t *vis_bits,
                                        const uint32_t *vis_wpre, const uint32_t *obrays,
                                        const uint32_t *erank, uint32_t *E, const uint32_t *ctr)
 {
     if (ctr[C_OVERFLOW]) return;
+    const int64_t n = (int64_t)ps->nproc * ps->kk;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         uint32_t b = rbid[e];
         if (b == kNone) continue;
@@ -564,25 +594,33 @@ struct SelectEmit {
     }
 };
 
+// the LRU list in use and the one being built, chosen by the pass parity
+struct LruPair {
+    uint32_t *l0, *l1;
+    const PassState *ps;
+    __device__ uint32_t *cur() const { return (ps->parity & 2) ? l1 : l0; }
+    __device__ uint32_t *next() const { return (ps->parity & 2) ? l0 : l1; }
+};
+
 struct VictimCount {
-    const uint32_t *lru;
+    LruPair lru;
     const uint8_t *touched;
     const uint32_t *skip;
     __device__ bool enabled() const { return !*skip; }
-    __device__ uint32_t operator()(int64_t i) const { return touched[lru[i]] ? 0u : 1u; }
+    __device__ uint32_t operator()(int64_t i) const { return touched[lru.cur()[i]] ? 0u : 1u; }
 };
 
 struct VictimEmit {
-    const uint32_t *lru;
+    LruPair lru;
     const uint32_t *n_miss;
     uint32_t *victim;
-    uint32_t *lru_next;
     __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
     {
         if (!c) return;
         uint32_t nm = *n_miss;
-        if (pre < nm) victim[pre] = lru[i];
-        else lru_next[pre - nm] = lru[i];
+        uint32_t slot = lru.cur()[i];
+        if (pre < nm) victim[pre] = slot;
+        else lru.next()[pre - nm] = slot;
     }
 };
 
@@ -617,11 +655,11 @@ struct TouchedCount {
 struct TouchedEmit {
     uint8_t *touched;
     const uint32_t *ctr;
-    uint32_t *lru_next;
+    LruPair lru;
     __device__ void operator()(int64_t s, uint32_t pre, uint32_t c) const
     {
         if (!c) return;
-        lru_next[ctr[C_NUNTOUCHED] - ctr[C_NMISS] + pre] = (uint32_t)s;
+        lru.next()[ctr[C_NUNTOUCHED] - ctr[C_NMISS] + pre] = (uint32_t)s;
         touched[s] = 0;
     }
 };
@@ -789,10 +827,10 @@ __device__ __forceinline__ uint32_t pick8(const uint32_t s[8], int k)
 
 // Intersect the ray with the isosurface inside block (bx,by,bz).  On a hit,
 // returns the 44 low bits of the resolve key: depth bits, local cell, grey.
-__device__ bool intersect_block(const RT &R, const Ray &r, int bx, int by, int bz, uint64_t &payload)
+__device__ bool intersect_block(const RT &R, const Ray &r, float isov, int bx, int by, int bz, uint64_t &payload)
 {
     const VolGeom &g = R.P.g;
-    const float iso = R.P.iso;
+    const float iso = isov;
     const int bq[3] = {bx, by, bz};
     float o[3];
     int ext[3];
@@ -953,34 +991,38 @@ __device__ bool intersect_block(const RT &R, const Ray &r, int bx, int by, int b
     return false;
 }
 
-__global__ void __launch_bounds__(128) intersect_kernel(RT R, int64_t cap, const uint32_t *__restrict__ E,
+__global__ void __launch_bounds__(128) intersect_kernel(RT R, const uint32_t *__restrict__ E,
                                                         const uint32_t *__restrict__ rbid,
-                                                        const uint32_t *__restrict__ live, int kk,
+                                                        const uint32_t *__restrict__ live0,
+                                                        const uint32_t *__restrict__ live1,
+                                                        const PassState *__restrict__ ps,
                                                         unsigned long long *keys, const uint32_t *ctr)
 {
     if (ctr[C_OVERFLOW]) return;
+    const uint32_t kk = ps->kk;
+    const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
+    const Cam cam = *R.P.camd;
+    const float iso = *R.P.isod;
     const int64_t n = ctr[C_NENT];
     const VolGeom &g = R.P.g;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         uint32_t e = E[idx];
         uint32_t b = rbid[e];
-        uint32_t i = e / (uint32_t)kk, j = e - i * (uint32_t)kk;
+        uint32_t i = e / kk, j = e - i * kk;
         uint32_t ray = live[i];
         Ray r;
-        make_ray(r, R.P.cam.eye, R.P.cam.p00, R.P.cam.du, R.P.cam.dv, (int)(ray % R.P.W), (int)(ray / R.P.W));
+        make_ray(r, cam.eye, cam.p00, cam.du, cam.dv, (int)(ray % R.P.W), (int)(ray / R.P.W));
         int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((uint32_t)g.nb[0] * g.nb[1]));
         uint64_t payload;
-        if (intersect_block(R, r, bx, by, bz, payload)) atomicMin(keys + ray, ((uint64_t)j << 52) | payload);
+        if (intersect_block(R, r, iso, bx, by, bz, payload)) atomicMin(keys + ray, ((uint64_t)j << 52) | payload);
     }
 }
 
 // ---------------------------------------------------------------- resolve
 struct ResolveCount {
-    const uint32_t *live;
-    uint32_t nproc;
-    int kk;
-    int pass;
+    const uint32_t *live0, *live1;
+    const PassState *ps;
     int Dx, Dy;
     VolGeom g;
     unsigned long long *keys;
@@ -996,6 +1038,9 @@ struct ResolveCount {
     __device__ bool enabled() const { return !ctr[C_OVERFLOW]; }
     __device__ uint32_t operator()(int64_t i) const
     {
+        const uint32_t *live = (ps->parity & 1) ? live1 : live0;
+        const uint32_t nproc = ps->nproc, kk = ps->kk;
+        const int pass = (int)ps->pass + 1;
         const uint32_t ray = live[i];
         uint32_t alive = 1, hit = 0, gone = 0;
         if (i < (int64_t)nproc) {
@@ -1034,6 +1079,99 @@ struct ResolveCount {
         return alive;
     }
 };
+
+struct LiveEmit {
+    uint32_t *live0, *live1;
+    const PassState *ps;
+    __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
+    {
+        if (!c) return;
+        if (ps->parity & 1) live0[pre] = live1[i];
+        else live1[pre] = live0[i];
+    }
+};
+
+// ------------------------------------------------------------ pass control
+__global__ void begin_pass_kernel(PassState *ps, uint32_t *ctr)
+{
+    if (threadIdx.x < C_COUNT) ctr[threadIdx.x] = 0u;
+    if (threadIdx.x == 0 && !ps->open) {
+        uint32_t n = ps->n_live;
+        uint32_t k = ps->spec_mode == SPR_SPEC_FIXED
+                         ? ps->k_fixed
+                         : max(1u, min(ps->k_max, ps->npix / max(n, 1u)));
+        ps->k = k;
+        ps->kk = k;
+        ps->nproc = n;
+        ps->retries = 0;
+    }
+}
+
+__global__ void end_pass_kernel(PassState *ps, const uint32_t *ctr, spr_pass_stats *recs,
+                                cudaGraphConditionalHandle handle, int use_handle)
+{
+    if (threadIdx.x != 0) return;
+    if (ctr[C_SCANFLAGS] || ctr[C_BAD]) {
+        ps->error = (ctr[C_SCANFLAGS] ? 1u : 0u) | (ctr[C_BAD] << 1);
+        ps->run = 0;
+    } else if (ps->n_live == 0) {
+        ps->run = 0;
+    } else if (ctr[C_OVERFLOW]) {
+        ps->retries += 1;
+        ps->open = 1;
+        if (ps->kk > 1) ps->kk /= 2;
+        else ps->nproc = max(1u, ps->nproc / 2);
+    } else {
+        if (ps->pass < ps->max_passes) {
+            spr_pass_stats st{};
+            st.pass = (int32_t)ps->pass + 1;
+            st.k = (int32_t)ps->k;
+            st.k_used = (int32_t)ps->kk;
+            st.retries = (int32_t)ps->retries;
+            st.n_active = ps->n_live;
+            st.n_processed = ps->nproc;
+            st.n_entries = ctr[C_NENT];
+            st.n_visible = ctr[C_NVIS];
+            st.n_requested = ctr[C_NACT];
+            st.n_decoded = ctr[C_NMISS];
+            st.n_evicted = ctr[C_EVICT];
+            st.n_term_hit = ctr[C_HIT];
+            st.n_term_miss = ctr[C_MISSRAY];
+            st.n_active_after = ctr[C_NLIVE];
+            st.utilization = (double)ctr[C_NENT] / (double)ps->npix;
+            recs[ps->pass] = st;
+        }
+        ps->pass += 1;
+        ps->parity ^= 3u;
+        ps->n_live = ctr[C_NLIVE];
+        ps->open = 0;
+        ps->run = (ps->n_live > 0 && ps->pass < ps->max_passes) ? 1u : 0u;
+    }
+    if (use_handle) cudaGraphSetConditional(handle, ps->run);
+}
+
+__global__ void config_kernel(PassState *ps, uint32_t spec_mode, uint32_t k_fixed, uint32_t k_max, uint32_t npix)
+{
+    if (threadIdx.x != 0) return;
+    ps->spec_mode = spec_mode;
+    ps->k_fixed = k_fixed;
+    ps->k_max = k_max;
+    ps->npix = npix;
+}
+
+// after ray generation: the live list is list 0 and the pass count restarts
+__global__ void after_raygen_kernel(PassState *ps, const uint32_t *ctr)
+{
+    if (threadIdx.x != 0) return;
+    ps->n_live = ctr[C_NLIVE];
+    ps->n_enter = ctr[C_NLIVE];
+    ps->pass = 0;
+    ps->parity &= ~1u;
+    ps->open = 0;
+    ps->retries = 0;
+    ps->error = ctr[C_SCANFLAGS] ? 1u : 0u;
+    ps->run = ps->n_live > 0 ? 1u : 0u;
+}
 
 // -------------------------------------------------------------- utilities
 thread_local int64_t *g_launch_counter = nullptr;
@@ -1077,7 +1215,8 @@ struct spr_renderer {
 
     bool need_raygen = true;
     bool cache_dirty = true;
-    int pass = 0;
+    bool params_dirty = true;   // camera / isovalue / speculation not yet on the device
+    int pass = 0;               // passes completed (host mirror of the device state)
     uint32_t n_live = 0;
     uint32_t n_enter = 0;
     float ms_raygen = 0.f;
@@ -1089,33 +1228,53 @@ struct spr_renderer {
     DevBuf vis_bits, act_bits, vis_wpre, act_wpre, ivis, iact, nbrays, obrays;
     int64_t nwords = 0, cap_act = 0;
     DevBuf cache, blk_slot, slot_blk, lru[2], touched, miss, victim;
-    int cur_lru = 0, cur_live = 0;
-    int64_t launches = 0;   // kernels launched since the last render started
+    int64_t launches = 0;         // kernels launched since the last render started
     DevBuf occ_fine, occ_super;   // brick masks per coarse cell and per super cell
     Occ occ{};
     float occ_iso = NAN;
     DevBuf scan_status, scan_ticket, ctr;
-    uint32_t *h_ctr = nullptr;
+    DevBuf ps, recs, camd;        // device pass state, per-pass records, camera + isovalue
+    static constexpr int kRecCap = 4096;
+    PassState *h_ps = nullptr;    // pinned
+    uint32_t *h_ctr = nullptr;    // pinned
     cudaEvent_t ev[8] = {};
+    // the pass loop as one graph: a while node whose body is one pass
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_kernels = 0;        // kernels in one pass of the body
 };
 
 namespace {
 
+void drop_graph(spr_renderer *r)
+{
+    if (r->gexec) cudaGraphExecDestroy(r->gexec);
+    if (r->graph) cudaGraphDestroy(r->graph);
+    r->gexec = nullptr;
+    r->graph = nullptr;
+}
+
 void free_all(spr_renderer *r)
 {
     cudaDeviceSynchronize();
+    drop_graph(r);
     DevBuf *bufs[] = {&r->state_in, &r->state_out, &r->status, &r->live[0], &r->live[1], &r->keys,
                       &r->fb_depth, &r->fb_rgba, &r->fb_block, &r->fb_cell, &r->fb_final, &r->rbid,
                       &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre, &r->act_wpre,
                       &r->ivis, &r->iact, &r->nbrays, &r->obrays, &r->cache, &r->blk_slot,
                       &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
-                      &r->scan_status, &r->scan_ticket, &r->ctr, &r->occ_fine,
-                      &r->occ_super};
+                      &r->scan_status, &r->scan_ticket, &r->ctr, &r->occ_fine, &r->occ_super,
+                      &r->ps, &r->recs, &r->camd};
     for (DevBuf *b : bufs) buf_free(*b, nullptr);
     if (r->h_ctr) cudaFreeHost(r->h_ctr);
+    if (r->h_ps) cudaFreeHost(r->h_ps);
     r->h_ctr = nullptr;
+    r->h_ps = nullptr;
     for (auto &e : r->ev)
         if (e) cudaEventDestroy(e);
+    if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
+    r->cap_stream = nullptr;
 }
 
 int64_t entries_needed(const spr_renderer *r)
@@ -1130,6 +1289,7 @@ int ensure_entry_buffers(spr_renderer *r, cudaStream_t s)
     if (cap > 0x7FFFFFFFll)
         return set_error(SPR_ERR_INVALID_ARG, "width*height*k = %lld exceeds 2^31 entries", (long long)cap);
     if (cap <= r->cap_entries) return SPR_OK;
+    drop_graph(r);
     SPR_TRY(buf_reserve(r->rbid, sizeof(uint32_t) * cap, s));
     SPR_TRY(buf_reserve(r->erank, sizeof(uint32_t) * cap, s));
     SPR_TRY(buf_reserve(r->E, sizeof(uint32_t) * cap, s));
@@ -1148,7 +1308,9 @@ int ensure_entry_buffers(spr_renderer *r, cudaStream_t s)
 int ensure_scan_scratch(spr_renderer *r, cudaStream_t s)
 {
     int64_t biggest = std::max({r->npix, r->n_slots, r->nwords, r->cap_entries, r->cap_act, (int64_t)1});
-    return buf_reserve(r->scan_status, sizeof(unsigned long long) * (scan_tiles(biggest) + 1), s);
+    size_t need = sizeof(unsigned long long) * (scan_tiles(biggest) + 1);
+    if (r->scan_status.bytes < need) drop_graph(r);
+    return buf_reserve(r->scan_status, need, s);
 }
 
 int reset_cache(spr_renderer *r, cudaStream_t s)
@@ -1157,10 +1319,11 @@ int reset_cache(spr_renderer *r, cudaStream_t s)
     SPR_CUDA_TRY(cudaMemsetAsync(r->blk_slot.p, 0xFF, sizeof(uint32_t) * g.nblocks, s));
     SPR_CUDA_TRY(cudaMemsetAsync(r->slot_blk.p, 0xFF, sizeof(uint32_t) * r->n_slots, s));
     SPR_CUDA_TRY(cudaMemsetAsync(r->touched.p, 0, r->n_slots, s));
+    // both LRU lists start as the identity, so either parity holds it
     lru_init_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, s>>>(r->lru[0].as<uint32_t>(), r->n_slots);
-    count_launch();
+    lru_init_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, s>>>(r->lru[1].as<uint32_t>(), r->n_slots);
+    count_launch(2);
     SPR_CUDA_TRY(cudaGetLastError());
-    r->cur_lru = 0;
     r->cache_dirty = false;
     return SPR_OK;
 }
@@ -1171,8 +1334,8 @@ Geo make_geo(const spr_renderer *r)
     P.g = r->vol->g;
     P.fine = r->vol->fine.as<float2>();
     P.coarse = r->vol->coarse.as<float2>();
-    P.iso = r->iso;
-    P.cam = r->cam;
+    P.camd = r->camd.as<Cam>();
+    P.isod = reinterpret_cast<const float *>(r->camd.as<char>() + sizeof(Cam));
     P.W = r->W;
     P.occ = r->occ;
     return P;
@@ -1194,7 +1357,25 @@ int update_occupancy(spr_renderer *r, cudaStream_t s)
     return SPR_OK;
 }
 
-int raygen(spr_renderer *r, cudaStream_t s)
+// camera, isovalue and the speculation configuration to the device
+int upload_params(spr_renderer *r, cudaStream_t s)
+{
+    if (!r->params_dirty) return SPR_OK;
+    struct {
+        Cam cam;
+        float iso;
+    } h{r->cam, r->iso};
+    SPR_CUDA_TRY(cudaMemcpyAsync(r->camd.p, &h, sizeof h, cudaMemcpyHostToDevice, s));
+    config_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), (uint32_t)r->spec_mode, (uint32_t)r->k_fixed,
+                                   (uint32_t)r->k_max, (uint32_t)r->npix);
+    count_launch();
+    SPR_CUDA_TRY(cudaStreamSynchronize(s));   // h lives on this stack frame
+    r->params_dirty = false;
+    return SPR_OK;
+}
+
+// ray generation (no host synchronisation): rays, live list 0, pass state
+int enqueue_raygen(spr_renderer *r, cudaStream_t s)
 {
     SPR_TRY(update_occupancy(r, s));
     uint32_t *ctr = r->ctr.as<uint32_t>();
@@ -1202,42 +1383,48 @@ int raygen(spr_renderer *r, cudaStream_t s)
     RaygenCount cf{make_geo(r),           r->state_in.as<uint64_t>(), r->status.as<uint8_t>(),
                    r->keys.as<uint64_t>(), r->fb_depth.as<float>(),   r->fb_rgba.as<uint32_t>(),
                    r->fb_block.as<uint32_t>(), r->fb_cell.as<uint64_t>(), r->fb_final.as<int32_t>()};
-    r->cur_live = 0;
     IndexEmit ef{r->live[0].as<uint32_t>()};
     SPR_TRY(run_compact(r->scan_status, r->scan_ticket, ctr + C_SCANFLAGS, r->npix, nullptr, cf, ef,
                         ctr + C_NLIVE, s));
-    SPR_CUDA_TRY(cudaMemcpyAsync(r->h_ctr, ctr, sizeof(uint32_t) * C_COUNT, cudaMemcpyDeviceToHost, s));
-    SPR_CUDA_TRY(cudaStreamSynchronize(s));
-    if (r->h_ctr[C_SCANFLAGS]) return set_error(SPR_ERR_DEVICE_TIMEOUT, "ray compaction timed out");
-    r->n_live = r->h_ctr[C_NLIVE];
-    r->n_enter = r->n_live;
-    r->pass = 0;
+    after_raygen_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), ctr);
+    count_launch();
+    SPR_CUDA_TRY(cudaGetLastError());
     r->need_raygen = false;
+    r->pass = 0;
     return SPR_OK;
 }
 
-// one attempt of a pass with kk and nproc; counters land in h_ctr
-int pass_attempt(spr_renderer *r, cudaStream_t s, int kk, uint32_t nproc, float *stage_ms)
+__global__ void set_limit_kernel(PassState *ps, uint32_t more)
+{
+    if (threadIdx.x != 0) return;
+    ps->max_passes = ps->pass + more;
+    ps->run = (ps->n_live > 0 && more > 0) ? 1u : 0u;
+}
+
+// One attempt of a pass, entirely on the device.  Capturable: no host
+// synchronisation and no host-side scalars that change between passes.
+// With events, records ev[0..6] around the stages.
+int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphConditionalHandle h, int use_h)
 {
     const VolGeom &g = r->vol->g;
     uint32_t *ctr = r->ctr.as<uint32_t>();
     uint32_t *flags = ctr + C_SCANFLAGS;
-    const bool prof = r->profiling;
-    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
-    SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
+    PassState *ps = r->ps.as<PassState>();
+    uint32_t *live0 = r->live[0].as<uint32_t>(), *live1 = r->live[1].as<uint32_t>();
+    const int64_t cap = r->cap_entries;
+    int64_t k0 = r->launches;
+    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
+    begin_pass_kernel<<<1, 32, 0, s>>>(ps, ctr);
     SPR_CUDA_TRY(cudaMemsetAsync(r->vis_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
     SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
-    const uint32_t *live = r->live[r->cur_live].as<uint32_t>();
-    uint32_t *live_next = r->live[1 - r->cur_live].as<uint32_t>();
-    const int64_t n_ent = (int64_t)nproc * kk;
 
     // (a) traversal with speculation, marking visible and active blocks
-    traverse_kernel<<<grid_for(nproc, 128, 16), 128, 0, s>>>(
-        make_geo(r), live, nproc, kk, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
+    traverse_kernel<<<grid_for(r->npix, 128, 16), 128, 0, s>>>(
+        make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
         r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr);
-    count_launch();
+    count_launch(2);
     SPR_CUDA_TRY(cudaGetLastError());
-    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
+    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
 
     // (b) compact the marks; group the entries by visible block
     SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->nwords, nullptr,
@@ -1251,58 +1438,57 @@ int pass_attempt(spr_renderer *r, cudaStream_t s, int kk, uint32_t nproc, float 
                                  nullptr},
                         ctr + C_NACT, s));
     overflow_kernel<<<1, 32, 0, s>>>(ctr, r->n_slots);
-    count_launch(3);  // overflow check, entry count, entry scatter
-    count_entries_kernel<<<grid_for(n_ent, 256, 16), 256, 0, s>>>(
-        n_ent, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
+    count_entries_kernel<<<grid_for(cap, 256, 16), 256, 0, s>>>(
+        ps, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
         r->nbrays.as<uint32_t>(), r->erank.as<uint32_t>(), ctr);
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->cap_entries, ctr + C_NVIS,
+    count_launch(2);
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, cap, ctr + C_NVIS,
                         ArrayCount{r->nbrays.as<uint32_t>(), ctr + C_OVERFLOW},
                         ArrayEmit{r->obrays.as<uint32_t>()}, ctr + C_NENT, s));
-    scatter_entries_kernel<<<grid_for(n_ent, 256, 16), 256, 0, s>>>(
-        n_ent, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
+    scatter_entries_kernel<<<grid_for(cap, 256, 16), 256, 0, s>>>(
+        ps, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
         r->obrays.as<uint32_t>(), r->erank.as<uint32_t>(), r->E.as<uint32_t>(), ctr);
+    count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
-    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[2], s));
+    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[2], s));
 
     // (c) cache: look up, pick least recently used victims, assign
-    uint32_t *lru = r->lru[r->cur_lru].as<uint32_t>(), *lru_next = r->lru[1 - r->cur_lru].as<uint32_t>();
+    LruPair lp{r->lru[0].as<uint32_t>(), r->lru[1].as<uint32_t>(), ps};
     SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->cap_act, ctr + C_NACT,
                         LookupCount{r->iact.as<uint32_t>(), r->blk_slot.as<uint32_t>(), r->touched.as<uint8_t>(),
                                     ctr + C_OVERFLOW},
                         SelectEmit{r->iact.as<uint32_t>(), r->miss.as<uint32_t>()}, ctr + C_NMISS, s));
     SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, nullptr,
-                        VictimCount{lru, r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
-                        VictimEmit{lru, ctr + C_NMISS, r->victim.as<uint32_t>(), lru_next}, ctr + C_NUNTOUCHED,
-                        s));
+                        VictimCount{lp, r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
+                        VictimEmit{lp, ctr + C_NMISS, r->victim.as<uint32_t>()}, ctr + C_NUNTOUCHED, s));
     assign_kernel<<<grid_for(r->cap_act, 256, 8), 256, 0, s>>>(r->cap_act, r->miss.as<uint32_t>(),
                                                               r->victim.as<uint32_t>(), r->blk_slot.as<uint32_t>(),
                                                               r->slot_blk.as<uint32_t>(), r->touched.as<uint8_t>(), ctr);
     count_launch();
     SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, nullptr,
                         TouchedCount{r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
-                        TouchedEmit{r->touched.as<uint8_t>(), ctr, lru_next}, nullptr, s));
-    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[3], s));
+                        TouchedEmit{r->touched.as<uint8_t>(), ctr, lp}, nullptr, s));
+    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[3], s));
 
     // (d) decode the misses into their slots
     SPR_TRY(launch_decode_list(r->vol->comp.as<uint8_t>(), g.nblocks, g.rate, r->miss.as<uint32_t>(),
                                r->victim.as<uint32_t>(), r->cap_act, ctr + C_NMISS, ctr + C_OVERFLOW,
                                r->cache.as<float>(), ctr + C_BAD, s));
     count_launch();
-    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[4], s));
+    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[4], s));
 
     // (e) intersect the entries, block by block
     RT R{make_geo(r), r->cache.as<float>(), r->blk_slot.as<uint32_t>()};
-    intersect_kernel<<<grid_for(n_ent, 128, 16), 128, 0, s>>>(R, n_ent, r->E.as<uint32_t>(), r->rbid.as<uint32_t>(),
-                                                             live, kk, r->keys.as<unsigned long long>(), ctr);
+    intersect_kernel<<<grid_for(cap, 128, 16), 128, 0, s>>>(R, r->E.as<uint32_t>(), r->rbid.as<uint32_t>(), live0,
+                                                           live1, ps, r->keys.as<unsigned long long>(), ctr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
-    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[5], s));
+    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[5], s));
 
-    // (f) resolve hits and exits, compact the live rays in order
-    ResolveCount rc{live,
-                    nproc,
-                    kk,
-                    r->pass + 1,
+    // (f) resolve hits and exits, compact the live rays in order, end the pass
+    ResolveCount rc{live0,
+                    live1,
+                    ps,
                     g.dims[0],
                     g.dims[1],
                     g,
@@ -1317,17 +1503,13 @@ int pass_attempt(spr_renderer *r, cudaStream_t s, int kk, uint32_t nproc, float 
                     r->fb_cell.as<uint64_t>(),
                     r->fb_final.as<int32_t>(),
                     ctr};
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_live, nullptr, rc, SelectEmit{live, live_next},
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->npix, &ps->n_live, rc, LiveEmit{live0, live1, ps},
                         ctr + C_NLIVE, s));
-    if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[6], s));
-    SPR_CUDA_TRY(cudaMemcpyAsync(r->h_ctr, ctr, sizeof(uint32_t) * C_COUNT, cudaMemcpyDeviceToHost, s));
-    SPR_CUDA_TRY(cudaStreamSynchronize(s));
-    if (prof) {
-        for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&stage_ms[k], r->ev[k], r->ev[k + 1]);
-    }
-    if (r->h_ctr[C_SCANFLAGS]) return set_error(SPR_ERR_DEVICE_TIMEOUT, "a decoupled look-back wait timed out");
-    if (r->h_ctr[C_BAD] & 1u) return set_error(SPR_ERR_DEVICE_ERROR, "a kernel flagged an out-of-range block id");
-    if (r->h_ctr[C_BAD] & 2u) return set_error(SPR_ERR_DEVICE_ERROR, "a traversal exceeded its step bound");
+    end_pass_kernel<<<1, 32, 0, s>>>(ps, ctr, r->recs.as<spr_pass_stats>(), h, use_h);
+    count_launch();
+    SPR_CUDA_TRY(cudaGetLastError());
+    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[6], s));
+    r->graph_kernels = (int)(r->launches - k0);
     return SPR_OK;
 }
 
@@ -1339,74 +1521,127 @@ int check_ready(spr_renderer *r)
     return SPR_OK;
 }
 
-int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
+int prepare(spr_renderer *r, cudaStream_t s)
 {
     SPR_TRY(check_ready(r));
-    if (r->need_raygen) r->launches = 0;
+    SPR_TRY(ensure_entry_buffers(r, s));
+    SPR_TRY(ensure_scan_scratch(r, s));
+    SPR_TRY(upload_params(r, s));
+    if (r->cache_dirty) SPR_TRY(reset_cache(r, s));
+    return SPR_OK;
+}
+
+int read_state(spr_renderer *r, cudaStream_t s)
+{
+    SPR_CUDA_TRY(cudaMemcpyAsync(r->h_ps, r->ps.p, sizeof(PassState), cudaMemcpyDeviceToHost, s));
+    SPR_CUDA_TRY(cudaStreamSynchronize(s));
+    const PassState &h = *r->h_ps;
+    r->n_live = h.n_live;
+    r->n_enter = h.n_enter;
+    r->pass = (int)h.pass;
+    if (h.error & 1u) return set_error(SPR_ERR_DEVICE_TIMEOUT, "a decoupled look-back wait timed out");
+    if (h.error & 2u) return set_error(SPR_ERR_DEVICE_ERROR, "a kernel flagged an out-of-range block id");
+    if (h.error & 4u) return set_error(SPR_ERR_DEVICE_ERROR, "a traversal exceeded its step bound");
+    return SPR_OK;
+}
+
+// one pass driven from the host (used by spr_render_pass and for per-stage
+// timing): attempts until the pass completes
+int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
+{
+    SPR_TRY(prepare(r, s));
     struct Scope {
         Scope(int64_t *p) { g_launch_counter = p; }
         ~Scope() { g_launch_counter = nullptr; }
     } scope(&r->launches);
-    SPR_TRY(ensure_entry_buffers(r, s));
-    SPR_TRY(ensure_scan_scratch(r, s));
-    if (r->cache_dirty) SPR_TRY(reset_cache(r, s));
+    const bool prof = r->profiling;
     if (r->need_raygen) {
-        if (r->profiling) SPR_CUDA_TRY(cudaEventRecord(r->ev[7], s));
-        SPR_TRY(raygen(r, s));
-        if (r->profiling) {
+        r->launches = 0;
+        if (prof) SPR_CUDA_TRY(cudaEventRecord(r->ev[7], s));
+        SPR_TRY(enqueue_raygen(r, s));
+        if (prof) {
             SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
             SPR_CUDA_TRY(cudaEventSynchronize(r->ev[0]));
             cudaEventElapsedTime(&r->ms_raygen, r->ev[7], r->ev[0]);
         }
     }
+    SPR_TRY(read_state(r, s));
     spr_pass_stats st;
     memset(&st, 0, sizeof st);
-    st.n_active = r->n_live;
     st.pass = r->pass;
     if (r->n_live == 0) {
         if (out) *out = st;
         return SPR_OK;
     }
-    int k = r->spec_mode == SPR_SPEC_FIXED
-                ? r->k_fixed
-                : (int)std::max<int64_t>(1, std::min<int64_t>(r->k_max, r->npix / r->n_live));
-    int kk = k;
-    uint32_t nproc = r->n_live;
-    int retries = 0;
+    if (r->pass >= spr_renderer::kRecCap) return set_error(SPR_ERR_INVALID_ARG, "more than %d passes", spr_renderer::kRecCap);
+    set_limit_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), 1u);
+    count_launch();
     float stage_ms[6] = {0, 0, 0, 0, 0, 0};
-    for (;;) {
-        SPR_TRY(pass_attempt(r, s, kk, nproc, stage_ms));
-        if (!r->h_ctr[C_OVERFLOW]) break;
-        ++retries;
-        if (kk > 1) kk /= 2;
-        else nproc = nproc > 1 ? nproc / 2 : 1;
+    const int before = r->pass;
+    for (int attempt = 0; attempt < 64 && r->pass == before; ++attempt) {
+        SPR_TRY(enqueue_attempt(r, s, prof, 0, 0));
+        SPR_TRY(read_state(r, s));
+        if (prof)
+            for (int k = 0; k < 6; ++k) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, r->ev[k], r->ev[k + 1]);
+                stage_ms[k] += ms;
+            }
     }
-    const uint32_t *h = r->h_ctr;
-    r->cur_lru = 1 - r->cur_lru;
-    r->cur_live = 1 - r->cur_live;
-    r->pass += 1;
-    st.pass = r->pass;
-    st.k = k;
-    st.k_used = kk;
-    st.retries = retries;
-    st.n_processed = nproc;
-    st.n_entries = h[C_NENT];
-    st.n_visible = h[C_NVIS];
-    st.n_requested = h[C_NACT];
-    st.n_decoded = h[C_NMISS];
-    st.n_evicted = h[C_EVICT];
-    st.n_term_hit = h[C_HIT];
-    st.n_term_miss = h[C_MISSRAY];
-    st.n_active_after = h[C_NLIVE];
-    st.utilization = (double)st.n_entries / (double)r->npix;
+    if (r->pass == before) return set_error(SPR_ERR_DEVICE_ERROR, "a pass did not fit the cache after 64 attempts");
+    SPR_CUDA_TRY(cudaMemcpyAsync(&st, r->recs.as<spr_pass_stats>() + before, sizeof st, cudaMemcpyDeviceToHost, s));
+    SPR_CUDA_TRY(cudaStreamSynchronize(s));
     float tot = 0.f;
     for (int i = 0; i < 6; ++i) {
         st.ms_stage[i] = stage_ms[i];
         tot += stage_ms[i];
     }
     st.ms = tot;
-    r->n_live = h[C_NLIVE];
     if (out) *out = st;
+    return SPR_OK;
+}
+
+// Capture the pass loop once: a conditional while node whose body is one
+// attempt; end_pass_kernel sets the condition.
+int build_graph(spr_renderer *r)
+{
+    if (r->gexec) return SPR_OK;
+    if (!r->cap_stream) SPR_CUDA_TRY(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    SPR_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_error(SPR_ERR_CUDA, "conditional graph node: %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(r->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    int rc = SPR_OK;
+    int64_t saved = r->launches;
+    if (e == cudaSuccess) rc = enqueue_attempt(r, r->cap_stream, false, h, 1);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(r->cap_stream, &captured);
+    r->launches = saved;
+    if (e != cudaSuccess || e2 != cudaSuccess || rc != SPR_OK) {
+        cudaGraphDestroy(g);
+        if (rc != SPR_OK) return rc;
+        return set_error(SPR_ERR_CUDA, "pass capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&r->gexec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        r->gexec = nullptr;
+        return set_error(SPR_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    r->graph = g;
     return SPR_OK;
 }
 
@@ -1438,12 +1673,17 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         (rc = buf_alloc(r->act_bits, 4 * r->nwords, s)) || (rc = buf_alloc(r->vis_wpre, 4 * r->nwords, s)) ||
         (rc = buf_alloc(r->act_wpre, 4 * r->nwords, s)) ||
         (rc = buf_alloc(r->blk_slot, 4 * vol->g.nblocks, s)) || (rc = buf_alloc(r->scan_ticket, 64, s)) ||
-        (rc = buf_alloc(r->ctr, sizeof(uint32_t) * C_COUNT, s))) {
+        (rc = buf_alloc(r->ctr, sizeof(uint32_t) * C_COUNT, s)) ||
+        (rc = buf_alloc(r->ps, sizeof(PassState), s)) ||
+        (rc = buf_alloc(r->recs, sizeof(spr_pass_stats) * spr_renderer::kRecCap, s)) ||
+        (rc = buf_alloc(r->camd, sizeof(Cam) + 16, s))) {
         free_all(r);
         delete r;
         return rc;
     }
-    if (cudaMallocHost((void **)&r->h_ctr, sizeof(uint32_t) * C_COUNT) != cudaSuccess) {
+    if (cudaMemset(r->ps.p, 0, sizeof(PassState)) != cudaSuccess ||
+        cudaMallocHost((void **)&r->h_ctr, sizeof(uint32_t) * C_COUNT) != cudaSuccess ||
+        cudaMallocHost((void **)&r->h_ps, sizeof(PassState)) != cudaSuccess) {
         free_all(r);
         delete r;
         return set_error(SPR_ERR_OUT_OF_MEMORY, "pinned host allocation failed");
@@ -1510,6 +1750,7 @@ extern "C" int spr_set_camera(spr_renderer *r, const float eye[3], const float p
     }
     r->has_cam = true;
     r->need_raygen = true;
+    r->params_dirty = true;
     return SPR_OK;
 }
 
@@ -1519,6 +1760,7 @@ extern "C" int spr_set_isovalue(spr_renderer *r, float iso)
     if (!r || !std::isfinite(iso)) return set_error(SPR_ERR_INVALID_ARG, "bad isovalue");
     r->iso = iso;
     r->need_raygen = true;
+    r->params_dirty = true;
     return SPR_OK;
 }
 
@@ -1531,6 +1773,7 @@ extern "C" int spr_set_cache_budget(spr_renderer *r, size_t bytes)
     if (slots > 0x7FFFFFFFll) return set_error(SPR_ERR_INVALID_ARG, "cache budget too large");
     cudaStream_t s = nullptr;
     cudaDeviceSynchronize();
+    drop_graph(r);
     buf_free(r->cache, s);
     buf_free(r->slot_blk, s);
     buf_free(r->lru[0], s);
@@ -1566,6 +1809,7 @@ extern "C" int spr_set_speculation(spr_renderer *r, int mode, int k, int k_max)
     }
     r->spec_mode = mode;
     r->need_raygen = true;
+    r->params_dirty = true;
     return SPR_OK;
 }
 
@@ -1600,28 +1844,77 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
     cudaStream_t s = as_stream(stream);
     spr_render_stats rs;
     memset(&rs, 0, sizeof rs);
-    bool fresh = r->need_raygen;
+    const bool fresh = r->need_raygen;
     int passes = 0;
     float ms = 0.f;
-    while (passes < max_passes) {
-        spr_pass_stats st;
-        SPR_TRY(do_pass(r, s, &st));
-        if (st.n_active == 0) break;
-        if (per_pass) per_pass[passes] = st;
-        ++passes;
-        rs.blocks_decoded += st.n_decoded;
-        rs.entries += st.n_entries;
-        rs.evictions += st.n_evicted;
-        rs.n_hits += st.n_term_hit;
-        ms += st.ms;
-        if (r->n_live == 0) break;
+    if (r->profiling) {
+        // host-driven passes with per-stage CUDA events
+        while (passes < max_passes) {
+            spr_pass_stats st;
+            SPR_TRY(do_pass(r, s, &st));
+            if (st.n_active == 0) break;
+            if (per_pass) per_pass[passes] = st;
+            ++passes;
+            rs.blocks_decoded += st.n_decoded;
+            rs.entries += st.n_entries;
+            rs.evictions += st.n_evicted;
+            rs.n_hits += st.n_term_hit;
+            ms += st.ms;
+            if (r->n_live == 0) break;
+        }
+        rs.ms_raygen = fresh ? r->ms_raygen : 0.f;
+        rs.ms_total = ms + rs.ms_raygen;
+    } else {
+        // the whole render on the device: ray generation, then one graph
+        // launch whose while node runs passes until none is live
+        SPR_TRY(prepare(r, s));
+        struct Scope {
+            Scope(int64_t *p) { g_launch_counter = p; }
+            ~Scope() { g_launch_counter = nullptr; }
+        } scope(&r->launches);
+        SPR_CUDA_TRY(cudaEventRecord(r->ev[7], s));
+        if (fresh) {
+            r->launches = 0;
+            SPR_TRY(enqueue_raygen(r, s));
+        }
+        SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
+        SPR_TRY(build_graph(r));
+        int first = r->pass;
+        int more = std::min(max_passes, spr_renderer::kRecCap - first);
+        if (more < 1) return set_error(SPR_ERR_INVALID_ARG, "more than %d passes", spr_renderer::kRecCap);
+        set_limit_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), (uint32_t)more);
+        count_launch();
+        SPR_CUDA_TRY(cudaGraphLaunch(r->gexec, s));
+        SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
+        SPR_TRY(read_state(r, s));
+        passes = r->pass - first;
+        spr_pass_stats *recs = per_pass;
+        spr_pass_stats tmp[64];
+        if (!recs && passes <= 64) recs = tmp;
+        int64_t attempts = passes;
+        if (recs && passes > 0) {
+            SPR_CUDA_TRY(cudaMemcpyAsync(recs, r->recs.as<spr_pass_stats>() + first, sizeof(spr_pass_stats) * passes,
+                                         cudaMemcpyDeviceToHost, s));
+            SPR_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int i = 0; i < passes; ++i) {
+                rs.blocks_decoded += recs[i].n_decoded;
+                rs.entries += recs[i].n_entries;
+                rs.evictions += recs[i].n_evicted;
+                rs.n_hits += recs[i].n_term_hit;
+                attempts += recs[i].retries;
+            }
+        }
+        r->launches += (int64_t)r->graph_kernels * std::max<int64_t>(attempts, 1);
+        float t_all = 0.f, t_ray = 0.f;
+        cudaEventElapsedTime(&t_all, r->ev[7], r->ev[0]);
+        cudaEventElapsedTime(&t_ray, r->ev[7], r->ev[1]);
+        rs.ms_raygen = fresh ? t_ray : 0.f;
+        rs.ms_total = t_all;
     }
     rs.passes = passes;
     rs.n_rays = r->n_enter;
     rs.converged = r->n_live == 0;
     rs.bytes_decoded = rs.blocks_decoded * 256;
-    rs.ms_raygen = fresh ? r->ms_raygen : 0.f;
-    rs.ms_total = ms + rs.ms_raygen;
     rs.kernel_launches = r->launches;
     if (out) *out = rs;
     if (!rs.converged) return set_error(SPR_ERR_NOT_CONVERGED, "%d passes left rays live", passes);

@@ -273,3 +273,55 @@ def test_allocator_cap_gives_out_of_memory(spr, orc):
     finally:
         spr.spr_set_allocator()
     assert used["n"] == 0
+
+
+def test_graph_and_host_driven_passes_agree(spr, orc):
+    """The whole-render graph (a conditional while node over passes) and the
+    host-driven passes used for per-stage timing give identical images and
+    per-pass counters."""
+    import torch
+    sc = value_scene(orc, (40, 36, 44), 41, 96, 80, rate=4, q=0.6)
+    out = []
+    for prof in (False, True, False):
+        v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+        r = spr.spr_create_renderer(v, sc.W, sc.H)
+        spr.spr_set_camera(r, sc.cam)
+        spr.spr_set_isovalue(r, sc.iso)
+        spr.spr_set_cache_budget(r, 256 * 60)
+        spr.spr_set_speculation(r, spr.SPR_SPEC_FIXED, k=6)
+        spr.spr_set_profiling(r, prof)
+        rs, passes = spr.spr_render_to_convergence(r, 10000)
+        out.append((spr.spr_read_framebuffer(r), rs, passes))
+        r.close()
+        v.close()
+    compare(sc, out[0][0])
+    for fb, rs, passes in out[1:]:
+        for key in fb:
+            assert np.array_equal(fb[key], out[0][0][key]), key
+        assert len(passes) == len(out[0][2])
+        for a, b in zip(passes, out[0][2]):
+            for name in ("n_active", "k_used", "n_entries", "n_visible", "n_requested",
+                         "n_decoded", "n_evicted", "n_term_hit", "n_term_miss", "retries"):
+                assert a[name] == b[name], name
+    assert out[0][1]["passes"] > 2
+
+
+def test_progressive_single_passes_then_graph(spr, orc):
+    """spr_render_pass twice, then spr_render_to_convergence finishes the same
+    render: the image equals a one-call render."""
+    import torch
+    sc = value_scene(orc, (32, 30, 28), 43, 64, 64, rate=8, q=0.6)
+    v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    r = spr.spr_create_renderer(v, sc.W, sc.H)
+    spr.spr_set_camera(r, sc.cam)
+    spr.spr_set_isovalue(r, sc.iso)
+    spr.spr_set_speculation(r, spr.SPR_SPEC_FIXED, k=1)
+    p1 = spr.spr_render_pass(r)
+    p2 = spr.spr_render_pass(r)
+    assert p1["pass"] == 1 and p2["pass"] == 2
+    rs, passes = spr.spr_render_to_convergence(r, 10000)
+    assert passes[0]["pass"] == 3
+    fb = spr.spr_read_framebuffer(r)
+    r.close()
+    v.close()
+    compare(sc, fb)
