@@ -163,6 +163,8 @@ typedef struct {
     double  utilization;    /* n_entries / (w*h) (Table 2)                      */
     float   ms;             /* device time of the pass (profiling on, else 0)   */
     float   ms_stage[6];    /* traverse, group, cache, decode, intersect, resolve*/
+    int64_t n_steps;        /* block and skip steps of all walks in the pass    */
+    int64_t max_steps;      /* steps of the longest walk in the pass            */
 } spr_pass_stats;
 
 typedef struct {
@@ -225,8 +227,11 @@ int spr_set_profiling(spr_renderer *r, int on);
 int spr_render_pass(spr_renderer *r, spr_stream stream, spr_pass_stats *out);
 
 /* Run passes until no ray is live or max_passes passes ran (then
- * SPR_ERR_NOT_CONVERGED, with the partial image valid).  per_pass (may be
- * NULL) receives up to max_passes records.  out may be NULL. */
+ * SPR_ERR_NOT_CONVERGED, with the partial image valid).  Without profiling
+ * the whole render is one CUDA graph launch (a conditional while node over
+ * passes) and the host waits once at the end.  per_pass (may be NULL)
+ * receives one record per pass, for the first 4096 passes since ray
+ * generation; the totals in out cover every pass.  out may be NULL. */
 int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int max_passes,
                               spr_render_stats *out, spr_pass_stats *per_pass);
 

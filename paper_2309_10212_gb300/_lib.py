@@ -47,7 +47,8 @@ class PassStats(ctypes.Structure):
                 ("n_decoded", ctypes.c_int64), ("n_evicted", ctypes.c_int64),
                 ("n_term_hit", ctypes.c_int64), ("n_term_miss", ctypes.c_int64),
                 ("n_active_after", ctypes.c_int64), ("utilization", ctypes.c_double),
-                ("ms", ctypes.c_float), ("ms_stage", ctypes.c_float * 6)]
+                ("ms", ctypes.c_float), ("ms_stage", ctypes.c_float * 6),
+                ("n_steps", ctypes.c_int64), ("max_steps", ctypes.c_int64)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "ms_stage"}

@@ -245,12 +245,12 @@ def spr_render_to_convergence(r: Renderer, max_passes: int = 10000, stream=None,
                               allow_partial: bool = False):
     """Returns (render stats, [pass stats])."""
     rs = _lib.RenderStats()
-    per = (_lib.PassStats * max_passes)()
+    per = (_lib.PassStats * min(max_passes, 4096))()
     status = load().spr_render_to_convergence(r.handle, _stream(stream), int(max_passes),
                                               ctypes.byref(rs), per)
     if not (allow_partial and status == _lib.SPR_ERR_NOT_CONVERGED):
         check(status)
-    return rs.as_dict(), [per[i].as_dict() for i in range(rs.passes)]
+    return rs.as_dict(), [per[i].as_dict() for i in range(min(rs.passes, max_passes, 4096))]
 
 
 def spr_get_framebuffer(r: Renderer) -> dict:

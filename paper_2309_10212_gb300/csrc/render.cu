@@ -51,6 +51,8 @@ enum Ctr {
     C_MISSRAY,
     C_SCANFLAGS,
     C_BAD,
+    C_STEPS,     // walk steps of all rays this pass
+    C_MAXSTEPS,  // longest walk this pass
     C_COUNT = 16
 };
 
@@ -72,6 +74,8 @@ struct PassState {
     uint32_t spec_mode, k_fixed, k_max;
     uint32_t npix;
     uint32_t n_enter;     // rays that entered the volume at ray generation
+    uint32_t attempts;    // pass attempts since ray generation (retries included)
+    unsigned long long tot_decoded, tot_entries, tot_evicted, tot_hits;
 };
 
 struct Cam {
@@ -488,6 +492,12 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
         if (!alive) flags |= kDone;
         for (int j = cnt; j < kk; ++j) out[j] = kNone;
         state_out[ray] = pack_state(w.b, flags);
+        warp_add(&ctr[C_STEPS], (uint32_t)steps);
+        {
+            unsigned m = __activemask();
+            uint32_t mx = __reduce_max_sync(m, (uint32_t)steps);
+            if ((threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicMax(&ctr[C_MAXSTEPS], mx);
+        }
     }
 }
 
@@ -1107,10 +1117,11 @@ __global__ void begin_pass_kernel(PassState *ps, uint32_t *ctr)
     }
 }
 
-__global__ void end_pass_kernel(PassState *ps, const uint32_t *ctr, spr_pass_stats *recs,
+__global__ void end_pass_kernel(PassState *ps, const uint32_t *ctr, spr_pass_stats *recs, uint32_t n_recs,
                                 cudaGraphConditionalHandle handle, int use_handle)
 {
     if (threadIdx.x != 0) return;
+    if (ps->n_live > 0) ps->attempts += 1;
     if (ctr[C_SCANFLAGS] || ctr[C_BAD]) {
         ps->error = (ctr[C_SCANFLAGS] ? 1u : 0u) | (ctr[C_BAD] << 1);
         ps->run = 0;
@@ -1122,7 +1133,11 @@ __global__ void end_pass_kernel(PassState *ps, const uint32_t *ctr, spr_pass_sta
         if (ps->kk > 1) ps->kk /= 2;
         else ps->nproc = max(1u, ps->nproc / 2);
     } else {
-        if (ps->pass < ps->max_passes) {
+        ps->tot_decoded += ctr[C_NMISS];
+        ps->tot_entries += ctr[C_NENT];
+        ps->tot_evicted += ctr[C_EVICT];
+        ps->tot_hits += ctr[C_HIT];
+        if (ps->pass < n_recs) {
             spr_pass_stats st{};
             st.pass = (int32_t)ps->pass + 1;
             st.k = (int32_t)ps->k;
@@ -1139,6 +1154,8 @@ __global__ void end_pass_kernel(PassState *ps, const uint32_t *ctr, spr_pass_sta
             st.n_term_miss = ctr[C_MISSRAY];
             st.n_active_after = ctr[C_NLIVE];
             st.utilization = (double)ctr[C_NENT] / (double)ps->npix;
+            st.n_steps = ctr[C_STEPS];
+            st.max_steps = ctr[C_MAXSTEPS];
             recs[ps->pass] = st;
         }
         ps->pass += 1;
@@ -1169,6 +1186,8 @@ __global__ void after_raygen_kernel(PassState *ps, const uint32_t *ctr)
     ps->parity &= ~1u;
     ps->open = 0;
     ps->retries = 0;
+    ps->attempts = 0;
+    ps->tot_decoded = ps->tot_entries = ps->tot_evicted = ps->tot_hits = 0ull;
     ps->error = ctr[C_SCANFLAGS] ? 1u : 0u;
     ps->run = ps->n_live > 0 ? 1u : 0u;
 }
@@ -1505,7 +1524,8 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
                     ctr};
     SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->npix, &ps->n_live, rc, LiveEmit{live0, live1, ps},
                         ctr + C_NLIVE, s));
-    end_pass_kernel<<<1, 32, 0, s>>>(ps, ctr, r->recs.as<spr_pass_stats>(), h, use_h);
+    end_pass_kernel<<<1, 32, 0, s>>>(ps, ctr, r->recs.as<spr_pass_stats>(), (uint32_t)spr_renderer::kRecCap, h,
+                                     use_h);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[6], s));
@@ -1573,7 +1593,6 @@ int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
         if (out) *out = st;
         return SPR_OK;
     }
-    if (r->pass >= spr_renderer::kRecCap) return set_error(SPR_ERR_INVALID_ARG, "more than %d passes", spr_renderer::kRecCap);
     set_limit_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), 1u);
     count_launch();
     float stage_ms[6] = {0, 0, 0, 0, 0, 0};
@@ -1589,8 +1608,12 @@ int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
             }
     }
     if (r->pass == before) return set_error(SPR_ERR_DEVICE_ERROR, "a pass did not fit the cache after 64 attempts");
-    SPR_CUDA_TRY(cudaMemcpyAsync(&st, r->recs.as<spr_pass_stats>() + before, sizeof st, cudaMemcpyDeviceToHost, s));
-    SPR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (before < spr_renderer::kRecCap) {
+        SPR_CUDA_TRY(cudaMemcpyAsync(&st, r->recs.as<spr_pass_stats>() + before, sizeof st, cudaMemcpyDeviceToHost, s));
+        SPR_CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+        st.pass = before + 1;   // past the record buffer: counts only in the render totals
+    }
     float tot = 0.f;
     for (int i = 0; i < 6; ++i) {
         st.ms_stage[i] = stage_ms[i];
@@ -1853,7 +1876,7 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
             spr_pass_stats st;
             SPR_TRY(do_pass(r, s, &st));
             if (st.n_active == 0) break;
-            if (per_pass) per_pass[passes] = st;
+            if (per_pass && st.pass <= spr_renderer::kRecCap) per_pass[passes] = st;
             ++passes;
             rs.blocks_decoded += st.n_decoded;
             rs.entries += st.n_entries;
@@ -1880,29 +1903,25 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
         SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
         SPR_TRY(build_graph(r));
         int first = r->pass;
-        int more = std::min(max_passes, spr_renderer::kRecCap - first);
-        if (more < 1) return set_error(SPR_ERR_INVALID_ARG, "more than %d passes", spr_renderer::kRecCap);
-        set_limit_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), (uint32_t)more);
+        const PassState before = *r->h_ps;
+        set_limit_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), (uint32_t)max_passes);
         count_launch();
         SPR_CUDA_TRY(cudaGraphLaunch(r->gexec, s));
         SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
         SPR_TRY(read_state(r, s));
         passes = r->pass - first;
-        spr_pass_stats *recs = per_pass;
-        spr_pass_stats tmp[64];
-        if (!recs && passes <= 64) recs = tmp;
-        int64_t attempts = passes;
-        if (recs && passes > 0) {
-            SPR_CUDA_TRY(cudaMemcpyAsync(recs, r->recs.as<spr_pass_stats>() + first, sizeof(spr_pass_stats) * passes,
+        const PassState &after = *r->h_ps;
+        const bool same = !fresh;   // totals restart at ray generation
+        rs.blocks_decoded = (int64_t)(after.tot_decoded - (same ? before.tot_decoded : 0));
+        rs.entries = (int64_t)(after.tot_entries - (same ? before.tot_entries : 0));
+        rs.evictions = (int64_t)(after.tot_evicted - (same ? before.tot_evicted : 0));
+        rs.n_hits = (int64_t)(after.tot_hits - (same ? before.tot_hits : 0));
+        int64_t attempts = (int64_t)after.attempts - (same ? (int64_t)before.attempts : 0);
+        int nrec = std::max(0, std::min(first + passes, spr_renderer::kRecCap) - first);
+        if (per_pass && nrec > 0) {
+            SPR_CUDA_TRY(cudaMemcpyAsync(per_pass, r->recs.as<spr_pass_stats>() + first, sizeof(spr_pass_stats) * nrec,
                                          cudaMemcpyDeviceToHost, s));
             SPR_CUDA_TRY(cudaStreamSynchronize(s));
-            for (int i = 0; i < passes; ++i) {
-                rs.blocks_decoded += recs[i].n_decoded;
-                rs.entries += recs[i].n_entries;
-                rs.evictions += recs[i].n_evicted;
-                rs.n_hits += recs[i].n_term_hit;
-                attempts += recs[i].retries;
-            }
         }
         r->launches += (int64_t)r->graph_kernels * std::max<int64_t>(attempts, 1);
         float t_all = 0.f, t_ray = 0.f;
