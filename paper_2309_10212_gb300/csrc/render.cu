@@ -53,6 +53,7 @@ enum Ctr {
     C_BAD,
     C_STEPS,     // walk steps of all rays this pass
     C_MAXSTEPS,  // longest walk this pass
+    C_NEEDUSED,  // victims taken from the used-slot list (the rest are fresh slots)
     C_COUNT = 16
 };
 
@@ -75,6 +76,10 @@ struct PassState {
     uint32_t npix;
     uint32_t n_enter;     // rays that entered the volume at ray generation
     uint32_t attempts;    // pass attempts since ray generation (retries included)
+    // LRU cache: slots >= fresh_lo were never used (handed out in increasing
+    // order, they are the least recently used); the used ones are listed, least
+    // recently used first, in the list selected by parity bit 1
+    uint32_t fresh_lo, fresh_hi, n_used;
     unsigned long long tot_decoded, tot_entries, tot_evicted, tot_hits;
 };
 
@@ -528,10 +533,6 @@ struct BitsEmit {
     }
 };
 
-__global__ void overflow_kernel(uint32_t *ctr, int64_t n_slots)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) ctr[C_OVERFLOW] = (int64_t)ctr[C_NACT] > n_slots ? 1u : 0u;
-}
 
 __device__ __forceinline__ uint32_t vis_rank(const uint32_t *bits, const uint32_t *wpre, uint32_t b)
 {
@@ -612,6 +613,13 @@ struct LruPair {
     __device__ uint32_t *next() const { return (ps->parity & 2) ? l0 : l1; }
 };
 
+// misses served from never-used slots; the rest come from the used list
+__device__ __forceinline__ uint32_t fresh_taken(const PassState *ps, const uint32_t *ctr, uint32_t n_slots)
+{
+    return min(ctr[C_NMISS], n_slots - ps->fresh_lo);
+}
+
+// untouched used slots in LRU order: the first ones become victims
 struct VictimCount {
     LruPair lru;
     const uint8_t *touched;
@@ -622,25 +630,38 @@ struct VictimCount {
 
 struct VictimEmit {
     LruPair lru;
-    const uint32_t *n_miss;
+    const uint32_t *ctr;
     uint32_t *victim;
+    uint32_t n_slots;
     __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
     {
         if (!c) return;
-        uint32_t nm = *n_miss;
-        uint32_t slot = lru.cur()[i];
-        if (pre < nm) victim[pre] = slot;
-        else lru.next()[pre - nm] = slot;
+        const uint32_t nf = fresh_taken(lru.ps, ctr, n_slots);
+        const uint32_t need = ctr[C_NMISS] - nf;
+        const uint32_t slot = lru.cur()[i];
+        if (pre < need) victim[nf + pre] = slot;
+        else lru.next()[pre - need] = slot;
     }
 };
 
-__global__ void assign_kernel(int64_t cap, const uint32_t *__restrict__ miss, const uint32_t *__restrict__ victim,
-                              uint32_t *blk_slot, uint32_t *slot_blk, uint8_t *touched, uint32_t *ctr)
+__global__ void assign_kernel(const uint32_t *__restrict__ miss, uint32_t *__restrict__ victim, uint32_t *blk_slot,
+                              uint32_t *slot_blk, uint8_t *touched, uint32_t *ctr, PassState *ps, uint32_t n_slots)
 {
     if (ctr[C_OVERFLOW]) return;
+    const uint32_t nf = fresh_taken(ps, ctr, n_slots);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ps->fresh_hi = ps->fresh_lo + nf;
+        ctr[C_NEEDUSED] = ctr[C_NMISS] - nf;
+    }
     const int64_t n = ctr[C_NMISS];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t s = victim[i];
+        uint32_t s;
+        if (i < nf) {
+            s = ps->fresh_lo + (uint32_t)i;
+            victim[i] = s;
+        } else {
+            s = victim[i];
+        }
         uint32_t old = slot_blk[s];
         uint32_t ev = 0;
         if (old != kNone) {
@@ -662,6 +683,7 @@ struct TouchedCount {
     __device__ uint32_t operator()(int64_t s) const { return touched[s] ? 1u : 0u; }
 };
 
+// touched slots (hits and victims), all below fresh_hi, appended in slot order
 struct TouchedEmit {
     uint8_t *touched;
     const uint32_t *ctr;
@@ -669,7 +691,7 @@ struct TouchedEmit {
     __device__ void operator()(int64_t s, uint32_t pre, uint32_t c) const
     {
         if (!c) return;
-        lru.next()[ctr[C_NUNTOUCHED] - ctr[C_NMISS] + pre] = (uint32_t)s;
+        lru.next()[ctr[C_NUNTOUCHED] - ctr[C_NEEDUSED] + pre] = (uint32_t)s;
         touched[s] = 0;
     }
 };
@@ -1158,6 +1180,8 @@ __global__ void end_pass_kernel(PassState *ps, const uint32_t *ctr, spr_pass_sta
             st.max_steps = ctr[C_MAXSTEPS];
             recs[ps->pass] = st;
         }
+        ps->n_used += ps->fresh_hi - ps->fresh_lo;
+        ps->fresh_lo = ps->fresh_hi;
         ps->pass += 1;
         ps->parity ^= 3u;
         ps->n_live = ctr[C_NLIVE];
@@ -1165,6 +1189,13 @@ __global__ void end_pass_kernel(PassState *ps, const uint32_t *ctr, spr_pass_sta
         ps->run = (ps->n_live > 0 && ps->pass < ps->max_passes) ? 1u : 0u;
     }
     if (use_handle) cudaGraphSetConditional(handle, ps->run);
+}
+
+__global__ void cache_reset_kernel(PassState *ps)
+{
+    if (threadIdx.x != 0) return;
+    ps->fresh_lo = ps->fresh_hi = 0;
+    ps->n_used = 0;
 }
 
 __global__ void config_kernel(PassState *ps, uint32_t spec_mode, uint32_t k_fixed, uint32_t k_max, uint32_t npix)
@@ -1202,14 +1233,14 @@ inline void count_launch(int n = 1)
 template <class CF, class EF>
 int run_compact(DevBuf &status, DevBuf &ticket, uint32_t *flags, int64_t n_cap, const uint32_t *n_dev,
                 CF cf, EF ef, uint32_t *total, cudaStream_t s, int64_t spin = kDefaultSpinLimit,
-                int64_t withhold = -1)
+                int64_t withhold = -1, uint32_t *over = nullptr, uint32_t over_limit = 0)
 {
     int64_t tiles = std::max<int64_t>(1, scan_tiles(n_cap));
     if ((size_t)tiles * sizeof(unsigned long long) > status.bytes)
         return set_error(SPR_ERR_INVALID_ARG, "scan of %lld items exceeds its scratch", (long long)n_cap);
     SPR_CUDA_TRY(cudaMemsetAsync(status.p, 0, (size_t)tiles * sizeof(unsigned long long), s));
     SPR_CUDA_TRY(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned int), s));
-    ScanCtl ctl{status.as<unsigned long long>(), ticket.as<unsigned int>(), flags, spin, withhold};
+    ScanCtl ctl{status.as<unsigned long long>(), ticket.as<unsigned int>(), flags, spin, withhold, over, over_limit};
     compact_kernel<CF, EF><<<(unsigned)tiles, kScanThreads, 0, s>>>(n_cap, n_dev, ctl, cf, ef, total);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
@@ -1338,10 +1369,9 @@ int reset_cache(spr_renderer *r, cudaStream_t s)
     SPR_CUDA_TRY(cudaMemsetAsync(r->blk_slot.p, 0xFF, sizeof(uint32_t) * g.nblocks, s));
     SPR_CUDA_TRY(cudaMemsetAsync(r->slot_blk.p, 0xFF, sizeof(uint32_t) * r->n_slots, s));
     SPR_CUDA_TRY(cudaMemsetAsync(r->touched.p, 0, r->n_slots, s));
-    // both LRU lists start as the identity, so either parity holds it
-    lru_init_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, s>>>(r->lru[0].as<uint32_t>(), r->n_slots);
-    lru_init_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, s>>>(r->lru[1].as<uint32_t>(), r->n_slots);
-    count_launch(2);
+    // every slot is fresh again; the used-slot lists are empty
+    cache_reset_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>());
+    count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     r->cache_dirty = false;
     return SPR_OK;
@@ -1455,12 +1485,11 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
                         BitsCount{r->act_bits.as<uint32_t>(), nullptr},
                         BitsEmit{r->act_bits.as<uint32_t>(), r->act_wpre.as<uint32_t>(), r->iact.as<uint32_t>(),
                                  nullptr},
-                        ctr + C_NACT, s));
-    overflow_kernel<<<1, 32, 0, s>>>(ctr, r->n_slots);
+                        ctr + C_NACT, s, kDefaultSpinLimit, -1, ctr + C_OVERFLOW, (uint32_t)r->n_slots));
     count_entries_kernel<<<grid_for(cap, 256, 16), 256, 0, s>>>(
         ps, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
         r->nbrays.as<uint32_t>(), r->erank.as<uint32_t>(), ctr);
-    count_launch(2);
+    count_launch();
     SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, cap, ctr + C_NVIS,
                         ArrayCount{r->nbrays.as<uint32_t>(), ctr + C_OVERFLOW},
                         ArrayEmit{r->obrays.as<uint32_t>()}, ctr + C_NENT, s));
@@ -1477,14 +1506,14 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
                         LookupCount{r->iact.as<uint32_t>(), r->blk_slot.as<uint32_t>(), r->touched.as<uint8_t>(),
                                     ctr + C_OVERFLOW},
                         SelectEmit{r->iact.as<uint32_t>(), r->miss.as<uint32_t>()}, ctr + C_NMISS, s));
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, nullptr,
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, &ps->n_used,
                         VictimCount{lp, r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
-                        VictimEmit{lp, ctr + C_NMISS, r->victim.as<uint32_t>()}, ctr + C_NUNTOUCHED, s));
-    assign_kernel<<<grid_for(r->cap_act, 256, 8), 256, 0, s>>>(r->cap_act, r->miss.as<uint32_t>(),
-                                                              r->victim.as<uint32_t>(), r->blk_slot.as<uint32_t>(),
-                                                              r->slot_blk.as<uint32_t>(), r->touched.as<uint8_t>(), ctr);
+                        VictimEmit{lp, ctr, r->victim.as<uint32_t>(), (uint32_t)r->n_slots}, ctr + C_NUNTOUCHED, s));
+    assign_kernel<<<grid_for(r->cap_act, 256, 8), 256, 0, s>>>(r->miss.as<uint32_t>(), r->victim.as<uint32_t>(),
+                                                              r->blk_slot.as<uint32_t>(), r->slot_blk.as<uint32_t>(),
+                                                              r->touched.as<uint8_t>(), ctr, ps, (uint32_t)r->n_slots);
     count_launch();
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, nullptr,
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, &ps->fresh_hi,
                         TouchedCount{r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
                         TouchedEmit{r->touched.as<uint8_t>(), ctr, lp}, nullptr, s));
     if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[3], s));

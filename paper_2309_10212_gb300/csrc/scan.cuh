@@ -27,6 +27,8 @@ struct ScanCtl {
     unsigned int *flags;         // bit 0: a wait timed out
     int64_t spin_limit;
     int64_t withhold;            // test hook: this tile never publishes (-1: none)
+    uint32_t *over;              // optional: set to (total > over_limit) with the total
+    uint32_t over_limit;
 };
 
 constexpr unsigned long long kAgg = 1ull << 62;
@@ -60,7 +62,10 @@ __global__ void __launch_bounds__(kScanThreads)
     if (!count.enabled()) return;
     const int64_t base = tile * kScanTile;
     if (base >= n) {  // nobody waits on tiles past the end
-        if (tile == 0 && tid == 0 && total) *total = 0u;
+        if (tile == 0 && tid == 0) {
+            if (total) *total = 0u;
+            if (ctl.over) *ctl.over = 0u;
+        }
         return;
     }
 
@@ -130,7 +135,10 @@ __global__ void __launch_bounds__(kScanThreads)
             if (publish_ok) publish(&ctl.status[tile], kInc | (uint32_t)(prefix + total_tile));
         }
         s_prefix = prefix;
-        if (total && base + kScanTile >= n) *total = prefix + total_tile;
+        if (base + kScanTile >= n) {
+            if (total) *total = prefix + total_tile;
+            if (ctl.over) *ctl.over = (prefix + total_tile) > ctl.over_limit ? 1u : 0u;
+        }
     }
     __syncthreads();
     uint32_t run = s_prefix + excl;
