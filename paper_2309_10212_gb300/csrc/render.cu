@@ -210,11 +210,20 @@ __device__ __forceinline__ int cmp_plane(const Walk &w, int a, float X, Tq T, fl
     return exact_sign_diff(tx.n, T.ad, T.n, tx.ad);
 }
 
-// block index along axis a containing p(T+), known to lie in [lo, hi]
+// block index along axis a containing p(T+), known to lie in [lo, hi].  The
+// single-precision position p = e + T d is within tol of the true one; when
+// it is farther than tol from every block plane its floor is certain,
+// otherwise exact plane tests decide.
 __device__ __forceinline__ int locate_in(const Walk &w, int a, Tq T, float Tv, int lo, int hi)
 {
     float p = fmaf(Tv, w.r.d[a], w.r.e[a]);
     float q = fminf(fmaxf(__fmul_rn(p, 0.25f), (float)lo - 1.f), (float)hi + 1.f);
+    {
+        float fq = floorf(q), frac = q - fq;
+        float tol = (fabsf(Tv * w.r.d[a]) + fabsf(w.r.e[a])) * 1e-6f + 1e-6f;
+        int b = (int)fq;
+        if (frac > tol && frac < 1.f - tol && b >= lo && b <= hi) return b;
+    }
     int b;
     if (w.r.sgn[a] > 0) {
         b = min(max((int)floorf(q), lo), hi);
@@ -234,11 +243,12 @@ __device__ __forceinline__ int locate_in(const Walk &w, int a, Tq T, float Tv, i
 __device__ __forceinline__ bool skip_level(Walk &w, const VolGeom &g, int sb, const int tl[3])
 {
     const int L = 4 * sb;
+    const int lsb = sb == 16 ? 4 : 2;
     int c[3];
     float NL[3], TL[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        c[a] = w.b[a] / sb;
+        c[a] = w.b[a] >> lsb;
         if (w.r.sgn[a] == 0) {
             NL[a] = 0.f;
             TL[a] = INFINITY;
@@ -1241,7 +1251,8 @@ int run_compact(DevBuf &status, DevBuf &ticket, uint32_t *flags, int64_t n_cap, 
     SPR_CUDA_TRY(cudaMemsetAsync(status.p, 0, (size_t)tiles * sizeof(unsigned long long), s));
     SPR_CUDA_TRY(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned int), s));
     ScanCtl ctl{status.as<unsigned long long>(), ticket.as<unsigned int>(), flags, spin, withhold, over, over_limit};
-    compact_kernel<CF, EF><<<(unsigned)tiles, kScanThreads, 0, s>>>(n_cap, n_dev, ctl, cf, ef, total);
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * 4);
+    compact_kernel<CF, EF><<<(unsigned)grid, kScanThreads, 0, s>>>(n_cap, n_dev, ctl, cf, ef, total);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     return SPR_OK;

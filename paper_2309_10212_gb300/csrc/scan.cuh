@@ -53,100 +53,104 @@ __global__ void __launch_bounds__(kScanThreads)
 {
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_prefix;
+    __shared__ uint32_t s_total;
     __shared__ uint32_t s_warp[kScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(ctl.ticket, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
     if (!count.enabled()) return;
-    const int64_t base = tile * kScanTile;
-    if (base >= n) {  // nobody waits on tiles past the end
-        if (tile == 0 && tid == 0) {
-            if (total) *total = 0u;
-            if (ctl.over) *ctl.over = 0u;
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    // persistent: each CTA takes tiles in ticket order until none is left, so
+    // every tile a look-back waits on belongs to a running CTA
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(ctl.ticket, 1u);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        const int64_t base = tile * kScanTile;
+        if (base >= n) {  // nobody waits on tiles past the end
+            if (tile == 0 && tid == 0) {
+                if (total) *total = 0u;
+                if (ctl.over) *ctl.over = 0u;
+            }
+            return;
         }
-        return;
-    }
 
-    uint32_t c[kScanItems];
-    uint32_t local = 0;
-    const int64_t first = base + (int64_t)tid * kScanItems;
+        uint32_t c[kScanItems];
+        uint32_t local = 0;
+        const int64_t first = base + (int64_t)tid * kScanItems;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        int64_t i = first + k;
-        c[k] = i < n ? count(i) : 0u;
-        local += c[k];
-    }
-    // block-wide exclusive scan of the per-thread sums
-    uint32_t incl = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
-        uint32_t wi = w;
+        for (int k = 0; k < kScanItems; ++k) {
+            int64_t i = first + k;
+            c[k] = i < n ? count(i) : 0u;
+            local += c[k];
+        }
+        // block-wide exclusive scan of the per-thread sums
+        uint32_t incl = local;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-            if (lane >= o) wi += y;
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
         }
-        if (lane < kScanThreads / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
-    }
-    __syncthreads();
-    uint32_t excl = s_warp[wid] + incl - local;
-    // the tile total is the last thread's inclusive sum
-    __shared__ uint32_t s_total;
-    if (tid == kScanThreads - 1) s_total = excl + local;
-    __syncthreads();
-    const uint32_t total_tile = s_total;
-
-    if (tid == 0) {
-        uint32_t prefix = 0;
-        const bool publish_ok = tile != ctl.withhold;
-        if (tile == 0) {
-            if (publish_ok) publish(&ctl.status[0], kInc | total_tile);
-        } else {
-            if (publish_ok) publish(&ctl.status[tile], kAgg | total_tile);
-            int64_t pred = tile - 1;
-            int64_t polls = 0;
-            unsigned ns = 32;
-            while (pred >= 0) {
-                unsigned long long w = poll(&ctl.status[pred]);
-                unsigned long long st = w & (3ull << 62);
-                if (st == 0) {
-                    if (++polls > ctl.spin_limit) {
-                        atomicOr(ctl.flags, 1u);
-                        break;
-                    }
-                    if ((polls & 63) == 0 && (*(volatile unsigned int *)ctl.flags & 1u)) break;
-                    __nanosleep(ns);
-                    if (ns < 1024) ns <<= 1;
-                    continue;
-                }
-                prefix += (uint32_t)(w & 0xFFFFFFFFull);
-                if (st == kInc) break;
-                --pred;
-            }
-            if (publish_ok) publish(&ctl.status[tile], kInc | (uint32_t)(prefix + total_tile));
-        }
-        s_prefix = prefix;
-        if (base + kScanTile >= n) {
-            if (total) *total = prefix + total_tile;
-            if (ctl.over) *ctl.over = (prefix + total_tile) > ctl.over_limit ? 1u : 0u;
-        }
-    }
-    __syncthreads();
-    uint32_t run = s_prefix + excl;
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
+            uint32_t wi = w;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        int64_t i = first + k;
-        if (i < n) emit(i, run, c[k]);
-        run += c[k];
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            if (lane < kScanThreads / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
+        }
+        __syncthreads();
+        uint32_t excl = s_warp[wid] + incl - local;
+        if (tid == kScanThreads - 1) s_total = excl + local;
+        __syncthreads();
+        const uint32_t total_tile = s_total;
+
+        if (tid == 0) {
+            uint32_t prefix = 0;
+            const bool publish_ok = tile != ctl.withhold;
+            if (tile == 0) {
+                if (publish_ok) publish(&ctl.status[0], kInc | total_tile);
+            } else {
+                if (publish_ok) publish(&ctl.status[tile], kAgg | total_tile);
+                int64_t pred = tile - 1;
+                int64_t polls = 0;
+                unsigned ns = 32;
+                while (pred >= 0) {
+                    unsigned long long w = poll(&ctl.status[pred]);
+                    unsigned long long st = w & (3ull << 62);
+                    if (st == 0) {
+                        if (++polls > ctl.spin_limit) {
+                            atomicOr(ctl.flags, 1u);
+                            break;
+                        }
+                        if ((polls & 63) == 0 && (*(volatile unsigned int *)ctl.flags & 1u)) break;
+                        __nanosleep(ns);
+                        if (ns < 1024) ns <<= 1;
+                        continue;
+                    }
+                    prefix += (uint32_t)(w & 0xFFFFFFFFull);
+                    if (st == kInc) break;
+                    --pred;
+                }
+                if (publish_ok) publish(&ctl.status[tile], kInc | (uint32_t)(prefix + total_tile));
+            }
+            s_prefix = prefix;
+            if (base + kScanTile >= n) {
+                if (total) *total = prefix + total_tile;
+                if (ctl.over) *ctl.over = (prefix + total_tile) > ctl.over_limit ? 1u : 0u;
+            }
+        }
+        __syncthreads();
+        uint32_t run = s_prefix + excl;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            int64_t i = first + k;
+            if (i < n) emit(i, run, c[k]);
+            run += c[k];
+        }
+        __syncthreads();   // shared state is reused by this CTA's next tile
     }
 }
 
