@@ -1303,6 +1303,7 @@ struct spr_renderer {
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gprof = nullptr;  // one attempt with event nodes between stages
     int graph_kernels = 0;        // kernels in one pass of the body
 };
 
@@ -1312,6 +1313,8 @@ void drop_graph(spr_renderer *r)
 {
     if (r->gexec) cudaGraphExecDestroy(r->gexec);
     if (r->graph) cudaGraphDestroy(r->graph);
+    if (r->gprof) cudaGraphExecDestroy(r->gprof);
+    r->gprof = nullptr;
     r->gexec = nullptr;
     r->graph = nullptr;
 }
@@ -1461,10 +1464,17 @@ __global__ void set_limit_kernel(PassState *ps, uint32_t more)
     ps->run = (ps->n_live > 0 && more > 0) ? 1u : 0u;
 }
 
+// an event record that also works inside stream capture (as an event node)
+inline cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing)
+{
+    return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
 // One attempt of a pass, entirely on the device.  Capturable: no host
 // synchronisation and no host-side scalars that change between passes.
 // With events, records ev[0..6] around the stages.
-int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphConditionalHandle h, int use_h)
+int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphConditionalHandle h, int use_h,
+                    bool capturing = false)
 {
     const VolGeom &g = r->vol->g;
     uint32_t *ctr = r->ctr.as<uint32_t>();
@@ -1473,7 +1483,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     uint32_t *live0 = r->live[0].as<uint32_t>(), *live1 = r->live[1].as<uint32_t>();
     const int64_t cap = r->cap_entries;
     int64_t k0 = r->launches;
-    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
+    if (events) SPR_CUDA_TRY(record(r->ev[0], s, capturing));
     begin_pass_kernel<<<1, 32, 0, s>>>(ps, ctr);
     SPR_CUDA_TRY(cudaMemsetAsync(r->vis_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
     SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
@@ -1484,7 +1494,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
         r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr);
     count_launch(2);
     SPR_CUDA_TRY(cudaGetLastError());
-    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
+    if (events) SPR_CUDA_TRY(record(r->ev[1], s, capturing));
 
     // (b) compact the marks; group the entries by visible block
     SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->nwords, nullptr,
@@ -1509,7 +1519,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
         r->obrays.as<uint32_t>(), r->erank.as<uint32_t>(), r->E.as<uint32_t>(), ctr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
-    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[2], s));
+    if (events) SPR_CUDA_TRY(record(r->ev[2], s, capturing));
 
     // (c) cache: look up, pick least recently used victims, assign
     LruPair lp{r->lru[0].as<uint32_t>(), r->lru[1].as<uint32_t>(), ps};
@@ -1527,14 +1537,14 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, &ps->fresh_hi,
                         TouchedCount{r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
                         TouchedEmit{r->touched.as<uint8_t>(), ctr, lp}, nullptr, s));
-    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[3], s));
+    if (events) SPR_CUDA_TRY(record(r->ev[3], s, capturing));
 
     // (d) decode the misses into their slots
     SPR_TRY(launch_decode_list(r->vol->comp.as<uint8_t>(), g.nblocks, g.rate, r->miss.as<uint32_t>(),
                                r->victim.as<uint32_t>(), r->cap_act, ctr + C_NMISS, ctr + C_OVERFLOW,
                                r->cache.as<float>(), ctr + C_BAD, s));
     count_launch();
-    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[4], s));
+    if (events) SPR_CUDA_TRY(record(r->ev[4], s, capturing));
 
     // (e) intersect the entries, block by block
     RT R{make_geo(r), r->cache.as<float>(), r->blk_slot.as<uint32_t>()};
@@ -1542,7 +1552,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
                                                            live1, ps, r->keys.as<unsigned long long>(), ctr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
-    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[5], s));
+    if (events) SPR_CUDA_TRY(record(r->ev[5], s, capturing));
 
     // (f) resolve hits and exits, compact the live rays in order, end the pass
     ResolveCount rc{live0,
@@ -1568,7 +1578,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
                                      use_h);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
-    if (events) SPR_CUDA_TRY(cudaEventRecord(r->ev[6], s));
+    if (events) SPR_CUDA_TRY(record(r->ev[6], s, capturing));
     r->graph_kernels = (int)(r->launches - k0);
     return SPR_OK;
 }
@@ -1605,6 +1615,8 @@ int read_state(spr_renderer *r, cudaStream_t s)
     return SPR_OK;
 }
 
+int build_prof_graph(spr_renderer *r);
+
 // one pass driven from the host (used by spr_render_pass and for per-stage
 // timing): attempts until the pass completes
 int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
@@ -1637,8 +1649,14 @@ int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
     count_launch();
     float stage_ms[6] = {0, 0, 0, 0, 0, 0};
     const int before = r->pass;
+    if (prof) SPR_TRY(build_prof_graph(r));
     for (int attempt = 0; attempt < 64 && r->pass == before; ++attempt) {
-        SPR_TRY(enqueue_attempt(r, s, prof, 0, 0));
+        if (prof) {
+            SPR_CUDA_TRY(cudaGraphLaunch(r->gprof, s));
+            r->launches += r->graph_kernels;
+        } else {
+            SPR_TRY(enqueue_attempt(r, s, false, 0, 0));
+        }
         SPR_TRY(read_state(r, s));
         if (prof)
             for (int k = 0; k < 6; ++k) {
@@ -1661,6 +1679,31 @@ int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
     }
     st.ms = tot;
     if (out) *out = st;
+    return SPR_OK;
+}
+
+// One attempt captured with event nodes between its stages, so that stage
+// times are device times, free of host launch gaps.
+int build_prof_graph(spr_renderer *r)
+{
+    if (r->gprof) return SPR_OK;
+    if (!r->cap_stream) SPR_CUDA_TRY(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
+    SPR_CUDA_TRY(cudaStreamBeginCapture(r->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int64_t saved = r->launches;
+    int rc = enqueue_attempt(r, r->cap_stream, true, 0, 0, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(r->cap_stream, &g);
+    r->launches = saved;
+    if (rc != SPR_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc != SPR_OK ? rc : set_error(SPR_ERR_CUDA, "profiling capture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&r->gprof, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        r->gprof = nullptr;
+        return set_error(SPR_ERR_CUDA, "profiling graph: %s", cudaGetErrorString(e));
+    }
     return SPR_OK;
 }
 
