@@ -259,6 +259,23 @@ int spr_exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 int spr_debug_scan_withhold(const uint32_t *in, uint32_t *out, int64_t n,
                             int64_t withhold_tile, int64_t spin_limit, spr_stream stream);
 
+/* Allocation-free variant of spr_exclusive_scan_u32 (same arguments, same
+ * results, same bounded waits).  The paper has no counterpart: it exists for
+ * callers that must not allocate device memory -- one recovering from an
+ * out-of-memory error, one running inside an allocator hook (allocating
+ * would re-enter the allocator), one on a latency-bound stream that cannot
+ * let cudaMalloc/cudaFree synchronise the device.  Its look-back scratch is
+ * a static device array (256 KiB + 256 B per device), so n is limited to
+ * 2^26 elements; a longer n returns SPR_ERR_INVALID_ARG before any device
+ * work.  Each call clears the scratch it uses on `stream` before its launch
+ * and synchronises `stream` afterwards.  The first call on a device, made
+ * with that device current, resolves the scratch address
+ * (cudaGetSymbolAddress); make that first call before any stream capture on
+ * the device.  Calls that overlap on one device (different streams or
+ * unordered host threads) share the scratch and race: order them. */
+int spr_exclusive_scan_u32_noalloc(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
+                                   spr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

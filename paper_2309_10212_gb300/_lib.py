@@ -107,6 +107,7 @@ PROTOTYPES = {
     "spr_read_framebuffer": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "spr_exclusive_scan_u32": ([_vp, _vp, _i64, _vp, _vp], _i32),
     "spr_debug_scan_withhold": ([_vp, _vp, _i64, _i64, _i64, _vp], _i32),
+    "spr_exclusive_scan_u32_noalloc": ([_vp, _vp, _i64, _vp, _vp], _i32),
 }
 
 _lock = threading.Lock()

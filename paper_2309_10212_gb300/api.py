@@ -109,6 +109,14 @@ def spr_exclusive_scan_u32(x, out=None, stream=None):
     return out, total
 
 
+def spr_exclusive_scan_u32_noalloc(x, out, total, stream=None):
+    """The allocation-free prefix sum: the caller supplies `out` (like x) and
+    `total` (one int32 on the device); the library allocates nothing."""
+    check(load().spr_exclusive_scan_u32_noalloc(_dev_ptr(x), _dev_ptr(out), x.numel(),
+                                                _dev_ptr(total), _stream(stream)))
+    return out, total
+
+
 def spr_debug_scan_withhold(x, withhold_tile: int, spin_limit: int, out=None, stream=None):
     """The bounded-wait test hook; returns the status instead of raising."""
     torch = _torch()
