@@ -241,8 +241,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--dump", default="", help="write per-pass details to this JSON file")
+    ap.add_argument("--k-max", type=int, default=0,
+                    help="override the workload's speculation limit (k sweeps; 0 keeps it)")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.k_max > 0:
+        wl["k"] = args.k_max
+        wl["name"] = wl["name"].rsplit("k<=", 1)[0] + f"k<={args.k_max}" if "k<=" in wl["name"] else wl["name"]
     if args.impl == "reference":
         return run_reference(args, wl)
     if args.warmup < 3:

@@ -13,7 +13,8 @@
  *   (e) a ray whose hit block is among its taken blocks finishes with a hit;
  *       a ray that got fewer than k blocks has left the volume and finishes
  *       without one (Sec. 4.4);
- *   (f) the remaining rays form the next pass's live list, in pixel order.
+ *   (f) the remaining rays form the next pass's live list, in the order of
+ *       the first live list.
  * k is the fixed count, or floor(w*h / N_Act) capped at k_max (Sec. 4).
  *
  * Choices where the paper is silent (the cache of Sec. 3.5 grows instead):
@@ -23,6 +24,10 @@
  *   - When a pass needs more active blocks than the cache has slots, k is
  *     halved and the pass redone; at k = 1 the live list is cut to its first
  *     half instead, until the pass fits.  Neither changes the image.
+ *   - The first live list holds the rays that enter the volume in screen
+ *     tiles of 8 x 4 pixels, tiles left to right then top to bottom, pixels
+ *     row by row inside a tile.  The order only decides which rays a cut
+ *     live list keeps.
  */
 #include "orc.h"
 
@@ -90,8 +95,13 @@ int orc_simulate(int W, int H, const int32_t dims[3], const int32_t *enters,
     if (final_pass) memset(final_pass, 0, sizeof(int32_t) * npix);
 
     int64_t n_live = 0;
-    for (int64_t p = 0; p < npix; p++)
-        if (enters[p]) live[n_live++] = p;
+    for (int ty = 0; ty < H; ty += 4)
+        for (int tx = 0; tx < W; tx += 8)
+            for (int y = ty; y < ty + 4 && y < H; y++)
+                for (int x = tx; x < tx + 8 && x < W; x++) {
+                    int64_t p = (int64_t)y * W + x;
+                    if (enters[p]) live[n_live++] = p;
+                }
 
     int pass = 0, rc = 0;
     uint32_t *vis_set = NULL, *act_set = NULL;

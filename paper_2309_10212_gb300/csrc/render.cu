@@ -364,8 +364,30 @@ __global__ void smask_kernel(const unsigned long long *__restrict__ fmask, VolGe
 }
 
 // ------------------------------------------------------------- ray setup
+// Rays are enumerated in tiles of 8x4 pixels (a warp's worth), tiles in
+// row-major order, so the rays one warp traverses and intersects are screen
+// neighbours.  The live lists keep this order from pass to pass.
+constexpr int kRayTileW = 8, kRayTileH = 4;
+
+inline int64_t tiled_ray_count(int W, int H)
+{
+    return (int64_t)((W + kRayTileW - 1) / kRayTileW) * ((H + kRayTileH - 1) / kRayTileH) * 32;
+}
+
+// pixel of tiled position t, or -1 where the tile overhangs the image
+__device__ __forceinline__ int64_t tiled_pixel(int64_t t, int W, int H)
+{
+    const int64_t tile = t >> 5;
+    const int l = (int)(t & 31);
+    const int tiles_x = (W + kRayTileW - 1) / kRayTileW;
+    const int x = (int)(tile % tiles_x) * kRayTileW + (l & (kRayTileW - 1));
+    const int y = (int)(tile / tiles_x) * kRayTileH + (l >> 3);
+    return (x < W && y < H) ? (int64_t)y * W + x : -1;
+}
+
 struct RaygenCount {
     Geo P;
+    int H;
     uint64_t *state;
     uint8_t *status;
     uint64_t *keys;
@@ -374,8 +396,10 @@ struct RaygenCount {
     uint64_t *cell;
     int32_t *final_pass;
     __device__ bool enabled() const { return true; }
-    __device__ uint32_t operator()(int64_t p) const
+    __device__ uint32_t operator()(int64_t t) const
     {
+        const int64_t p = tiled_pixel(t, P.W, H);
+        if (p < 0) return 0;
         keys[p] = kNoKey;
         depth[p] = INFINITY;
         rgba[p] = 0u;
@@ -419,9 +443,10 @@ struct RaygenCount {
 
 struct IndexEmit {
     uint32_t *out;
-    __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
+    int W, H;
+    __device__ void operator()(int64_t t, uint32_t pre, uint32_t c) const
     {
-        if (c) out[pre] = (uint32_t)i;
+        if (c) out[pre] = (uint32_t)tiled_pixel(t, W, H);
     }
 };
 
@@ -1248,9 +1273,10 @@ int run_compact(DevBuf &status, DevBuf &ticket, uint32_t *flags, int64_t n_cap, 
     int64_t tiles = std::max<int64_t>(1, scan_tiles(n_cap));
     if ((size_t)tiles * sizeof(unsigned long long) > status.bytes)
         return set_error(SPR_ERR_INVALID_ARG, "scan of %lld items exceeds its scratch", (long long)n_cap);
-    SPR_CUDA_TRY(cudaMemsetAsync(status.p, 0, (size_t)tiles * sizeof(unsigned long long), s));
-    SPR_CUDA_TRY(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned int), s));
-    ScanCtl ctl{status.as<unsigned long long>(), ticket.as<unsigned int>(), flags, spin, withhold, over, over_limit};
+    // status words and ticket/done/epoch were zeroed when allocated; the
+    // kernel leaves them ready for the next launch
+    ScanCtl ctl{status.as<unsigned long long>(), (int64_t)(status.bytes / sizeof(unsigned long long)),
+                ticket.as<unsigned int>(), flags, spin, withhold, over, over_limit};
     const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * 4);
     compact_kernel<CF, EF><<<(unsigned)grid, kScanThreads, 0, s>>>(n_cap, n_dev, ctl, cf, ef, total);
     count_launch();
@@ -1371,10 +1397,14 @@ int ensure_entry_buffers(spr_renderer *r, cudaStream_t s)
 
 int ensure_scan_scratch(spr_renderer *r, cudaStream_t s)
 {
-    int64_t biggest = std::max({r->npix, r->n_slots, r->nwords, r->cap_entries, r->cap_act, (int64_t)1});
+    int64_t biggest = std::max({tiled_ray_count(r->W, r->H), r->n_slots, r->nwords, r->cap_entries, r->cap_act,
+                                (int64_t)1});
     size_t need = sizeof(unsigned long long) * (scan_tiles(biggest) + 1);
-    if (r->scan_status.bytes < need) drop_graph(r);
-    return buf_reserve(r->scan_status, need, s);
+    if (r->scan_status.bytes >= need) return SPR_OK;
+    drop_graph(r);
+    SPR_TRY(buf_reserve(r->scan_status, need, s));
+    SPR_CUDA_TRY(cudaMemsetAsync(r->scan_status.p, 0, r->scan_status.bytes, s));
+    return SPR_OK;
 }
 
 int reset_cache(spr_renderer *r, cudaStream_t s)
@@ -1443,12 +1473,19 @@ int enqueue_raygen(spr_renderer *r, cudaStream_t s)
     SPR_TRY(update_occupancy(r, s));
     uint32_t *ctr = r->ctr.as<uint32_t>();
     SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
-    RaygenCount cf{make_geo(r),           r->state_in.as<uint64_t>(), r->status.as<uint8_t>(),
-                   r->keys.as<uint64_t>(), r->fb_depth.as<float>(),   r->fb_rgba.as<uint32_t>(),
-                   r->fb_block.as<uint32_t>(), r->fb_cell.as<uint64_t>(), r->fb_final.as<int32_t>()};
-    IndexEmit ef{r->live[0].as<uint32_t>()};
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, ctr + C_SCANFLAGS, r->npix, nullptr, cf, ef,
-                        ctr + C_NLIVE, s));
+    RaygenCount cf{make_geo(r),
+                   r->H,
+                   r->state_in.as<uint64_t>(),
+                   r->status.as<uint8_t>(),
+                   r->keys.as<uint64_t>(),
+                   r->fb_depth.as<float>(),
+                   r->fb_rgba.as<uint32_t>(),
+                   r->fb_block.as<uint32_t>(),
+                   r->fb_cell.as<uint64_t>(),
+                   r->fb_final.as<int32_t>()};
+    IndexEmit ef{r->live[0].as<uint32_t>(), r->W, r->H};
+    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, ctr + C_SCANFLAGS, tiled_ray_count(r->W, r->H), nullptr,
+                        cf, ef, ctr + C_NLIVE, s));
     after_raygen_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), ctr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
@@ -1788,6 +1825,7 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         return rc;
     }
     if (cudaMemset(r->ps.p, 0, sizeof(PassState)) != cudaSuccess ||
+        cudaMemset(r->scan_ticket.p, 0, r->scan_ticket.bytes) != cudaSuccess ||
         cudaMallocHost((void **)&r->h_ctr, sizeof(uint32_t) * C_COUNT) != cudaSuccess ||
         cudaMallocHost((void **)&r->h_ps, sizeof(PassState)) != cudaSuccess) {
         free_all(r);
@@ -2075,7 +2113,8 @@ int scan_impl(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total, int
         cleanup();
         return rc;
     }
-    if (cudaMemsetAsync(flags.p, 0, 64, s) != cudaSuccess) {
+    if (cudaMemsetAsync(flags.p, 0, 64, s) != cudaSuccess || cudaMemsetAsync(ticket.p, 0, 64, s) != cudaSuccess ||
+        cudaMemsetAsync(status.p, 0, status.bytes, s) != cudaSuccess) {
         cleanup();
         return set_error(SPR_ERR_CUDA, "memset failed");
     }

@@ -7,9 +7,14 @@
 // take their index from an atomic ticket, so every tile a thread waits on is
 // already running or done.  Each tile publishes its aggregate, then its
 // inclusive prefix, in one 64-bit word: bits 63..62 = status (1 aggregate,
-// 2 inclusive), bits 31..0 = value.  Waits are bounded: after `spin_limit`
-// polls (with nanosleep back-off) a tile sets the timeout flag and gives up,
-// and every other waiting tile stops as soon as it sees the flag.
+// 2 inclusive), bits 61..32 = the launch's epoch, bits 31..0 = value.  A
+// word whose epoch is not the current one reads as "not yet published", so
+// the status words need no clearing between launches: the last CTA to leave
+// resets the ticket and advances the epoch (and clears every status word
+// when the 30-bit epoch wraps).  Status words and the ticket/done/epoch
+// words must be zero when first allocated.  Waits are bounded: after
+// `spin_limit` polls (with nanosleep back-off) a tile sets the timeout flag
+// and gives up, and every other waiting tile stops as soon as it sees it.
 #pragma once
 
 #include <stdint.h>
@@ -22,8 +27,9 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int64_t kDefaultSpinLimit = int64_t(1) << 22;
 
 struct ScanCtl {
-    unsigned long long *status;  // one word per tile, zeroed before launch
-    unsigned int *ticket;        // zeroed before launch
+    unsigned long long *status;  // one word per tile; zero when allocated
+    int64_t n_status;            // words in status
+    unsigned int *seq;           // [0] ticket, [1] CTAs done, [2] epoch; zero when allocated
     unsigned int *flags;         // bit 0: a wait timed out
     int64_t spin_limit;
     int64_t withhold;            // test hook: this tile never publishes (-1: none)
@@ -33,6 +39,9 @@ struct ScanCtl {
 
 constexpr unsigned long long kAgg = 1ull << 62;
 constexpr unsigned long long kInc = 2ull << 62;
+constexpr unsigned long long kStatusBits = 3ull << 62;
+constexpr unsigned long long kEpochBits = 0x3FFFFFFFull << 32;
+constexpr unsigned int kEpochMask = 0x3FFFFFFFu;
 
 __device__ __forceinline__ void publish(unsigned long long *w, unsigned long long v)
 {
@@ -54,14 +63,17 @@ __global__ void __launch_bounds__(kScanThreads)
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_prefix;
     __shared__ uint32_t s_total;
+    __shared__ uint32_t s_epoch;
+    __shared__ uint32_t s_last;
     __shared__ uint32_t s_warp[kScanThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = threadIdx.x >> 5;
     if (!count.enabled()) return;
     const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    if (tid == 0) s_epoch = *(volatile unsigned int *)&ctl.seq[2] & kEpochMask;
     // persistent: each CTA takes tiles in ticket order until none is left, so
     // every tile a look-back waits on belongs to a running CTA
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(ctl.ticket, 1u);
+        if (tid == 0) s_tile = atomicAdd(&ctl.seq[0], 1u);
         __syncthreads();
         const int64_t tile = s_tile;
         const int64_t base = tile * kScanTile;
@@ -70,8 +82,9 @@ __global__ void __launch_bounds__(kScanThreads)
                 if (total) *total = 0u;
                 if (ctl.over) *ctl.over = 0u;
             }
-            return;
+            break;
         }
+        const unsigned long long tag = (unsigned long long)s_epoch << 32;
 
         uint32_t c[kScanItems];
         uint32_t local = 0;
@@ -111,16 +124,16 @@ __global__ void __launch_bounds__(kScanThreads)
             uint32_t prefix = 0;
             const bool publish_ok = tile != ctl.withhold;
             if (tile == 0) {
-                if (publish_ok) publish(&ctl.status[0], kInc | total_tile);
+                if (publish_ok) publish(&ctl.status[0], kInc | tag | total_tile);
             } else {
-                if (publish_ok) publish(&ctl.status[tile], kAgg | total_tile);
+                if (publish_ok) publish(&ctl.status[tile], kAgg | tag | total_tile);
                 int64_t pred = tile - 1;
                 int64_t polls = 0;
                 unsigned ns = 32;
                 while (pred >= 0) {
                     unsigned long long w = poll(&ctl.status[pred]);
-                    unsigned long long st = w & (3ull << 62);
-                    if (st == 0) {
+                    unsigned long long st = w & kStatusBits;
+                    if (st == 0 || (w & kEpochBits) != tag) {  // not yet published in this launch
                         if (++polls > ctl.spin_limit) {
                             atomicOr(ctl.flags, 1u);
                             break;
@@ -134,7 +147,7 @@ __global__ void __launch_bounds__(kScanThreads)
                     if (st == kInc) break;
                     --pred;
                 }
-                if (publish_ok) publish(&ctl.status[tile], kInc | (uint32_t)(prefix + total_tile));
+                if (publish_ok) publish(&ctl.status[tile], kInc | tag | (uint32_t)(prefix + total_tile));
             }
             s_prefix = prefix;
             if (base + kScanTile >= n) {
@@ -151,6 +164,26 @@ __global__ void __launch_bounds__(kScanThreads)
             run += c[k];
         }
         __syncthreads();   // shared state is reused by this CTA's next tile
+    }
+    // every CTA has taken its last ticket when the done count reaches the
+    // grid size; that CTA resets the ticket and opens the next epoch
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&ctl.seq[1], 1u) == gridDim.x - 1 ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    const uint32_t next = (s_epoch + 1u) & kEpochMask;
+    if (next == 0) {  // epoch wrap: no stale word may carry a reused epoch
+        for (int64_t i = tid; i < ctl.n_status; i += kScanThreads) ctl.status[i] = 0ull;
+        __threadfence();
+        __syncthreads();
+    }
+    if (tid == 0) {
+        atomicExch(&ctl.seq[0], 0u);
+        atomicExch(&ctl.seq[1], 0u);
+        __threadfence();
+        atomicExch(&ctl.seq[2], next);
     }
 }
 

@@ -33,11 +33,11 @@ constexpr int64_t kNoAllocTiles = kNoAllocMaxN / kScanTile;
 static_assert(kNoAllocMaxN % kScanTile == 0, "whole tiles");
 
 // Layout of the scratch, in 64-bit words: [0, kNoAllocTiles) tile status
-// words; word kTicketWord holds the tile ticket (low 32 bits); word
-// kFlagsWord the flag word.  The two control words sit in their own 128-byte
-// lines.  All three parts must be zero when the kernel starts; every call
-// clears the status words of the tiles it uses and both control words on its
-// stream before the launch.
+// words; words kTicketWord.. hold the ticket, done and epoch counters (three
+// uint32); word kFlagsWord the flag word.  The control words sit in their
+// own 128-byte lines.  All of these must be zero when the kernel starts;
+// every call clears the status words of the tiles it uses and the control
+// words on its stream before the launch.
 constexpr int64_t kTicketWord = kNoAllocTiles;
 constexpr int64_t kFlagsWord = kNoAllocTiles + 16;
 constexpr int64_t kNoAllocWords = kNoAllocTiles + 32;  // 256 KiB + 256 B
@@ -115,7 +115,7 @@ extern "C" int spr_exclusive_scan_u32_noalloc(const uint32_t *in, uint32_t *out,
     SPR_CUDA_TRY(cudaMemsetAsync(status, 0, (size_t)tiles * sizeof(unsigned long long), s));
     SPR_CUDA_TRY(cudaMemsetAsync(d.scratch + kTicketWord, 0,
                                  (size_t)(kNoAllocWords - kTicketWord) * sizeof(unsigned long long), s));
-    ScanCtl ctl{status, ticket, flags, kDefaultSpinLimit, -1, nullptr, 0u};
+    ScanCtl ctl{status, tiles, ticket, flags, kDefaultSpinLimit, -1, nullptr, 0u};
     const int64_t grid = std::min<int64_t>(tiles, (int64_t)d.sms * 4);
     compact_kernel<NoAllocCount, NoAllocEmit>
         <<<(unsigned)grid, kScanThreads, 0, s>>>(n, nullptr, ctl, NoAllocCount{in}, NoAllocEmit{out}, total);
