@@ -54,7 +54,8 @@ enum Ctr {
     C_STEPS,     // walk steps of all rays this pass
     C_MAXSTEPS,  // longest walk this pass
     C_NEEDUSED,  // victims taken from the used-slot list (the rest are fresh slots)
-    C_COUNT = 16
+    C_QISECT,    // work queue of the intersection: entries handed out
+    C_COUNT = 20
 };
 
 // The pass loop's state lives on the device, so that a pass (and a whole
@@ -317,6 +318,18 @@ __device__ int locate_block(const Ray &r, int a, Tq T, int tb)
 __device__ __forceinline__ void set_bit(uint32_t *bits, uint32_t b)
 {
     atomicOr(bits + (b >> 5), 1u << (b & 31));   // result unused: a reduction
+}
+
+// A warp takes the next 32 items of a work queue (all lanes get the base).
+// The intersection runs one wave of CTAs that loop until the queue is dry,
+// so blocks with many entries do not hold back a fixed share of the grid.
+// (The traversal keeps a grid-stride loop over several waves: its lanes
+// diverge so much that a warp-wide take would wait on the longest ray.)
+__device__ __forceinline__ uint32_t warp_take(uint32_t *q)
+{
+    uint32_t base = 0;
+    if ((threadIdx.x & 31) == 0) base = atomicAdd(q, 32u);
+    return __shfl_sync(0xFFFFFFFFu, base, 0);
 }
 
 __device__ __forceinline__ void warp_add(uint32_t *ctr, uint32_t v)
@@ -1058,22 +1071,25 @@ __device__ bool intersect_block(const RT &R, const Ray &r, float isov, int bx, i
     return false;
 }
 
-__global__ void __launch_bounds__(128) intersect_kernel(RT R, const uint32_t *__restrict__ E,
+__global__ void __launch_bounds__(128, 4) intersect_kernel(RT R, const uint32_t *__restrict__ E,
                                                         const uint32_t *__restrict__ rbid,
                                                         const uint32_t *__restrict__ live0,
                                                         const uint32_t *__restrict__ live1,
                                                         const PassState *__restrict__ ps,
-                                                        unsigned long long *keys, const uint32_t *ctr)
+                                                        unsigned long long *keys, uint32_t *ctr)
 {
     if (ctr[C_OVERFLOW]) return;
     const uint32_t kk = ps->kk;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
     const Cam cam = *R.P.camd;
     const float iso = *R.P.isod;
-    const int64_t n = ctr[C_NENT];
+    const uint32_t n = ctr[C_NENT];
     const VolGeom &g = R.P.g;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (int64_t)gridDim.x * blockDim.x) {
+    for (;;) {
+        const uint32_t base = warp_take(&ctr[C_QISECT]);
+        if (base >= n) break;
+        const uint32_t idx = base + (threadIdx.x & 31);
+        if (idx >= n) continue;
         uint32_t e = E[idx];
         uint32_t b = rbid[e];
         uint32_t i = e / kk, j = e - i * kk;
@@ -1300,6 +1316,7 @@ struct spr_renderer {
     int64_t n_slots = 0;
     bool profiling = false;
 
+    int grid_isect = 1;   // one wave of the work-queue kernel
     bool need_raygen = true;
     bool cache_dirty = true;
     bool params_dirty = true;   // camera / isovalue / speculation not yet on the device
@@ -1319,12 +1336,19 @@ struct spr_renderer {
     DevBuf occ_fine, occ_super;   // brick masks per coarse cell and per super cell
     Occ occ{};
     float occ_iso = NAN;
-    DevBuf scan_status, scan_ticket, ctr;
+    // look-back scratch, one set per branch of a pass that can run a scan
+    // while another branch runs one: [0] main (grouping, resolve, ray
+    // generation), [1] cache, [2] LRU order
+    DevBuf scan_status[3], scan_ticket[3];
+    DevBuf ctr;
     DevBuf ps, recs, camd;        // device pass state, per-pass records, camera + isovalue
     static constexpr int kRecCap = 4096;
     PassState *h_ps = nullptr;    // pinned
     uint32_t *h_ctr = nullptr;    // pinned
     cudaEvent_t ev[8] = {};
+    // fork/join of the pass's branches (no timing)
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t jev[5] = {};
     // the pass loop as one graph: a while node whose body is one pass
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -1354,7 +1378,8 @@ void free_all(spr_renderer *r)
                       &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre, &r->act_wpre,
                       &r->ivis, &r->iact, &r->nbrays, &r->obrays, &r->cache, &r->blk_slot,
                       &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
-                      &r->scan_status, &r->scan_ticket, &r->ctr, &r->occ_fine, &r->occ_super,
+                      &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
+                      &r->scan_ticket[1], &r->scan_ticket[2], &r->ctr, &r->occ_fine, &r->occ_super,
                       &r->ps, &r->recs, &r->camd};
     for (DevBuf *b : bufs) buf_free(*b, nullptr);
     if (r->h_ctr) cudaFreeHost(r->h_ctr);
@@ -1363,6 +1388,10 @@ void free_all(spr_renderer *r)
     r->h_ps = nullptr;
     for (auto &e : r->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : r->jev)
+        if (e) cudaEventDestroy(e);
+    for (auto &a : r->aux)
+        if (a) cudaStreamDestroy(a);
     if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
     r->cap_stream = nullptr;
 }
@@ -1400,10 +1429,12 @@ int ensure_scan_scratch(spr_renderer *r, cudaStream_t s)
     int64_t biggest = std::max({tiled_ray_count(r->W, r->H), r->n_slots, r->nwords, r->cap_entries, r->cap_act,
                                 (int64_t)1});
     size_t need = sizeof(unsigned long long) * (scan_tiles(biggest) + 1);
-    if (r->scan_status.bytes >= need) return SPR_OK;
+    if (r->scan_status[0].bytes >= need) return SPR_OK;
     drop_graph(r);
-    SPR_TRY(buf_reserve(r->scan_status, need, s));
-    SPR_CUDA_TRY(cudaMemsetAsync(r->scan_status.p, 0, r->scan_status.bytes, s));
+    for (DevBuf &b : r->scan_status) {
+        SPR_TRY(buf_reserve(b, need, s));
+        SPR_CUDA_TRY(cudaMemsetAsync(b.p, 0, b.bytes, s));
+    }
     return SPR_OK;
 }
 
@@ -1473,6 +1504,10 @@ int enqueue_raygen(spr_renderer *r, cudaStream_t s)
     SPR_TRY(update_occupancy(r, s));
     uint32_t *ctr = r->ctr.as<uint32_t>();
     SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
+    // each attempt clears the bitmaps after use; this covers a render that
+    // stopped inside an attempt
+    SPR_CUDA_TRY(cudaMemsetAsync(r->vis_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
+    SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
     RaygenCount cf{make_geo(r),
                    r->H,
                    r->state_in.as<uint64_t>(),
@@ -1484,7 +1519,7 @@ int enqueue_raygen(spr_renderer *r, cudaStream_t s)
                    r->fb_cell.as<uint64_t>(),
                    r->fb_final.as<int32_t>()};
     IndexEmit ef{r->live[0].as<uint32_t>(), r->W, r->H};
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, ctr + C_SCANFLAGS, tiled_ray_count(r->W, r->H), nullptr,
+    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], ctr + C_SCANFLAGS, tiled_ray_count(r->W, r->H), nullptr,
                         cf, ef, ctr + C_NLIVE, s));
     after_raygen_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), ctr);
     count_launch();
@@ -1509,7 +1544,16 @@ inline cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing)
 
 // One attempt of a pass, entirely on the device.  Capturable: no host
 // synchronisation and no host-side scalars that change between passes.
-// With events, records ev[0..6] around the stages.
+// With events, records ev[0..6] around the stages and runs them in order;
+// without, the grouping and cache stages run as concurrent branches:
+//
+//   main:  begin, traverse --+-- visible scan ---(active)--- entry counts,
+//                            |                               offsets, scatter --(decode)-- intersect, resolve --(lru)-- end
+//   aux 0:                   +-- active scan -- lookup -- victims -- assign --+-- decode
+//   aux 1:                                                                   +-- LRU order scan
+//
+// The bitmaps are cleared right after their last reader, ready for the next
+// attempt.
 int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphConditionalHandle h, int use_h,
                     bool capturing = false)
 {
@@ -1519,36 +1563,48 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     PassState *ps = r->ps.as<PassState>();
     uint32_t *live0 = r->live[0].as<uint32_t>(), *live1 = r->live[1].as<uint32_t>();
     const int64_t cap = r->cap_entries;
+    const bool fork = !events;
+    cudaStream_t sa = fork ? r->aux[0] : s;   // cache branch
+    cudaStream_t sl = fork ? r->aux[1] : s;   // LRU order branch
+    cudaEvent_t ev_trav = r->jev[0], ev_act = r->jev[1], ev_assign = r->jev[2], ev_dec = r->jev[3],
+                ev_lru = r->jev[4];
     int64_t k0 = r->launches;
     if (events) SPR_CUDA_TRY(record(r->ev[0], s, capturing));
     begin_pass_kernel<<<1, 32, 0, s>>>(ps, ctr);
-    SPR_CUDA_TRY(cudaMemsetAsync(r->vis_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
-    SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
+    count_launch();
 
     // (a) traversal with speculation, marking visible and active blocks
     traverse_kernel<<<grid_for(r->npix, 128, 16), 128, 0, s>>>(
         make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
         r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr);
-    count_launch(2);
+    count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     if (events) SPR_CUDA_TRY(record(r->ev[1], s, capturing));
+    if (fork) {
+        SPR_CUDA_TRY(cudaEventRecord(ev_trav, s));
+        SPR_CUDA_TRY(cudaStreamWaitEvent(sa, ev_trav, 0));
+    }
 
-    // (b) compact the marks; group the entries by visible block
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->nwords, nullptr,
+    // (b) compact the marks; group the entries by visible block.  The active
+    // scan (cache branch) decides whether the pass overflows the cache.
+    SPR_TRY(run_compact(r->scan_status[1], r->scan_ticket[1], flags, r->nwords, nullptr,
+                        BitsCount{r->act_bits.as<uint32_t>(), nullptr},
+                        BitsEmit{r->act_bits.as<uint32_t>(), r->act_wpre.as<uint32_t>(), r->iact.as<uint32_t>(),
+                                 nullptr},
+                        ctr + C_NACT, sa, kDefaultSpinLimit, -1, ctr + C_OVERFLOW, (uint32_t)r->n_slots));
+    SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, sa));
+    if (fork) SPR_CUDA_TRY(cudaEventRecord(ev_act, sa));
+    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, r->nwords, nullptr,
                         BitsCount{r->vis_bits.as<uint32_t>(), nullptr},
                         BitsEmit{r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(), r->ivis.as<uint32_t>(),
                                  r->nbrays.as<uint32_t>()},
                         ctr + C_NVIS, s));
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->nwords, nullptr,
-                        BitsCount{r->act_bits.as<uint32_t>(), nullptr},
-                        BitsEmit{r->act_bits.as<uint32_t>(), r->act_wpre.as<uint32_t>(), r->iact.as<uint32_t>(),
-                                 nullptr},
-                        ctr + C_NACT, s, kDefaultSpinLimit, -1, ctr + C_OVERFLOW, (uint32_t)r->n_slots));
+    if (fork) SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_act, 0));
     count_entries_kernel<<<grid_for(cap, 256, 16), 256, 0, s>>>(
         ps, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
         r->nbrays.as<uint32_t>(), r->erank.as<uint32_t>(), ctr);
     count_launch();
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, cap, ctr + C_NVIS,
+    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, cap, ctr + C_NVIS,
                         ArrayCount{r->nbrays.as<uint32_t>(), ctr + C_OVERFLOW},
                         ArrayEmit{r->obrays.as<uint32_t>()}, ctr + C_NENT, s));
     scatter_entries_kernel<<<grid_for(cap, 256, 16), 256, 0, s>>>(
@@ -1556,37 +1612,47 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
         r->obrays.as<uint32_t>(), r->erank.as<uint32_t>(), r->E.as<uint32_t>(), ctr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
+    SPR_CUDA_TRY(cudaMemsetAsync(r->vis_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
     if (events) SPR_CUDA_TRY(record(r->ev[2], s, capturing));
 
     // (c) cache: look up, pick least recently used victims, assign
     LruPair lp{r->lru[0].as<uint32_t>(), r->lru[1].as<uint32_t>(), ps};
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->cap_act, ctr + C_NACT,
+    SPR_TRY(run_compact(r->scan_status[1], r->scan_ticket[1], flags, r->cap_act, ctr + C_NACT,
                         LookupCount{r->iact.as<uint32_t>(), r->blk_slot.as<uint32_t>(), r->touched.as<uint8_t>(),
                                     ctr + C_OVERFLOW},
-                        SelectEmit{r->iact.as<uint32_t>(), r->miss.as<uint32_t>()}, ctr + C_NMISS, s));
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, &ps->n_used,
+                        SelectEmit{r->iact.as<uint32_t>(), r->miss.as<uint32_t>()}, ctr + C_NMISS, sa));
+    SPR_TRY(run_compact(r->scan_status[1], r->scan_ticket[1], flags, r->n_slots, &ps->n_used,
                         VictimCount{lp, r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
-                        VictimEmit{lp, ctr, r->victim.as<uint32_t>(), (uint32_t)r->n_slots}, ctr + C_NUNTOUCHED, s));
-    assign_kernel<<<grid_for(r->cap_act, 256, 8), 256, 0, s>>>(r->miss.as<uint32_t>(), r->victim.as<uint32_t>(),
-                                                              r->blk_slot.as<uint32_t>(), r->slot_blk.as<uint32_t>(),
-                                                              r->touched.as<uint8_t>(), ctr, ps, (uint32_t)r->n_slots);
+                        VictimEmit{lp, ctr, r->victim.as<uint32_t>(), (uint32_t)r->n_slots}, ctr + C_NUNTOUCHED, sa));
+    assign_kernel<<<grid_for(r->cap_act, 256, 8), 256, 0, sa>>>(r->miss.as<uint32_t>(), r->victim.as<uint32_t>(),
+                                                               r->blk_slot.as<uint32_t>(), r->slot_blk.as<uint32_t>(),
+                                                               r->touched.as<uint8_t>(), ctr, ps, (uint32_t)r->n_slots);
     count_launch();
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->n_slots, &ps->fresh_hi,
+    SPR_CUDA_TRY(cudaGetLastError());
+    if (fork) {
+        SPR_CUDA_TRY(cudaEventRecord(ev_assign, sa));
+        SPR_CUDA_TRY(cudaStreamWaitEvent(sl, ev_assign, 0));
+    }
+    SPR_TRY(run_compact(r->scan_status[2], r->scan_ticket[2], flags, r->n_slots, &ps->fresh_hi,
                         TouchedCount{r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
-                        TouchedEmit{r->touched.as<uint8_t>(), ctr, lp}, nullptr, s));
+                        TouchedEmit{r->touched.as<uint8_t>(), ctr, lp}, nullptr, sl));
     if (events) SPR_CUDA_TRY(record(r->ev[3], s, capturing));
 
     // (d) decode the misses into their slots
     SPR_TRY(launch_decode_list(r->vol->comp.as<uint8_t>(), g.nblocks, g.rate, r->miss.as<uint32_t>(),
                                r->victim.as<uint32_t>(), r->cap_act, ctr + C_NMISS, ctr + C_OVERFLOW,
-                               r->cache.as<float>(), ctr + C_BAD, s));
+                               r->cache.as<float>(), ctr + C_BAD, sa));
     count_launch();
     if (events) SPR_CUDA_TRY(record(r->ev[4], s, capturing));
+    if (fork) {
+        SPR_CUDA_TRY(cudaEventRecord(ev_dec, sa));
+        SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_dec, 0));
+    }
 
     // (e) intersect the entries, block by block
     RT R{make_geo(r), r->cache.as<float>(), r->blk_slot.as<uint32_t>()};
-    intersect_kernel<<<grid_for(cap, 128, 16), 128, 0, s>>>(R, r->E.as<uint32_t>(), r->rbid.as<uint32_t>(), live0,
-                                                           live1, ps, r->keys.as<unsigned long long>(), ctr);
+    intersect_kernel<<<r->grid_isect, 128, 0, s>>>(R, r->E.as<uint32_t>(), r->rbid.as<uint32_t>(), live0, live1, ps,
+                                                   r->keys.as<unsigned long long>(), ctr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     if (events) SPR_CUDA_TRY(record(r->ev[5], s, capturing));
@@ -1609,8 +1675,12 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
                     r->fb_cell.as<uint64_t>(),
                     r->fb_final.as<int32_t>(),
                     ctr};
-    SPR_TRY(run_compact(r->scan_status, r->scan_ticket, flags, r->npix, &ps->n_live, rc, LiveEmit{live0, live1, ps},
-                        ctr + C_NLIVE, s));
+    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, r->npix, &ps->n_live, rc,
+                        LiveEmit{live0, live1, ps}, ctr + C_NLIVE, s));
+    if (fork) {   // the LRU order must be complete before the pass ends
+        SPR_CUDA_TRY(cudaEventRecord(ev_lru, sl));
+        SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_lru, 0));
+    }
     end_pass_kernel<<<1, 32, 0, s>>>(ps, ctr, r->recs.as<spr_pass_stats>(), (uint32_t)spr_renderer::kRecCap, h,
                                      use_h);
     count_launch();
@@ -1815,7 +1885,8 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         (rc = buf_alloc(r->fb_final, 4 * np, s)) || (rc = buf_alloc(r->vis_bits, 4 * r->nwords, s)) ||
         (rc = buf_alloc(r->act_bits, 4 * r->nwords, s)) || (rc = buf_alloc(r->vis_wpre, 4 * r->nwords, s)) ||
         (rc = buf_alloc(r->act_wpre, 4 * r->nwords, s)) ||
-        (rc = buf_alloc(r->blk_slot, 4 * vol->g.nblocks, s)) || (rc = buf_alloc(r->scan_ticket, 64, s)) ||
+        (rc = buf_alloc(r->blk_slot, 4 * vol->g.nblocks, s)) || (rc = buf_alloc(r->scan_ticket[0], 64, s)) ||
+        (rc = buf_alloc(r->scan_ticket[1], 64, s)) || (rc = buf_alloc(r->scan_ticket[2], 64, s)) ||
         (rc = buf_alloc(r->ctr, sizeof(uint32_t) * C_COUNT, s)) ||
         (rc = buf_alloc(r->ps, sizeof(PassState), s)) ||
         (rc = buf_alloc(r->recs, sizeof(spr_pass_stats) * spr_renderer::kRecCap, s)) ||
@@ -1825,7 +1896,10 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         return rc;
     }
     if (cudaMemset(r->ps.p, 0, sizeof(PassState)) != cudaSuccess ||
-        cudaMemset(r->scan_ticket.p, 0, r->scan_ticket.bytes) != cudaSuccess ||
+        cudaMemset(r->scan_ticket[0].p, 0, 64) != cudaSuccess || cudaMemset(r->scan_ticket[1].p, 0, 64) != cudaSuccess ||
+        cudaMemset(r->scan_ticket[2].p, 0, 64) != cudaSuccess ||
+        cudaMemset(r->vis_bits.p, 0, 4 * r->nwords) != cudaSuccess ||
+        cudaMemset(r->act_bits.p, 0, 4 * r->nwords) != cudaSuccess ||
         cudaMallocHost((void **)&r->h_ctr, sizeof(uint32_t) * C_COUNT) != cudaSuccess ||
         cudaMallocHost((void **)&r->h_ps, sizeof(PassState)) != cudaSuccess) {
         free_all(r);
@@ -1833,6 +1907,15 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         return set_error(SPR_ERR_OUT_OF_MEMORY, "pinned host allocation failed");
     }
     for (auto &e : r->ev) cudaEventCreate(&e);
+    for (auto &e : r->jev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    for (auto &a : r->aux) cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
+    // one wave of the work-queue kernel
+    {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, intersect_kernel, 128, 0) != cudaSuccess || nb < 1)
+            nb = 1;
+        r->grid_isect = nb * device_sm_count();
+    }
     for (int a = 0; a < 3; ++a) {
         r->occ.ns[a] = (vol->g.nc[a] + 3) / 4;
         r->occ.ts[a] = (vol->g.tc[a] + 3) / 4;
