@@ -411,6 +411,40 @@ def main():
         e2e_ms = statistics.mean(e2e)
         d2h_total = d2h + 64 * statistics.mean(pass_reads)
 
+        # Decode of every block once (up to 16M blocks, 4 GB out) through
+        # spr_decode_blocks: the decoder's HBM roofline figure, 8*rate bytes
+        # read and 256 bytes written per block.  The library allocates its
+        # 4-byte error flag from torch's caching allocator here, so no
+        # cudaMalloc sits between the events.
+        nb_vol = int(np.prod([(d + 3) // 4 for d in wl["dims"]]))
+        nb_all = min(nb_vol, 16 << 20)
+        # a contiguous run of block ids centred on the middle z layer (the
+        # mixing layer of the paper-scale field), not the empty bottom slabs
+        first = (nb_vol - nb_all) // 2
+        dec_ids = torch.arange(first, first + nb_all, dtype=torch.int64, device="cuda").to(torch.int32)
+        dec_out = torch.empty((nb_all, 64), dtype=torch.float32, device="cuda")
+        spr.use_torch_allocator()
+        try:
+            for _ in range(2):
+                spr.spr_decode_blocks(comp, nb_vol, wl["rate"], ids=dec_ids, n=nb_all, out=dec_out,
+                                      stream=stream)
+            dec_times = []
+            for i in range(5):
+                flush.fill_(i & 255)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                spr.spr_decode_blocks(comp, nb_vol, wl["rate"], ids=dec_ids, n=nb_all, out=dec_out,
+                                      stream=stream)
+                b.record(stream)
+                b.synchronize()
+                dec_times.append(a.elapsed_time(b))
+        finally:
+            spr.spr_set_allocator()
+        del dec_out, dec_ids
+        dec_all_ms = statistics.median(dec_times)
+        dec_all_gbs = nb_all * (256 + 8 * wl["rate"] + 4) / 1e9 / (dec_all_ms / 1e3)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and wl["dims"][0] != 2048:
         try:
@@ -460,6 +494,12 @@ def main():
             "images_per_s": round(1e3 / ms_image * world, 2),
             "stage_ms_per_image": {k: round(v / max(1, len(prof_stats)), 4) for k, v in stage.items()},
             "roofline": roofline,
+            "decode_all": {"kernel": "decode_list_kernel", "blocks": nb_all,
+                           "ms": round(dec_all_ms, 4), "achieved": round(dec_all_gbs, 1),
+                           "peak": pk["hbm_gbs"], "unit": "GB/s",
+                           "frac": round(dec_all_gbs / pk["hbm_gbs"], 4),
+                           "first_block": first, "bytes_per_block": 256 + 8 * wl["rate"] + 4,
+                           "timing": "median of 5 CUDA-event timed calls, L2 flushed before each"},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": int(d2h_total)},

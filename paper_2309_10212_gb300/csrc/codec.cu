@@ -135,7 +135,15 @@ __global__ void encode_kernel(const T *__restrict__ vol, VolGeom g, uint8_t *__r
 }
 
 // decode blocks ids[i] (or i) to out + dst[i]*64 (or i*64), a warp writing
-// its 32 blocks with coalesced stores
+// its 32 blocks with coalesced stores.  Each lane loads its own destination
+// slot once and the warp shares them by shuffles.  At rates <= 2 the loads
+// are software-pipelined: while a lane decodes item k, the bitstream of item
+// k+1 and the block id of item k+2 are in flight.
+__device__ __forceinline__ int64_t dec_id(const uint32_t *ids, int64_t i, int64_t n)
+{
+    return i < n ? (ids ? (int64_t)ids[i] : i) : -1;
+}
+
 __global__ void __launch_bounds__(kDecThreads) decode_list_kernel(
     const uint8_t *__restrict__ comp, int64_t nblocks, int rate, const uint32_t *__restrict__ ids,
     const uint32_t *__restrict__ dst_ids, int64_t n_host, const uint32_t *n_dev,
@@ -147,16 +155,27 @@ __global__ void __launch_bounds__(kDecThreads) decode_list_kernel(
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t *col = col_s + threadIdx.x;
     const int64_t bytes = 8 * (int64_t)rate;
-    for (int64_t base = (int64_t)blockIdx.x * kDecThreads + wid * 32; base < n;
-         base += (int64_t)gridDim.x * kDecThreads) {
-        int64_t i = base + lane;
+    const int64_t stride = (int64_t)gridDim.x * kDecThreads;
+    const bool reg = rate <= 2;
+    int64_t base = (int64_t)blockIdx.x * kDecThreads + wid * 32;
+    int64_t id = dec_id(ids, base + lane, n);
+    int64_t id_next = dec_id(ids, base + stride + lane, n);
+    frc4::RegBits cur{0ull, 0ull};
+    if (reg && id >= 0 && id < nblocks) cur = frc4::load_reg_bits(comp + id * bytes, rate);
+    for (; base < n; base += stride) {
+        const int64_t i = base + lane;
+        // loads for the next items, consumed one and two iterations later
+        frc4::RegBits nxt{0ull, 0ull};
+        if (reg && id_next >= 0 && id_next < nblocks) nxt = frc4::load_reg_bits(comp + id_next * bytes, rate);
+        const int64_t id_after = dec_id(ids, base + 2 * stride + lane, n);
+        const uint32_t my_slot = i < n ? (dst_ids ? dst_ids[i] : (uint32_t)i) : 0u;
         if (i < n) {
-            int64_t id = ids ? (int64_t)ids[i] : i;
             float v[64];
             int emax = 0;
             bool nz = false;
             if (id < nblocks) {
-                nz = frc4::decode_block_coeffs(comp + id * bytes, rate, col, kColStride, &emax);
+                nz = reg ? frc4::decode_coeffs(cur, rate, col, kColStride, &emax)
+                         : frc4::decode_block_coeffs(comp + id * bytes, rate, col, kColStride, &emax);
             } else {
                 atomicOr(bad, 1u);
             }
@@ -170,15 +189,18 @@ __global__ void __launch_bounds__(kDecThreads) decode_list_kernel(
             }
         }
         __syncwarp();
-        const int64_t m = n - base < 32 ? n - base : 32;
+        const int m = n - base < 32 ? (int)(n - base) : 32;
         for (int t = 0; t < m; ++t) {
-            int64_t slot = dst_ids ? (int64_t)dst_ids[base + t] : base + t;
-            float *dst = out + slot * 64;
+            const uint32_t slot = __shfl_sync(0xFFFFFFFFu, my_slot, t);
+            float *dst = out + (int64_t)slot * 64;
             const uint32_t *src = col_s + wid * 32 + t;
             dst[lane] = __uint_as_float(src[lane * kColStride]);
             dst[lane + 32] = __uint_as_float(src[(lane + 32) * kColStride]);
         }
         __syncwarp();
+        cur = nxt;
+        id = id_next;
+        id_next = id_after;
     }
 }
 
@@ -227,7 +249,16 @@ int launch_decode_list(const uint8_t *comp, int64_t nblocks, int rate, const uin
                        const uint32_t *skip, float *out, unsigned int *bad, cudaStream_t s)
 {
     if (n_host <= 0) return SPR_OK;
-    decode_list_kernel<<<grid_for(n_host, kDecThreads, 8), kDecThreads, 0, s>>>(
+    // one wave: as many CTAs as are resident at once (shared memory bound)
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decode_list_kernel, kDecThreads, 0) != cudaSuccess ||
+            nb < 1)
+            nb = 1;
+        per_sm = nb;
+    }
+    decode_list_kernel<<<grid_for(n_host, kDecThreads, per_sm), kDecThreads, 0, s>>>(
         comp, nblocks, rate, ids, dst, n_host, n_dev, skip, out, bad);
     SPR_CUDA_TRY(cudaGetLastError());
     return SPR_OK;
