@@ -34,6 +34,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms to final image & per pass at 1280×720; decoded GB/s vs HBM peak; blocks decoded"
 
+# The traversal is bound by dependent integer/float instruction chains, not by
+# memory: its roofline is the SM issue rate (4 warp instructions per clock per
+# SM, 32 lanes each).  Thread instructions per walk step and DRAM bytes per
+# launch come from one ncu capture of traverse_kernel on the medium workload
+# (smsp__thread_inst_executed.sum and dram__bytes_read/write.sum over the four
+# passes of one render: 1.111e9 thread instructions for 5,313,018 steps;
+# 4.70 MB over 4 launches); the live run supplies the steps and the time.
+TRAV_THREAD_INST_PER_STEP = 209.2
+TRAV_DRAM_BYTES_PER_LAUNCH = 1175872
+
 WORKLOADS = {
     "medium": dict(dims=(512, 512, 512), rate=2, iso=0.3, W=1280, H=720, poses=16,
                    cache_bytes=int(0.10 * 512 ** 3 * 4), spec="adaptive", k=16,
@@ -363,9 +373,24 @@ def main():
                         "achieved": round(dec_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                         "frac": round(dec_gbs / pk["hbm_gbs"], 4), "traffic": None,
                         "peak_source": pk["src"]}
+        elif dom == "traverse":
+            per_pass = [p for _, ps in prof_stats for p in ps]
+            steps_ = sum(p["n_steps"] for p in per_pass)
+            ms_ = stage[dom]
+            sms = torch.cuda.get_device_properties(local).multi_processor_count
+            f_mhz = (clk.summary() or {}).get("sm_max_mhz") or 2070.0
+            peak_ti = sms * 4 * 32 * f_mhz * 1e6 / 1e12
+            ach = steps_ * TRAV_THREAD_INST_PER_STEP / (ms_ / 1e3) / 1e12 if ms_ > 0 else 0.0
+            roofline = {"kernel": one_kernel[dom], "bound": "alu", "achieved": round(ach, 3),
+                        "peak": round(peak_ti, 2), "unit": "Tinst/s", "frac": round(ach / peak_ti, 4),
+                        "traffic": TRAV_DRAM_BYTES_PER_LAUNCH,
+                        "peak_source": "%d SMs x 4 issue slots x 32 lanes x %.0f MHz" % (sms, f_mhz),
+                        "work": "walk steps x %.1f thread instructions per step (ncu)"
+                                % TRAV_THREAD_INST_PER_STEP,
+                        "hbm_frac": None}
         else:
-            # traversal and intersection are latency/ALU bound; report their
-            # algorithmic HBM bytes against the copy peak
+            # the intersection is latency/ALU bound; report its algorithmic
+            # HBM bytes against the copy peak
             per_pass = [p for _, ps in prof_stats for p in ps]
             if dom == "traverse":
                 bytes_ = sum(p["n_processed"] * (4 + 8 + 8) + p["n_processed"] * p["k_used"] * 4

@@ -81,11 +81,24 @@ struct PassState {
     // order, they are the least recently used); the used ones are listed, least
     // recently used first, in the list selected by parity bit 1
     uint32_t fresh_lo, fresh_hi, n_used;
+    uint32_t live_words;  // ceil(n_live / 32): words of the alive bitmap of this pass
     unsigned long long tot_decoded, tot_entries, tot_evicted, tot_hits;
 };
 
 struct Cam {
     float eye[3], p00[3], du[3], dv[3];
+};
+
+// Per-render parameters in device memory, copied from a pinned host block by
+// the first node of the render's start graph (so the captured graphs stay
+// valid when the camera, isovalue, speculation or pass limit change).
+struct DevParams {
+    Cam cam;
+    float iso;
+    uint32_t spec_mode, k_fixed, k_max, npix;
+    uint32_t more;    // passes this call may run
+    uint32_t reset;   // 1: empty the cache before ray generation
+    uint32_t pad;
 };
 
 // occupancy of the three skipping levels for the current isovalue: one bit
@@ -398,70 +411,78 @@ __device__ __forceinline__ int64_t tiled_pixel(int64_t t, int W, int H)
     return (x < W && y < H) ? (int64_t)y * W + x : -1;
 }
 
-struct RaygenCount {
-    Geo P;
-    int H;
-    uint64_t *state;
-    uint8_t *status;
-    uint64_t *keys;
-    float *depth;
-    uint32_t *rgba, *block;
-    uint64_t *cell;
-    int32_t *final_pass;
-    __device__ bool enabled() const { return true; }
-    __device__ uint32_t operator()(int64_t t) const
-    {
+// Ray generation, one thread per tiled position: clear the pixel's outputs,
+// find the ray's entry block, and set bit t of `enter` (warp ballots) when
+// the ray enters the domain.
+__global__ void __launch_bounds__(256) raygen_kernel(Geo P, int H, uint64_t *__restrict__ state,
+                                                     uint8_t *__restrict__ status, uint64_t *__restrict__ keys,
+                                                     float *__restrict__ depth, uint32_t *__restrict__ rgba,
+                                                     uint32_t *__restrict__ block, uint64_t *__restrict__ cell,
+                                                     int32_t *__restrict__ final_pass, uint32_t *__restrict__ enter,
+                                                     int64_t n_tiled)
+{
+    const Cam cam = *P.camd;
+    const VolGeom &g = P.g;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiled;
+         t += (int64_t)gridDim.x * blockDim.x) {   // n_tiled is a multiple of 32: whole warps iterate
         const int64_t p = tiled_pixel(t, P.W, H);
-        if (p < 0) return 0;
-        keys[p] = kNoKey;
-        depth[p] = INFINITY;
-        rgba[p] = 0u;
-        block[p] = kNone;
-        cell[p] = kNoKey;
-        final_pass[p] = 0;
-        Ray r;
-        const Cam &cam = *P.camd;
-        make_ray(r, cam.eye, cam.p00, cam.du, cam.dv, (int)(p % P.W), (int)(p / P.W));
-        const VolGeom &g = P.g;
-        Tq tin{0.f, 1.f}, tout{0.f, 1.f};
-        bool have_out = false;
-        for (int a = 0; a < 3; ++a) {
-            if (r.sgn[a] == 0) {
-                if (r.e[a] < 0.f || r.e[a] > (float)(g.dims[a] - 1)) {
-                    status[p] = 2;
-                    return 0;
+        bool in = false;
+        if (p >= 0) {
+            keys[p] = kNoKey;
+            depth[p] = INFINITY;
+            rgba[p] = 0u;
+            block[p] = kNone;
+            cell[p] = kNoKey;
+            final_pass[p] = 0;
+            Ray r;
+            make_ray(r, cam.eye, cam.p00, cam.du, cam.dv, (int)(p % P.W), (int)(p / P.W));
+            Tq tin{0.f, 1.f}, tout{0.f, 1.f};
+            bool have_out = false, outside = false;
+            for (int a = 0; a < 3; ++a) {
+                if (r.sgn[a] == 0) {
+                    if (r.e[a] < 0.f || r.e[a] > (float)(g.dims[a] - 1)) outside = true;
+                    continue;
                 }
-                continue;
+                float nearp = r.sgn[a] > 0 ? 0.f : (float)(g.dims[a] - 1);
+                float farp = r.sgn[a] > 0 ? (float)(g.dims[a] - 1) : 0.f;
+                Tq tn = plane_t(r, a, nearp), tf = plane_t(r, a, farp);
+                if (tcmp(tn, tin) > 0) tin = tn;
+                if (!have_out || tcmp(tf, tout) < 0) {
+                    tout = tf;
+                    have_out = true;
+                }
             }
-            float nearp = r.sgn[a] > 0 ? 0.f : (float)(g.dims[a] - 1);
-            float farp = r.sgn[a] > 0 ? (float)(g.dims[a] - 1) : 0.f;
-            Tq tn = plane_t(r, a, nearp), tf = plane_t(r, a, farp);
-            if (tcmp(tn, tin) > 0) tin = tn;
-            if (!have_out || tcmp(tf, tout) < 0) {
-                tout = tf;
-                have_out = true;
+            if (outside || !have_out || tcmp(tin, tout) >= 0) {
+                status[p] = 2;
+            } else {
+                int b[3];
+                for (int a = 0; a < 3; ++a) b[a] = locate_block(r, a, tin, g.tb[a]);
+                state[p] = pack_state(b, 0);
+                status[p] = 0;
+                in = true;
             }
         }
-        if (!have_out || tcmp(tin, tout) >= 0) {
-            status[p] = 2;
-            return 0;
+        const unsigned bits = __ballot_sync(0xFFFFFFFFu, in);
+        if ((threadIdx.x & 31) == 0) enter[t >> 5] = bits;
+    }
+}
+
+// live list 0 from the enter bitmap: position t -> its pixel
+struct EnterEmit {
+    const uint32_t *bits;
+    uint32_t *out;
+    int W, H;
+    __device__ void operator()(int64_t w, uint32_t pre, uint32_t) const
+    {
+        uint32_t x = bits[w];
+        while (x) {
+            int b = __ffs(x) - 1;
+            x &= x - 1;
+            out[pre++] = (uint32_t)tiled_pixel(32 * w + b, W, H);
         }
-        int b[3];
-        for (int a = 0; a < 3; ++a) b[a] = locate_block(r, a, tin, g.tb[a]);
-        state[p] = pack_state(b, 0);
-        status[p] = 0;
-        return 1;
     }
 };
 
-struct IndexEmit {
-    uint32_t *out;
-    int W, H;
-    __device__ void operator()(int64_t t, uint32_t pre, uint32_t c) const
-    {
-        if (c) out[pre] = (uint32_t)tiled_pixel(t, W, H);
-    }
-};
 
 // ------------------------------------------------------------- traversal
 __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__restrict__ live0,
@@ -1103,30 +1124,32 @@ __global__ void __launch_bounds__(128, 4) intersect_kernel(RT R, const uint32_t 
 }
 
 // ---------------------------------------------------------------- resolve
-struct ResolveCount {
-    const uint32_t *live0, *live1;
-    const PassState *ps;
-    int Dx, Dy;
-    VolGeom g;
-    unsigned long long *keys;
-    const uint32_t *rbid;
-    uint64_t *state_in;
-    const uint64_t *state_out;
-    uint8_t *status;
-    float *depth;
-    uint32_t *rgba, *block;
-    uint64_t *cell;
-    int32_t *final_pass;
-    uint32_t *ctr;
-    __device__ bool enabled() const { return !ctr[C_OVERFLOW]; }
-    __device__ uint32_t operator()(int64_t i) const
-    {
-        const uint32_t *live = (ps->parity & 1) ? live1 : live0;
-        const uint32_t nproc = ps->nproc, kk = ps->kk;
-        const int pass = (int)ps->pass + 1;
-        const uint32_t ray = live[i];
-        uint32_t alive = 1, hit = 0, gone = 0;
+// Resolve, one thread per live position i < n_live: a ray with a key writes
+// its hit, a ray whose walk left the volume its miss; every other ray stays
+// live.  Bit i of `alive` (warp ballots) marks the survivors.
+__global__ void __launch_bounds__(256) resolve_kernel(const uint32_t *__restrict__ live0,
+                                                      const uint32_t *__restrict__ live1,
+                                                      const PassState *__restrict__ ps, int Dx, int Dy, VolGeom g,
+                                                      unsigned long long *__restrict__ keys,
+                                                      const uint32_t *__restrict__ rbid,
+                                                      uint64_t *__restrict__ state_in,
+                                                      const uint64_t *__restrict__ state_out,
+                                                      uint8_t *__restrict__ status, float *__restrict__ depth,
+                                                      uint32_t *__restrict__ rgba, uint32_t *__restrict__ block,
+                                                      uint64_t *__restrict__ cell, int32_t *__restrict__ final_pass,
+                                                      uint32_t *__restrict__ alive_bits, uint32_t *ctr)
+{
+    if (ctr[C_OVERFLOW]) return;
+    const uint32_t *live = (ps->parity & 1) ? live1 : live0;
+    const uint32_t n_live = ps->n_live, nproc = ps->nproc, kk = ps->kk;
+    const int64_t n_pad = (int64_t)ps->live_words * 32;
+    const int pass = (int)ps->pass + 1;
+    uint32_t nh = 0, ng = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad;
+         i += (int64_t)gridDim.x * blockDim.x) {   // whole warps iterate
+        bool alive = i < (int64_t)n_live;
         if (i < (int64_t)nproc) {
+            const uint32_t ray = live[i];
             const unsigned long long key = keys[ray];
             const uint64_t st = state_out[ray];
             state_in[ray] = st;
@@ -1144,33 +1167,41 @@ struct ResolveCount {
                 final_pass[ray] = pass;
                 status[ray] = 1;
                 keys[ray] = kNoKey;
-                alive = 0;
-                hit = 1;
+                alive = false;
+                ++nh;
             } else if ((st >> 48) & kDone) {
                 final_pass[ray] = pass;
                 status[ray] = 2;
-                alive = 0;
-                gone = 1;
+                alive = false;
+                ++ng;
             }
         }
-        unsigned m = __activemask();
-        uint32_t nh = __popc(__ballot_sync(m, hit)), ng = __popc(__ballot_sync(m, gone));
-        if ((threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) {
-            if (nh) atomicAdd(&ctr[C_HIT], nh);
-            if (ng) atomicAdd(&ctr[C_MISSRAY], ng);
-        }
-        return alive;
+        const unsigned bits = __ballot_sync(0xFFFFFFFFu, alive);
+        if ((threadIdx.x & 31) == 0) alive_bits[i >> 5] = bits;
     }
-};
+    nh = __reduce_add_sync(0xFFFFFFFFu, nh);
+    ng = __reduce_add_sync(0xFFFFFFFFu, ng);
+    if ((threadIdx.x & 31) == 0) {
+        if (nh) atomicAdd(&ctr[C_HIT], nh);
+        if (ng) atomicAdd(&ctr[C_MISSRAY], ng);
+    }
+}
 
+// the next live list from the alive bitmap, in order
 struct LiveEmit {
+    const uint32_t *bits;
     uint32_t *live0, *live1;
     const PassState *ps;
-    __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
+    __device__ void operator()(int64_t w, uint32_t pre, uint32_t) const
     {
-        if (!c) return;
-        if (ps->parity & 1) live0[pre] = live1[i];
-        else live1[pre] = live0[i];
+        uint32_t x = bits[w];
+        const uint32_t *src = (ps->parity & 1) ? live1 : live0;
+        uint32_t *dst = (ps->parity & 1) ? live0 : live1;
+        while (x) {
+            int b = __ffs(x) - 1;
+            x &= x - 1;
+            dst[pre++] = src[32 * w + b];
+        }
     }
 };
 
@@ -1187,6 +1218,7 @@ __global__ void begin_pass_kernel(PassState *ps, uint32_t *ctr)
         ps->kk = k;
         ps->nproc = n;
         ps->retries = 0;
+        ps->live_words = (n + 31) / 32;
     }
 }
 
@@ -1242,20 +1274,40 @@ __global__ void end_pass_kernel(PassState *ps, const uint32_t *ctr, spr_pass_sta
     if (use_handle) cudaGraphSetConditional(handle, ps->run);
 }
 
-__global__ void cache_reset_kernel(PassState *ps)
+// Empty the cache by undoing only what was used: every slot below
+// max(fresh_lo, fresh_hi) (slots above were never handed out) drops its
+// block's mapping and its touched flag; then every slot is fresh again.
+// Runs when `reset` is null or *reset is nonzero.
+__global__ void cache_clear_used_kernel(PassState *ps, const uint32_t *reset, uint32_t *__restrict__ slot_blk,
+                                        uint32_t *__restrict__ blk_slot, uint8_t *__restrict__ touched,
+                                        int64_t n_slots)
 {
-    if (threadIdx.x != 0) return;
+    if (reset && !*reset) return;
+    const int64_t hi = min((int64_t)max(ps->fresh_lo, ps->fresh_hi), n_slots);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = slot_blk[i];
+        if (b != kNone) {
+            blk_slot[b] = kNone;
+            slot_blk[i] = kNone;
+        }
+        touched[i] = 0;
+    }
+}
+
+__global__ void cache_reset_kernel(PassState *ps, const uint32_t *reset)
+{
+    if (threadIdx.x != 0 || (reset && !*reset)) return;
     ps->fresh_lo = ps->fresh_hi = 0;
     ps->n_used = 0;
 }
 
-__global__ void config_kernel(PassState *ps, uint32_t spec_mode, uint32_t k_fixed, uint32_t k_max, uint32_t npix)
+__global__ void config_kernel(PassState *ps, const DevParams *p)
 {
     if (threadIdx.x != 0) return;
-    ps->spec_mode = spec_mode;
-    ps->k_fixed = k_fixed;
-    ps->k_max = k_max;
-    ps->npix = npix;
+    ps->spec_mode = p->spec_mode;
+    ps->k_fixed = p->k_fixed;
+    ps->k_max = p->k_max;
+    ps->npix = p->npix;
 }
 
 // after ray generation: the live list is list 0 and the pass count restarts
@@ -1319,6 +1371,7 @@ struct spr_renderer {
     int grid_isect = 1;   // one wave of the work-queue kernel
     bool need_raygen = true;
     bool cache_dirty = true;
+    bool cache_init = false;    // slot tables consistent (else the next reset clears them whole)
     bool params_dirty = true;   // camera / isovalue / speculation not yet on the device
     int pass = 0;               // passes completed (host mirror of the device state)
     uint32_t n_live = 0;
@@ -1330,6 +1383,7 @@ struct spr_renderer {
     DevBuf rbid, erank, E;
     int64_t cap_entries = 0;
     DevBuf vis_bits, act_bits, vis_wpre, act_wpre, ivis, iact, nbrays, obrays;
+    DevBuf lbits;   // enter bits at ray generation, alive bits at resolve (one per live position)
     int64_t nwords = 0, cap_act = 0;
     DevBuf cache, blk_slot, slot_blk, lru[2], touched, miss, victim;
     int64_t launches = 0;         // kernels launched since the last render started
@@ -1341,7 +1395,10 @@ struct spr_renderer {
     // generation), [1] cache, [2] LRU order
     DevBuf scan_status[3], scan_ticket[3];
     DevBuf ctr;
-    DevBuf ps, recs, camd;        // device pass state, per-pass records, camera + isovalue
+    DevBuf ps, recs, camd;        // device pass state, per-pass records, DevParams
+    DevParams *h_params = nullptr;  // pinned source of camd
+    cudaEvent_t ev_upload = nullptr;  // the last copy out of h_params has run
+    cudaGraphExec_t gstart = nullptr, glimit = nullptr;  // render start with / without ray generation
     static constexpr int kRecCap = 4096;
     PassState *h_ps = nullptr;    // pinned
     uint32_t *h_ctr = nullptr;    // pinned
@@ -1364,9 +1421,13 @@ void drop_graph(spr_renderer *r)
     if (r->gexec) cudaGraphExecDestroy(r->gexec);
     if (r->graph) cudaGraphDestroy(r->graph);
     if (r->gprof) cudaGraphExecDestroy(r->gprof);
+    if (r->gstart) cudaGraphExecDestroy(r->gstart);
+    if (r->glimit) cudaGraphExecDestroy(r->glimit);
     r->gprof = nullptr;
     r->gexec = nullptr;
     r->graph = nullptr;
+    r->gstart = nullptr;
+    r->glimit = nullptr;
 }
 
 void free_all(spr_renderer *r)
@@ -1380,10 +1441,14 @@ void free_all(spr_renderer *r)
                       &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
                       &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
                       &r->scan_ticket[1], &r->scan_ticket[2], &r->ctr, &r->occ_fine, &r->occ_super,
-                      &r->ps, &r->recs, &r->camd};
+                      &r->ps, &r->recs, &r->camd, &r->lbits};
     for (DevBuf *b : bufs) buf_free(*b, nullptr);
     if (r->h_ctr) cudaFreeHost(r->h_ctr);
     if (r->h_ps) cudaFreeHost(r->h_ps);
+    if (r->h_params) cudaFreeHost(r->h_params);
+    r->h_params = nullptr;
+    if (r->ev_upload) cudaEventDestroy(r->ev_upload);
+    r->ev_upload = nullptr;
     r->h_ctr = nullptr;
     r->h_ps = nullptr;
     for (auto &e : r->ev)
@@ -1438,14 +1503,25 @@ int ensure_scan_scratch(spr_renderer *r, cudaStream_t s)
     return SPR_OK;
 }
 
+// Empty the cache.  The first time (and after the slot tables are
+// reallocated) every table is cleared; afterwards only the used slots are
+// undone, which costs O(slots used) instead of O(blocks).
 int reset_cache(spr_renderer *r, cudaStream_t s)
 {
     const VolGeom &g = r->vol->g;
-    SPR_CUDA_TRY(cudaMemsetAsync(r->blk_slot.p, 0xFF, sizeof(uint32_t) * g.nblocks, s));
-    SPR_CUDA_TRY(cudaMemsetAsync(r->slot_blk.p, 0xFF, sizeof(uint32_t) * r->n_slots, s));
-    SPR_CUDA_TRY(cudaMemsetAsync(r->touched.p, 0, r->n_slots, s));
+    if (!r->cache_init) {
+        SPR_CUDA_TRY(cudaMemsetAsync(r->blk_slot.p, 0xFF, sizeof(uint32_t) * g.nblocks, s));
+        SPR_CUDA_TRY(cudaMemsetAsync(r->slot_blk.p, 0xFF, sizeof(uint32_t) * r->n_slots, s));
+        SPR_CUDA_TRY(cudaMemsetAsync(r->touched.p, 0, r->n_slots, s));
+        r->cache_init = true;
+    } else {
+        cache_clear_used_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, s>>>(
+            r->ps.as<PassState>(), nullptr, r->slot_blk.as<uint32_t>(), r->blk_slot.as<uint32_t>(),
+            r->touched.as<uint8_t>(), r->n_slots);
+        count_launch();
+    }
     // every slot is fresh again; the used-slot lists are empty
-    cache_reset_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>());
+    cache_reset_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), nullptr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     r->cache_dirty = false;
@@ -1458,8 +1534,8 @@ Geo make_geo(const spr_renderer *r)
     P.g = r->vol->g;
     P.fine = r->vol->fine.as<float2>();
     P.coarse = r->vol->coarse.as<float2>();
-    P.camd = r->camd.as<Cam>();
-    P.isod = reinterpret_cast<const float *>(r->camd.as<char>() + sizeof(Cam));
+    P.camd = &r->camd.as<DevParams>()->cam;
+    P.isod = &r->camd.as<DevParams>()->iso;
     P.W = r->W;
     P.occ = r->occ;
     return P;
@@ -1481,57 +1557,78 @@ int update_occupancy(spr_renderer *r, cudaStream_t s)
     return SPR_OK;
 }
 
-// camera, isovalue and the speculation configuration to the device
+// Fill the pinned parameter block (after the previous copy out of it ran).
+int write_params(spr_renderer *r, uint32_t more, uint32_t reset)
+{
+    SPR_CUDA_TRY(cudaEventSynchronize(r->ev_upload));
+    DevParams &h = *r->h_params;
+    h.cam = r->cam;
+    h.iso = r->iso;
+    h.spec_mode = (uint32_t)r->spec_mode;
+    h.k_fixed = (uint32_t)r->k_fixed;
+    h.k_max = (uint32_t)r->k_max;
+    h.npix = (uint32_t)r->npix;
+    h.more = more;
+    h.reset = reset;
+    h.pad = 0;
+    return SPR_OK;
+}
+
+// camera, isovalue and the speculation configuration to the device (the
+// host-driven path; the graph path copies them inside its start graph)
 int upload_params(spr_renderer *r, cudaStream_t s)
 {
     if (!r->params_dirty) return SPR_OK;
-    struct {
-        Cam cam;
-        float iso;
-    } h{r->cam, r->iso};
-    SPR_CUDA_TRY(cudaMemcpyAsync(r->camd.p, &h, sizeof h, cudaMemcpyHostToDevice, s));
-    config_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), (uint32_t)r->spec_mode, (uint32_t)r->k_fixed,
-                                   (uint32_t)r->k_max, (uint32_t)r->npix);
+    SPR_TRY(write_params(r, 0u, 0u));
+    SPR_CUDA_TRY(cudaMemcpyAsync(r->camd.p, r->h_params, sizeof(DevParams), cudaMemcpyHostToDevice, s));
+    SPR_CUDA_TRY(cudaEventRecord(r->ev_upload, s));
+    config_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), r->camd.as<DevParams>());
     count_launch();
-    SPR_CUDA_TRY(cudaStreamSynchronize(s));   // h lives on this stack frame
+    SPR_CUDA_TRY(cudaGetLastError());
     r->params_dirty = false;
     return SPR_OK;
 }
 
-// ray generation (no host synchronisation): rays, live list 0, pass state
-int enqueue_raygen(spr_renderer *r, cudaStream_t s)
+// ray generation, device work only (capturable): rays, live list 0, pass state
+int enqueue_raygen_body(spr_renderer *r, cudaStream_t s)
 {
-    SPR_TRY(update_occupancy(r, s));
     uint32_t *ctr = r->ctr.as<uint32_t>();
     SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
     // each attempt clears the bitmaps after use; this covers a render that
     // stopped inside an attempt
     SPR_CUDA_TRY(cudaMemsetAsync(r->vis_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
     SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
-    RaygenCount cf{make_geo(r),
-                   r->H,
-                   r->state_in.as<uint64_t>(),
-                   r->status.as<uint8_t>(),
-                   r->keys.as<uint64_t>(),
-                   r->fb_depth.as<float>(),
-                   r->fb_rgba.as<uint32_t>(),
-                   r->fb_block.as<uint32_t>(),
-                   r->fb_cell.as<uint64_t>(),
-                   r->fb_final.as<int32_t>()};
-    IndexEmit ef{r->live[0].as<uint32_t>(), r->W, r->H};
-    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], ctr + C_SCANFLAGS, tiled_ray_count(r->W, r->H), nullptr,
-                        cf, ef, ctr + C_NLIVE, s));
+    const int64_t n_tiled = tiled_ray_count(r->W, r->H);
+    raygen_kernel<<<grid_for(n_tiled, 256, 8), 256, 0, s>>>(
+        make_geo(r), r->H, r->state_in.as<uint64_t>(), r->status.as<uint8_t>(), r->keys.as<uint64_t>(),
+        r->fb_depth.as<float>(), r->fb_rgba.as<uint32_t>(), r->fb_block.as<uint32_t>(), r->fb_cell.as<uint64_t>(),
+        r->fb_final.as<int32_t>(), r->lbits.as<uint32_t>(), n_tiled);
+    count_launch();
+    SPR_CUDA_TRY(cudaGetLastError());
+    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], ctr + C_SCANFLAGS, n_tiled / 32, nullptr,
+                        BitsCount{r->lbits.as<uint32_t>(), nullptr},
+                        EnterEmit{r->lbits.as<uint32_t>(), r->live[0].as<uint32_t>(), r->W, r->H}, ctr + C_NLIVE, s));
     after_raygen_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), ctr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
+    return SPR_OK;
+}
+
+// ray generation (no host synchronisation)
+int enqueue_raygen(spr_renderer *r, cudaStream_t s)
+{
+    SPR_TRY(update_occupancy(r, s));
+    SPR_TRY(enqueue_raygen_body(r, s));
     r->need_raygen = false;
     r->pass = 0;
     return SPR_OK;
 }
 
-__global__ void set_limit_kernel(PassState *ps, uint32_t more)
+// allow `more` passes (*more_dev when given) from the current one
+__global__ void set_limit_kernel(PassState *ps, uint32_t more, const uint32_t *more_dev)
 {
     if (threadIdx.x != 0) return;
+    if (more_dev) more = *more_dev;
     ps->max_passes = ps->pass + more;
     ps->run = (ps->n_live > 0 && more > 0) ? 1u : 0u;
 }
@@ -1658,25 +1755,16 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     if (events) SPR_CUDA_TRY(record(r->ev[5], s, capturing));
 
     // (f) resolve hits and exits, compact the live rays in order, end the pass
-    ResolveCount rc{live0,
-                    live1,
-                    ps,
-                    g.dims[0],
-                    g.dims[1],
-                    g,
-                    r->keys.as<unsigned long long>(),
-                    r->rbid.as<uint32_t>(),
-                    r->state_in.as<uint64_t>(),
-                    r->state_out.as<uint64_t>(),
-                    r->status.as<uint8_t>(),
-                    r->fb_depth.as<float>(),
-                    r->fb_rgba.as<uint32_t>(),
-                    r->fb_block.as<uint32_t>(),
-                    r->fb_cell.as<uint64_t>(),
-                    r->fb_final.as<int32_t>(),
-                    ctr};
-    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, r->npix, &ps->n_live, rc,
-                        LiveEmit{live0, live1, ps}, ctr + C_NLIVE, s));
+    resolve_kernel<<<grid_for(r->npix, 256, 8), 256, 0, s>>>(
+        live0, live1, ps, g.dims[0], g.dims[1], g, r->keys.as<unsigned long long>(), r->rbid.as<uint32_t>(),
+        r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(), r->status.as<uint8_t>(), r->fb_depth.as<float>(),
+        r->fb_rgba.as<uint32_t>(), r->fb_block.as<uint32_t>(), r->fb_cell.as<uint64_t>(), r->fb_final.as<int32_t>(),
+        r->lbits.as<uint32_t>(), ctr);
+    count_launch();
+    SPR_CUDA_TRY(cudaGetLastError());
+    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, (r->npix + 31) / 32, &ps->live_words,
+                        BitsCount{r->lbits.as<uint32_t>(), ctr + C_OVERFLOW},
+                        LiveEmit{r->lbits.as<uint32_t>(), live0, live1, ps}, ctr + C_NLIVE, s));
     if (fork) {   // the LRU order must be complete before the pass ends
         SPR_CUDA_TRY(cudaEventRecord(ev_lru, sl));
         SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_lru, 0));
@@ -1752,7 +1840,7 @@ int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
         if (out) *out = st;
         return SPR_OK;
     }
-    set_limit_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), 1u);
+    set_limit_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), 1u, nullptr);
     count_launch();
     float stage_ms[6] = {0, 0, 0, 0, 0, 0};
     const int before = r->pass;
@@ -1810,6 +1898,47 @@ int build_prof_graph(spr_renderer *r)
     if (e != cudaSuccess) {
         r->gprof = nullptr;
         return set_error(SPR_ERR_CUDA, "profiling graph: %s", cudaGetErrorString(e));
+    }
+    return SPR_OK;
+}
+
+// The start of a render as one graph: copy the parameter block, apply the
+// speculation settings, empty the cache if asked, generate rays (with_raygen)
+// and set the pass limit.  Kernels in it: 4, and 3 more with ray generation.
+int build_start_graph(spr_renderer *r, bool with_raygen)
+{
+    cudaGraphExec_t &ge = with_raygen ? r->gstart : r->glimit;
+    if (ge) return SPR_OK;
+    if (!r->cap_stream) SPR_CUDA_TRY(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = r->cap_stream;
+    DevParams *dp = r->camd.as<DevParams>();
+    PassState *ps = r->ps.as<PassState>();
+    SPR_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int64_t saved = r->launches;
+    int rc = SPR_OK;
+    cudaError_t e = cudaMemcpyAsync(dp, r->h_params, sizeof(DevParams), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) {
+        config_kernel<<<1, 32, 0, cs>>>(ps, dp);
+        cache_clear_used_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, cs>>>(
+            ps, &dp->reset, r->slot_blk.as<uint32_t>(), r->blk_slot.as<uint32_t>(), r->touched.as<uint8_t>(),
+            r->n_slots);
+        cache_reset_kernel<<<1, 32, 0, cs>>>(ps, &dp->reset);
+        if (with_raygen) rc = enqueue_raygen_body(r, cs);
+        set_limit_kernel<<<1, 32, 0, cs>>>(ps, 0u, &dp->more);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    r->launches = saved;
+    if (e != cudaSuccess || e2 != cudaSuccess || rc != SPR_OK) {
+        if (g) cudaGraphDestroy(g);
+        if (rc != SPR_OK) return rc;
+        return set_error(SPR_ERR_CUDA, "start capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ge = nullptr;
+        return set_error(SPR_ERR_CUDA, "start graph: %s", cudaGetErrorString(e));
     }
     return SPR_OK;
 }
@@ -1889,8 +2018,9 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         (rc = buf_alloc(r->scan_ticket[1], 64, s)) || (rc = buf_alloc(r->scan_ticket[2], 64, s)) ||
         (rc = buf_alloc(r->ctr, sizeof(uint32_t) * C_COUNT, s)) ||
         (rc = buf_alloc(r->ps, sizeof(PassState), s)) ||
+        (rc = buf_alloc(r->lbits, 4 * (tiled_ray_count(width, height) / 32 + 1), s)) ||
         (rc = buf_alloc(r->recs, sizeof(spr_pass_stats) * spr_renderer::kRecCap, s)) ||
-        (rc = buf_alloc(r->camd, sizeof(Cam) + 16, s))) {
+        (rc = buf_alloc(r->camd, sizeof(DevParams) + 16, s))) {
         free_all(r);
         delete r;
         return rc;
@@ -1901,7 +2031,9 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         cudaMemset(r->vis_bits.p, 0, 4 * r->nwords) != cudaSuccess ||
         cudaMemset(r->act_bits.p, 0, 4 * r->nwords) != cudaSuccess ||
         cudaMallocHost((void **)&r->h_ctr, sizeof(uint32_t) * C_COUNT) != cudaSuccess ||
-        cudaMallocHost((void **)&r->h_ps, sizeof(PassState)) != cudaSuccess) {
+        cudaMallocHost((void **)&r->h_ps, sizeof(PassState)) != cudaSuccess ||
+        cudaMallocHost((void **)&r->h_params, sizeof(DevParams)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->ev_upload, cudaEventDisableTiming) != cudaSuccess) {
         free_all(r);
         delete r;
         return set_error(SPR_ERR_OUT_OF_MEMORY, "pinned host allocation failed");
@@ -2014,6 +2146,7 @@ extern "C" int spr_set_cache_budget(spr_renderer *r, size_t bytes)
         return rc;
     r->n_slots = slots;
     r->cache_dirty = true;
+    r->cache_init = false;
     r->need_raygen = true;
     return SPR_OK;
 }
@@ -2094,22 +2227,35 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
     } else {
         // the whole render on the device: ray generation, then one graph
         // launch whose while node runs passes until none is live
-        SPR_TRY(prepare(r, s));
+        // parameters, cache reset, ray generation and the pass limit travel
+        // in the start graph; only first-time clears and occupancy masks for
+        // a new isovalue are launched from here
+        SPR_TRY(ensure_entry_buffers(r, s));
+        SPR_TRY(ensure_scan_scratch(r, s));
         struct Scope {
             Scope(int64_t *p) { g_launch_counter = p; }
             ~Scope() { g_launch_counter = nullptr; }
         } scope(&r->launches);
-        SPR_CUDA_TRY(cudaEventRecord(r->ev[7], s));
-        if (fresh) {
-            r->launches = 0;
-            SPR_TRY(enqueue_raygen(r, s));
-        }
-        SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
+        if (fresh) r->launches = 0;
+        if (r->cache_dirty && !r->cache_init) SPR_TRY(reset_cache(r, s));
+        const uint32_t reset = r->cache_dirty ? 1u : 0u;
+        if (fresh) SPR_TRY(update_occupancy(r, s));
+        SPR_TRY(build_start_graph(r, fresh));
         SPR_TRY(build_graph(r));
+        SPR_TRY(write_params(r, (uint32_t)max_passes, reset));
+        SPR_CUDA_TRY(cudaEventRecord(r->ev[7], s));
+        SPR_CUDA_TRY(cudaGraphLaunch(fresh ? r->gstart : r->glimit, s));
+        SPR_CUDA_TRY(cudaEventRecord(r->ev_upload, s));
+        SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
+        r->launches += fresh ? 7 : 4;
+        r->cache_dirty = false;
+        r->params_dirty = false;
+        if (fresh) {
+            r->need_raygen = false;
+            r->pass = 0;
+        }
         int first = r->pass;
         const PassState before = *r->h_ps;
-        set_limit_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), (uint32_t)max_passes);
-        count_launch();
         SPR_CUDA_TRY(cudaGraphLaunch(r->gexec, s));
         SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
         SPR_TRY(read_state(r, s));
