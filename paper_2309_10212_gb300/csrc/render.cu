@@ -1222,8 +1222,10 @@ __global__ void begin_pass_kernel(PassState *ps, uint32_t *ctr)
     }
 }
 
+// ends an attempt; `recs` and `mirror` live in mapped host memory, so the
+// host reads the pass state and records after one stream synchronisation
 __global__ void end_pass_kernel(PassState *ps, const uint32_t *ctr, spr_pass_stats *recs, uint32_t n_recs,
-                                cudaGraphConditionalHandle handle, int use_handle)
+                                PassState *mirror, cudaGraphConditionalHandle handle, int use_handle)
 {
     if (threadIdx.x != 0) return;
     if (ps->n_live > 0) ps->attempts += 1;
@@ -1271,6 +1273,7 @@ __global__ void end_pass_kernel(PassState *ps, const uint32_t *ctr, spr_pass_sta
         ps->open = 0;
         ps->run = (ps->n_live > 0 && ps->pass < ps->max_passes) ? 1u : 0u;
     }
+    *mirror = *ps;
     if (use_handle) cudaGraphSetConditional(handle, ps->run);
 }
 
@@ -1311,7 +1314,7 @@ __global__ void config_kernel(PassState *ps, const DevParams *p)
 }
 
 // after ray generation: the live list is list 0 and the pass count restarts
-__global__ void after_raygen_kernel(PassState *ps, const uint32_t *ctr)
+__global__ void after_raygen_kernel(PassState *ps, const uint32_t *ctr, PassState *mirror)
 {
     if (threadIdx.x != 0) return;
     ps->n_live = ctr[C_NLIVE];
@@ -1324,6 +1327,7 @@ __global__ void after_raygen_kernel(PassState *ps, const uint32_t *ctr)
     ps->tot_decoded = ps->tot_entries = ps->tot_evicted = ps->tot_hits = 0ull;
     ps->error = ctr[C_SCANFLAGS] ? 1u : 0u;
     ps->run = ps->n_live > 0 ? 1u : 0u;
+    *mirror = *ps;
 }
 
 // -------------------------------------------------------------- utilities
@@ -1395,12 +1399,16 @@ struct spr_renderer {
     // generation), [1] cache, [2] LRU order
     DevBuf scan_status[3], scan_ticket[3];
     DevBuf ctr;
-    DevBuf ps, recs, camd;        // device pass state, per-pass records, DevParams
+    DevBuf ps, camd;              // device pass state, DevParams
+    // mapped host memory written by the device: per-pass records and a copy
+    // of the pass state after each pass (host pointers h_*, device aliases d_*)
+    spr_pass_stats *h_recs = nullptr, *d_recs = nullptr;
+    PassState *d_hps = nullptr;
     DevParams *h_params = nullptr;  // pinned source of camd
     cudaEvent_t ev_upload = nullptr;  // the last copy out of h_params has run
     cudaGraphExec_t gstart = nullptr, glimit = nullptr;  // render start with / without ray generation
     static constexpr int kRecCap = 4096;
-    PassState *h_ps = nullptr;    // pinned
+    PassState *h_ps = nullptr;    // mapped (see d_hps)
     uint32_t *h_ctr = nullptr;    // pinned
     cudaEvent_t ev[8] = {};
     // fork/join of the pass's branches (no timing)
@@ -1441,10 +1449,13 @@ void free_all(spr_renderer *r)
                       &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
                       &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
                       &r->scan_ticket[1], &r->scan_ticket[2], &r->ctr, &r->occ_fine, &r->occ_super,
-                      &r->ps, &r->recs, &r->camd, &r->lbits};
+                      &r->ps, &r->camd, &r->lbits};
     for (DevBuf *b : bufs) buf_free(*b, nullptr);
     if (r->h_ctr) cudaFreeHost(r->h_ctr);
     if (r->h_ps) cudaFreeHost(r->h_ps);
+    if (r->h_recs) cudaFreeHost(r->h_recs);
+    r->h_recs = r->d_recs = nullptr;
+    r->d_hps = nullptr;
     if (r->h_params) cudaFreeHost(r->h_params);
     r->h_params = nullptr;
     if (r->ev_upload) cudaEventDestroy(r->ev_upload);
@@ -1608,7 +1619,7 @@ int enqueue_raygen_body(spr_renderer *r, cudaStream_t s)
     SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], ctr + C_SCANFLAGS, n_tiled / 32, nullptr,
                         BitsCount{r->lbits.as<uint32_t>(), nullptr},
                         EnterEmit{r->lbits.as<uint32_t>(), r->live[0].as<uint32_t>(), r->W, r->H}, ctr + C_NLIVE, s));
-    after_raygen_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), ctr);
+    after_raygen_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), ctr, r->d_hps);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     return SPR_OK;
@@ -1769,8 +1780,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
         SPR_CUDA_TRY(cudaEventRecord(ev_lru, sl));
         SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_lru, 0));
     }
-    end_pass_kernel<<<1, 32, 0, s>>>(ps, ctr, r->recs.as<spr_pass_stats>(), (uint32_t)spr_renderer::kRecCap, h,
-                                     use_h);
+    end_pass_kernel<<<1, 32, 0, s>>>(ps, ctr, r->d_recs, (uint32_t)spr_renderer::kRecCap, r->d_hps, h, use_h);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     if (events) SPR_CUDA_TRY(record(r->ev[6], s, capturing));
@@ -1798,8 +1808,7 @@ int prepare(spr_renderer *r, cudaStream_t s)
 
 int read_state(spr_renderer *r, cudaStream_t s)
 {
-    SPR_CUDA_TRY(cudaMemcpyAsync(r->h_ps, r->ps.p, sizeof(PassState), cudaMemcpyDeviceToHost, s));
-    SPR_CUDA_TRY(cudaStreamSynchronize(s));
+    SPR_CUDA_TRY(cudaStreamSynchronize(s));   // h_ps is written by the last pass kernel
     const PassState &h = *r->h_ps;
     r->n_live = h.n_live;
     r->n_enter = h.n_enter;
@@ -1862,8 +1871,7 @@ int do_pass(spr_renderer *r, cudaStream_t s, spr_pass_stats *out)
     }
     if (r->pass == before) return set_error(SPR_ERR_DEVICE_ERROR, "a pass did not fit the cache after 64 attempts");
     if (before < spr_renderer::kRecCap) {
-        SPR_CUDA_TRY(cudaMemcpyAsync(&st, r->recs.as<spr_pass_stats>() + before, sizeof st, cudaMemcpyDeviceToHost, s));
-        SPR_CUDA_TRY(cudaStreamSynchronize(s));
+        st = r->h_recs[before];   // written by the pass's last kernel; the stream was synchronised
     } else {
         st.pass = before + 1;   // past the record buffer: counts only in the render totals
     }
@@ -2019,7 +2027,6 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         (rc = buf_alloc(r->ctr, sizeof(uint32_t) * C_COUNT, s)) ||
         (rc = buf_alloc(r->ps, sizeof(PassState), s)) ||
         (rc = buf_alloc(r->lbits, 4 * (tiled_ray_count(width, height) / 32 + 1), s)) ||
-        (rc = buf_alloc(r->recs, sizeof(spr_pass_stats) * spr_renderer::kRecCap, s)) ||
         (rc = buf_alloc(r->camd, sizeof(DevParams) + 16, s))) {
         free_all(r);
         delete r;
@@ -2031,13 +2038,19 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         cudaMemset(r->vis_bits.p, 0, 4 * r->nwords) != cudaSuccess ||
         cudaMemset(r->act_bits.p, 0, 4 * r->nwords) != cudaSuccess ||
         cudaMallocHost((void **)&r->h_ctr, sizeof(uint32_t) * C_COUNT) != cudaSuccess ||
-        cudaMallocHost((void **)&r->h_ps, sizeof(PassState)) != cudaSuccess ||
+        cudaHostAlloc((void **)&r->h_ps, sizeof(PassState), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&r->d_hps, r->h_ps, 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&r->h_recs, sizeof(spr_pass_stats) * spr_renderer::kRecCap, cudaHostAllocMapped) !=
+            cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&r->d_recs, r->h_recs, 0) != cudaSuccess ||
         cudaMallocHost((void **)&r->h_params, sizeof(DevParams)) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev_upload, cudaEventDisableTiming) != cudaSuccess) {
         free_all(r);
         delete r;
         return set_error(SPR_ERR_OUT_OF_MEMORY, "pinned host allocation failed");
     }
+    memset(r->h_ps, 0, sizeof(PassState));
+    memset(r->h_recs, 0, sizeof(spr_pass_stats) * spr_renderer::kRecCap);
     for (auto &e : r->ev) cudaEventCreate(&e);
     for (auto &e : r->jev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
     for (auto &a : r->aux) cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
@@ -2269,9 +2282,7 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
         int64_t attempts = (int64_t)after.attempts - (same ? (int64_t)before.attempts : 0);
         int nrec = std::max(0, std::min(first + passes, spr_renderer::kRecCap) - first);
         if (per_pass && nrec > 0) {
-            SPR_CUDA_TRY(cudaMemcpyAsync(per_pass, r->recs.as<spr_pass_stats>() + first, sizeof(spr_pass_stats) * nrec,
-                                         cudaMemcpyDeviceToHost, s));
-            SPR_CUDA_TRY(cudaStreamSynchronize(s));
+            memcpy(per_pass, r->h_recs + first, sizeof(spr_pass_stats) * nrec);
         }
         r->launches += (int64_t)r->graph_kernels * std::max<int64_t>(attempts, 1);
         float t_all = 0.f, t_ray = 0.f;
