@@ -89,6 +89,13 @@ struct Cam {
     float eye[3], p00[3], du[3], dv[3];
 };
 
+// every slot fresh again, the used-slot lists empty
+__device__ __forceinline__ void lru_reset(PassState *ps)
+{
+    ps->fresh_lo = ps->fresh_hi = 0;
+    ps->n_used = 0;
+}
+
 // Per-render parameters in device memory, copied from a pinned host block by
 // the first node of the render's start graph (so the captured graphs stay
 // valid when the camera, isovalue, speculation or pass limit change).
@@ -419,8 +426,9 @@ __global__ void __launch_bounds__(256) raygen_kernel(Geo P, int H, uint64_t *__r
                                                      float *__restrict__ depth, uint32_t *__restrict__ rgba,
                                                      uint32_t *__restrict__ block, uint64_t *__restrict__ cell,
                                                      int32_t *__restrict__ final_pass, uint32_t *__restrict__ enter,
-                                                     int64_t n_tiled)
+                                                     int64_t n_tiled, PassState *ps, const uint32_t *lru_reset_flag)
 {
+    if (lru_reset_flag && blockIdx.x == 0 && threadIdx.x == 0 && *lru_reset_flag) lru_reset(ps);
     const Cam cam = *P.camd;
     const VolGeom &g = P.g;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiled;
@@ -1297,11 +1305,37 @@ __global__ void cache_clear_used_kernel(PassState *ps, const uint32_t *reset, ui
     }
 }
 
+// First kernel of a render's start graph: the speculation settings, zeroed
+// pass counters, and (when p->reset) the used slots emptied.  The LRU state
+// itself is reset by a later kernel, after every thread here has read it.
+__global__ void start_kernel(PassState *ps, const DevParams *p, uint32_t *ctr, uint32_t *__restrict__ slot_blk,
+                             uint32_t *__restrict__ blk_slot, uint8_t *__restrict__ touched, int64_t n_slots)
+{
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < C_COUNT) ctr[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) {
+            ps->spec_mode = p->spec_mode;
+            ps->k_fixed = p->k_fixed;
+            ps->k_max = p->k_max;
+            ps->npix = p->npix;
+        }
+    }
+    if (!p->reset) return;
+    const int64_t hi = min((int64_t)max(ps->fresh_lo, ps->fresh_hi), n_slots);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = slot_blk[i];
+        if (b != kNone) {
+            blk_slot[b] = kNone;
+            slot_blk[i] = kNone;
+        }
+        touched[i] = 0;
+    }
+}
+
 __global__ void cache_reset_kernel(PassState *ps, const uint32_t *reset)
 {
     if (threadIdx.x != 0 || (reset && !*reset)) return;
-    ps->fresh_lo = ps->fresh_hi = 0;
-    ps->n_used = 0;
+    lru_reset(ps);
 }
 
 __global__ void config_kernel(PassState *ps, const DevParams *p)
@@ -1314,7 +1348,7 @@ __global__ void config_kernel(PassState *ps, const DevParams *p)
 }
 
 // after ray generation: the live list is list 0 and the pass count restarts
-__global__ void after_raygen_kernel(PassState *ps, const uint32_t *ctr, PassState *mirror)
+__global__ void after_raygen_kernel(PassState *ps, const uint32_t *ctr, PassState *mirror, const uint32_t *more_dev)
 {
     if (threadIdx.x != 0) return;
     ps->n_live = ctr[C_NLIVE];
@@ -1327,6 +1361,10 @@ __global__ void after_raygen_kernel(PassState *ps, const uint32_t *ctr, PassStat
     ps->tot_decoded = ps->tot_entries = ps->tot_evicted = ps->tot_hits = 0ull;
     ps->error = ctr[C_SCANFLAGS] ? 1u : 0u;
     ps->run = ps->n_live > 0 ? 1u : 0u;
+    if (more_dev) {   // the pass limit of this call
+        ps->max_passes = ps->pass + *more_dev;
+        ps->run = (ps->n_live > 0 && *more_dev > 0) ? 1u : 0u;
+    }
     *mirror = *ps;
 }
 
@@ -1376,6 +1414,7 @@ struct spr_renderer {
     bool need_raygen = true;
     bool cache_dirty = true;
     bool cache_init = false;    // slot tables consistent (else the next reset clears them whole)
+    bool bits_dirty = false;    // a render stopped on a device error: clear the bitmaps
     bool params_dirty = true;   // camera / isovalue / speculation not yet on the device
     int pass = 0;               // passes completed (host mirror of the device state)
     uint32_t n_live = 0;
@@ -1601,27 +1640,38 @@ int upload_params(spr_renderer *r, cudaStream_t s)
 }
 
 // ray generation, device work only (capturable): rays, live list 0, pass state
-int enqueue_raygen_body(spr_renderer *r, cudaStream_t s)
+// In the start graph (dp given) the counters were zeroed by start_kernel,
+// ray generation resets the LRU state when asked and after_raygen applies
+// the pass limit; eagerly (dp null) the counters are zeroed here.
+int enqueue_raygen_body(spr_renderer *r, cudaStream_t s, const DevParams *dp)
 {
     uint32_t *ctr = r->ctr.as<uint32_t>();
-    SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
-    // each attempt clears the bitmaps after use; this covers a render that
-    // stopped inside an attempt
-    SPR_CUDA_TRY(cudaMemsetAsync(r->vis_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
-    SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
+    if (!dp) SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
     const int64_t n_tiled = tiled_ray_count(r->W, r->H);
     raygen_kernel<<<grid_for(n_tiled, 256, 8), 256, 0, s>>>(
         make_geo(r), r->H, r->state_in.as<uint64_t>(), r->status.as<uint8_t>(), r->keys.as<uint64_t>(),
         r->fb_depth.as<float>(), r->fb_rgba.as<uint32_t>(), r->fb_block.as<uint32_t>(), r->fb_cell.as<uint64_t>(),
-        r->fb_final.as<int32_t>(), r->lbits.as<uint32_t>(), n_tiled);
+        r->fb_final.as<int32_t>(), r->lbits.as<uint32_t>(), n_tiled, r->ps.as<PassState>(),
+        dp ? &dp->reset : nullptr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], ctr + C_SCANFLAGS, n_tiled / 32, nullptr,
                         BitsCount{r->lbits.as<uint32_t>(), nullptr},
                         EnterEmit{r->lbits.as<uint32_t>(), r->live[0].as<uint32_t>(), r->W, r->H}, ctr + C_NLIVE, s));
-    after_raygen_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), ctr, r->d_hps);
+    after_raygen_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), ctr, r->d_hps, dp ? &dp->more : nullptr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
+    return SPR_OK;
+}
+
+// Each attempt clears the bitmaps after their last reader.  A render that
+// stopped on a device error clears them here before the next one.
+int clear_bits_if_dirty(spr_renderer *r, cudaStream_t s)
+{
+    if (!r->bits_dirty) return SPR_OK;
+    SPR_CUDA_TRY(cudaMemsetAsync(r->vis_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
+    SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
+    r->bits_dirty = false;
     return SPR_OK;
 }
 
@@ -1629,10 +1679,20 @@ int enqueue_raygen_body(spr_renderer *r, cudaStream_t s)
 int enqueue_raygen(spr_renderer *r, cudaStream_t s)
 {
     SPR_TRY(update_occupancy(r, s));
-    SPR_TRY(enqueue_raygen_body(r, s));
+    SPR_TRY(clear_bits_if_dirty(r, s));
+    SPR_TRY(enqueue_raygen_body(r, s, nullptr));
     r->need_raygen = false;
     r->pass = 0;
     return SPR_OK;
+}
+
+// start of a call that continues a render: LRU reset if asked, pass limit
+__global__ void limit_kernel(PassState *ps, const DevParams *p)
+{
+    if (threadIdx.x != 0) return;
+    if (p->reset) lru_reset(ps);
+    ps->max_passes = ps->pass + p->more;
+    ps->run = (ps->n_live > 0 && p->more > 0) ? 1u : 0u;
 }
 
 // allow `more` passes (*more_dev when given) from the current one
@@ -1813,6 +1873,7 @@ int read_state(spr_renderer *r, cudaStream_t s)
     r->n_live = h.n_live;
     r->n_enter = h.n_enter;
     r->pass = (int)h.pass;
+    if (h.error) r->bits_dirty = true;
     if (h.error & 1u) return set_error(SPR_ERR_DEVICE_TIMEOUT, "a decoupled look-back wait timed out");
     if (h.error & 2u) return set_error(SPR_ERR_DEVICE_ERROR, "a kernel flagged an out-of-range block id");
     if (h.error & 4u) return set_error(SPR_ERR_DEVICE_ERROR, "a traversal exceeded its step bound");
@@ -1912,7 +1973,7 @@ int build_prof_graph(spr_renderer *r)
 
 // The start of a render as one graph: copy the parameter block, apply the
 // speculation settings, empty the cache if asked, generate rays (with_raygen)
-// and set the pass limit.  Kernels in it: 4, and 3 more with ray generation.
+// and set the pass limit.  Kernels in it: 4 with ray generation, else 2.
 int build_start_graph(spr_renderer *r, bool with_raygen)
 {
     cudaGraphExec_t &ge = with_raygen ? r->gstart : r->glimit;
@@ -1926,13 +1987,12 @@ int build_start_graph(spr_renderer *r, bool with_raygen)
     int rc = SPR_OK;
     cudaError_t e = cudaMemcpyAsync(dp, r->h_params, sizeof(DevParams), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) {
-        config_kernel<<<1, 32, 0, cs>>>(ps, dp);
-        cache_clear_used_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, cs>>>(
-            ps, &dp->reset, r->slot_blk.as<uint32_t>(), r->blk_slot.as<uint32_t>(), r->touched.as<uint8_t>(),
-            r->n_slots);
-        cache_reset_kernel<<<1, 32, 0, cs>>>(ps, &dp->reset);
-        if (with_raygen) rc = enqueue_raygen_body(r, cs);
-        set_limit_kernel<<<1, 32, 0, cs>>>(ps, 0u, &dp->more);
+        start_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, cs>>>(ps, dp, r->ctr.as<uint32_t>(),
+                                                                  r->slot_blk.as<uint32_t>(),
+                                                                  r->blk_slot.as<uint32_t>(),
+                                                                  r->touched.as<uint8_t>(), r->n_slots);
+        if (with_raygen) rc = enqueue_raygen_body(r, cs, dp);
+        else limit_kernel<<<1, 32, 0, cs>>>(ps, dp);
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
@@ -2253,6 +2313,7 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
         if (r->cache_dirty && !r->cache_init) SPR_TRY(reset_cache(r, s));
         const uint32_t reset = r->cache_dirty ? 1u : 0u;
         if (fresh) SPR_TRY(update_occupancy(r, s));
+        SPR_TRY(clear_bits_if_dirty(r, s));
         SPR_TRY(build_start_graph(r, fresh));
         SPR_TRY(build_graph(r));
         SPR_TRY(write_params(r, (uint32_t)max_passes, reset));
@@ -2260,7 +2321,7 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
         SPR_CUDA_TRY(cudaGraphLaunch(fresh ? r->gstart : r->glimit, s));
         SPR_CUDA_TRY(cudaEventRecord(r->ev_upload, s));
         SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
-        r->launches += fresh ? 7 : 4;
+        r->launches += fresh ? 4 : 2;
         r->cache_dirty = false;
         r->params_dirty = false;
         if (fresh) {
