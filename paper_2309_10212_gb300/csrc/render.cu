@@ -475,19 +475,21 @@ __global__ void __launch_bounds__(256) raygen_kernel(Geo P, int H, uint64_t *__r
     }
 }
 
+// one item per bit of a bitmap (compactions driven by ballot bitmaps)
+struct BitCount {
+    const uint32_t *bits;
+    const uint32_t *skip;
+    __device__ bool enabled() const { return !skip || !*skip; }
+    __device__ uint32_t operator()(int64_t i) const { return (bits[i >> 5] >> (i & 31)) & 1u; }
+};
+
 // live list 0 from the enter bitmap: position t -> its pixel
 struct EnterEmit {
-    const uint32_t *bits;
     uint32_t *out;
     int W, H;
-    __device__ void operator()(int64_t w, uint32_t pre, uint32_t) const
+    __device__ void operator()(int64_t t, uint32_t pre, uint32_t c) const
     {
-        uint32_t x = bits[w];
-        while (x) {
-            int b = __ffs(x) - 1;
-            x &= x - 1;
-            out[pre++] = (uint32_t)tiled_pixel(32 * w + b, W, H);
-        }
+        if (c) out[pre] = (uint32_t)tiled_pixel(t, W, H);
     }
 };
 
@@ -1197,19 +1199,13 @@ __global__ void __launch_bounds__(256) resolve_kernel(const uint32_t *__restrict
 
 // the next live list from the alive bitmap, in order
 struct LiveEmit {
-    const uint32_t *bits;
     uint32_t *live0, *live1;
     const PassState *ps;
-    __device__ void operator()(int64_t w, uint32_t pre, uint32_t) const
+    __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
     {
-        uint32_t x = bits[w];
-        const uint32_t *src = (ps->parity & 1) ? live1 : live0;
-        uint32_t *dst = (ps->parity & 1) ? live0 : live1;
-        while (x) {
-            int b = __ffs(x) - 1;
-            x &= x - 1;
-            dst[pre++] = src[32 * w + b];
-        }
+        if (!c) return;
+        if (ps->parity & 1) live0[pre] = live1[i];
+        else live1[pre] = live0[i];
     }
 };
 
@@ -1655,9 +1651,9 @@ int enqueue_raygen_body(spr_renderer *r, cudaStream_t s, const DevParams *dp)
         dp ? &dp->reset : nullptr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
-    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], ctr + C_SCANFLAGS, n_tiled / 32, nullptr,
-                        BitsCount{r->lbits.as<uint32_t>(), nullptr},
-                        EnterEmit{r->lbits.as<uint32_t>(), r->live[0].as<uint32_t>(), r->W, r->H}, ctr + C_NLIVE, s));
+    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], ctr + C_SCANFLAGS, n_tiled, nullptr,
+                        BitCount{r->lbits.as<uint32_t>(), nullptr},
+                        EnterEmit{r->live[0].as<uint32_t>(), r->W, r->H}, ctr + C_NLIVE, s));
     after_raygen_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), ctr, r->d_hps, dp ? &dp->more : nullptr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
@@ -1833,9 +1829,9 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
         r->lbits.as<uint32_t>(), ctr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
-    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, (r->npix + 31) / 32, &ps->live_words,
-                        BitsCount{r->lbits.as<uint32_t>(), ctr + C_OVERFLOW},
-                        LiveEmit{r->lbits.as<uint32_t>(), live0, live1, ps}, ctr + C_NLIVE, s));
+    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, r->npix, &ps->n_live,
+                        BitCount{r->lbits.as<uint32_t>(), ctr + C_OVERFLOW}, LiveEmit{live0, live1, ps},
+                        ctr + C_NLIVE, s));
     if (fork) {   // the LRU order must be complete before the pass ends
         SPR_CUDA_TRY(cudaEventRecord(ev_lru, sl));
         SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_lru, 0));
