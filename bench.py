@@ -43,6 +43,7 @@ METRIC = "ms to final image & per pass at 1280×720; decoded GB/s vs HBM peak; b
 # 4.70 MB over 4 launches); the live run supplies the steps and the time.
 TRAV_THREAD_INST_PER_STEP = 209.2
 TRAV_DRAM_BYTES_PER_LAUNCH = 1175872
+TRAV_COOP_BELOW = 16384   # passes with fewer live rays walk one ray per warp
 
 WORKLOADS = {
     "medium": dict(dims=(512, 512, 512), rate=2, iso=0.3, W=1280, H=720, poses=16,
@@ -399,9 +400,11 @@ def main():
                         "frac": round(dec_gbs / pk["hbm_gbs"], 4), "traffic": None,
                         "peak_source": pk["src"]}
         elif dom == "traverse":
-            per_pass = [p for _, ps in prof_stats for p in ps]
+            # passes walked one ray per thread (the kernel the per-step
+            # instruction count describes); fewer rays go one per warp
+            per_pass = [p for _, ps in prof_stats for p in ps if p["n_processed"] >= TRAV_COOP_BELOW]
             steps_ = sum(p["n_steps"] for p in per_pass)
-            ms_ = stage[dom]
+            ms_ = sum(p["ms_stage"][0] for p in per_pass)
             sms = torch.cuda.get_device_properties(local).multi_processor_count
             f_mhz = (clk.summary() or {}).get("sm_max_mhz") or 2070.0
             peak_ti = sms * 4 * 32 * f_mhz * 1e6 / 1e12
@@ -410,8 +413,8 @@ def main():
                         "peak": round(peak_ti, 2), "unit": "Tinst/s", "frac": round(ach / peak_ti, 4),
                         "traffic": TRAV_DRAM_BYTES_PER_LAUNCH,
                         "peak_source": "%d SMs x 4 issue slots x 32 lanes x %.0f MHz" % (sms, f_mhz),
-                        "work": "walk steps x %.1f thread instructions per step (ncu)"
-                                % TRAV_THREAD_INST_PER_STEP,
+                        "work": "walk steps x %.1f thread instructions per step (ncu), passes "
+                                "with >= %d live rays" % (TRAV_THREAD_INST_PER_STEP, TRAV_COOP_BELOW),
                         "hbm_frac": None}
         else:
             # the intersection is latency/ALU bound; report its algorithmic

@@ -495,6 +495,13 @@ struct EnterEmit {
 
 
 // ------------------------------------------------------------- traversal
+// Passes with fewer live rays than this walk one ray per warp
+// (traverse_coop_kernel); larger passes one ray per thread (traverse_kernel).
+#ifndef SPR_COOP_BELOW
+#define SPR_COOP_BELOW 16384
+#endif
+constexpr uint32_t kCoopBelow = SPR_COOP_BELOW;
+
 __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__restrict__ live0,
                                                        const uint32_t *__restrict__ live1,
                                                        const PassState *__restrict__ ps,
@@ -506,6 +513,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
 {
     const VolGeom &g = P.g;
     const uint32_t nproc = ps->nproc;
+    if (nproc < kCoopBelow) return;   // few rays: traverse_coop_kernel walks them
     const int kk = (int)ps->kk;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
     const Cam cam = *P.camd;
@@ -582,6 +590,217 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
             uint32_t mx = __reduce_max_sync(m, (uint32_t)steps);
             if ((threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicMax(&ctr[C_MAXSTEPS], mx);
         }
+    }
+}
+
+// One ray per warp, for passes whose few rays make the walk latency-bound.
+// The walk is the same as traverse_kernel's; inside an occupied coarse cell
+// the blocks are found in one step instead of one by one.  Lane 4a + k - 1
+// (a < 3, k = 1..4) takes the k-th block-plane crossing of the ray along
+// axis a inside the cell; the last crossing per axis leaves the cell or the
+// volume, and the first of those, T_exit, ends the cell.  Exact comparisons
+// with the other axes' crossings give each crossing the number of crossings
+// per axis up to its time (the block after it) and its rank among the
+// distinct times; crossings at one time from several axes are one
+// (diagonal) step, represented by the lowest axis, as in walk_step.  The
+// visible blocks of the cell are then taken in rank order, and the walk moves
+// to the block after T_exit.  Empty coarse and super cells are skipped with
+// skip_level, computed identically by all lanes.
+__global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_t *__restrict__ live0,
+                                                            const uint32_t *__restrict__ live1,
+                                                            const PassState *__restrict__ ps,
+                                                            const uint64_t *__restrict__ state_in,
+                                                            uint64_t *__restrict__ state_out,
+                                                            uint32_t *__restrict__ rbid,
+                                                            uint32_t *vis_bits, uint32_t *act_bits,
+                                                            uint32_t *ctr)
+{
+    const VolGeom &g = P.g;
+    const uint32_t nproc = ps->nproc;
+    if (nproc >= kCoopBelow) return;
+    const int kk = (int)ps->kk;
+    const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
+    const Cam cam = *P.camd;
+    const int max_steps = 2 * (g.tb[0] + g.tb[1] + g.tb[2]) + 8;
+    const uint32_t nb0 = g.nb[0], nb1 = g.nb[1], nc0 = g.nc[0], nc1 = g.nc[1];
+    const uint32_t ns0 = P.occ.ns[0], ns1 = P.occ.ns[1];
+    const int lane = threadIdx.x & 31;
+    const bool elane = lane < 12;
+    const int ea = elane ? lane >> 2 : 0;   // axis of this lane's crossing
+    const int ek = (lane & 3) + 1;          // its number along that axis
+    const unsigned full = 0xFFFFFFFFu;
+    uint32_t tot_steps = 0, max_seen = 0;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nproc;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint32_t ray = live[i];
+        Walk w;
+        make_ray(w.r, cam.eye, cam.p00, cam.du, cam.dv, (int)(ray % P.W), (int)(ray / P.W));
+        const uint64_t st = state_in[ray];
+        w.b[0] = (int)(st & 0xFFFF);
+        w.b[1] = (int)((st >> 16) & 0xFFFF);
+        w.b[2] = (int)((st >> 32) & 0xFFFF);
+        uint64_t flags = st >> 48;
+        uint32_t *out = rbid + (uint64_t)i * kk;
+        int cnt = 0;
+        bool alive = !(flags & kDone);
+        if (alive) {
+            walk_init(w, g);
+            if (flags & kStep) alive = walk_step(w, g);
+        }
+        flags &= ~kStep;
+        int steps = 0;
+        while (alive) {   // uniform across the warp: every lane holds the same walk
+            if (++steps > max_steps) {
+                if (lane == 0) atomicOr(&ctr[C_BAD], 2u);
+                alive = false;
+                break;
+            }
+            const int *b = w.b;
+            const uint32_t sc =
+                (uint32_t)(b[0] >> 4) + ns0 * ((uint32_t)(b[1] >> 4) + ns1 * (uint32_t)(b[2] >> 4));
+            const uint32_t c =
+                (uint32_t)(b[0] >> 2) + nc0 * ((uint32_t)(b[1] >> 2) + nc1 * (uint32_t)(b[2] >> 2));
+            // both masks in flight at once (the coarse one is unused when the
+            // super mask says the cell is empty)
+            const unsigned long long smask = __ldg(P.occ.smask + sc);
+            const unsigned long long fmask = __ldg(P.occ.fmask + c);
+            if (!((smask >> (((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) & 1ull)) {
+                alive = skip_level(w, g, smask ? 4 : 16, smask ? g.tc : P.occ.ts);
+                continue;
+            }
+
+            // crossings inside this coarse cell per axis; the last one leaves it
+            int na[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (w.r.sgn[a] > 0) na[a] = min(4 * (b[a] >> 2) + 4 - b[a], g.tb[a] - b[a]);
+                else if (w.r.sgn[a] < 0) na[a] = b[a] - 4 * (b[a] >> 2) + 1;
+                else na[a] = 0;
+            }
+            // time of the k-th crossing along axis a (exact numerator over |d_a|)
+            auto cross = [&](int a, int k) -> Tq {
+                const float X = w.r.sgn[a] > 0 ? (float)min(4 * (b[a] + k), g.dims[a] - 1) : (float)(4 * (b[a] - k + 1));
+                const float n = __fsub_rn(X, w.r.e[a]);
+                return Tq{w.r.sgn[a] > 0 ? n : -n, w.r.ad[a]};
+            };
+            Tq tex{0.f, 1.f};
+            bool have = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (!na[a]) continue;
+                const Tq t = cross(a, na[a]);
+                if (!have || tcmp(t, tex) < 0) {
+                    tex = t;
+                    have = true;
+                }
+            }
+            // this lane's crossing: crossings per axis up to its time (cle:
+            // at or before, clt: strictly before); its axis's values are
+            // selected, not indexed, so the walk stays in registers
+            bool valid = false, rep = false, interior = false;
+            int cle[3] = {0, 0, 0}, clt[3] = {0, 0, 0};
+            const int na_e = ea == 0 ? na[0] : (ea == 1 ? na[1] : na[2]);
+            if (elane && ek <= na_e) {
+                const int sg = ea == 0 ? w.r.sgn[0] : (ea == 1 ? w.r.sgn[1] : w.r.sgn[2]);
+                const int bq = ea == 0 ? b[0] : (ea == 1 ? b[1] : b[2]);
+                const int dq = ea == 0 ? g.dims[0] : (ea == 1 ? g.dims[1] : g.dims[2]);
+                const float eq = ea == 0 ? w.r.e[0] : (ea == 1 ? w.r.e[1] : w.r.e[2]);
+                const float adq = ea == 0 ? w.r.ad[0] : (ea == 1 ? w.r.ad[1] : w.r.ad[2]);
+                const float Xq = sg > 0 ? (float)min(4 * (bq + ek), dq - 1) : (float)(4 * (bq - ek + 1));
+                const float nq = __fsub_rn(Xq, eq);
+                const Tq tl{sg > 0 ? nq : -nq, adq};
+                const int ce = tcmp(tl, tex);
+                valid = ce <= 0;
+                interior = ce < 0;
+                if (valid) {
+                    rep = true;
+#pragma unroll
+                    for (int a2 = 0; a2 < 3; ++a2) {
+                        if (a2 == ea) {
+                            cle[a2] = ek;
+                            clt[a2] = ek - 1;
+                            continue;
+                        }
+                        // crossing times grow with k2: count up to the first later one
+                        for (int k2 = 1; k2 <= na[a2]; ++k2) {
+                            const int cc = tcmp(cross(a2, k2), tl);
+                            if (cc > 0) break;
+                            ++cle[a2];
+                            if (cc < 0) ++clt[a2];
+                        }
+                        if (a2 < ea && cle[a2] != clt[a2]) rep = false;   // a lower axis crosses at the same time
+                    }
+                }
+            }
+            const unsigned repm = __ballot_sync(full, valid && rep);
+            const unsigned repi = __ballot_sync(full, interior && rep);
+            const unsigned ltm = ((1u << clt[0]) - 1u) | (((1u << clt[1]) - 1u) << 4) | (((1u << clt[2]) - 1u) << 8);
+            const int rank = __popc(repm & ltm);
+            int nbk[3];
+#pragma unroll
+            for (int a2 = 0; a2 < 3; ++a2) nbk[a2] = b[a2] + w.r.sgn[a2] * cle[a2];
+            // positions in the cell: 0 = the current block, rank + 1 = the
+            // block after an interior crossing
+            bool vis = false;
+            int pos = 0, bb[3] = {b[0], b[1], b[2]};
+            if (lane == 31) {
+                vis = (fmask >> ((b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) & 1ull;
+            } else if (interior && rep) {
+                pos = rank + 1;
+                bb[0] = nbk[0];
+                bb[1] = nbk[1];
+                bb[2] = nbk[2];
+                vis = (fmask >> ((bb[0] & 3) + 4 * (bb[1] & 3) + 16 * (bb[2] & 3))) & 1ull;
+            }
+            const unsigned vmask = __reduce_or_sync(full, vis ? (1u << pos) : 0u);
+            const int need = kk - cnt;
+            const int take = min(need, __popc(vmask));
+            const int idx = vis ? __popc(vmask & ((1u << pos) - 1u)) : 32;
+            if (idx < take) {
+                const uint32_t blin = (uint32_t)bb[0] + nb0 * ((uint32_t)bb[1] + nb1 * (uint32_t)bb[2]);
+                out[cnt + idx] = blin;
+                set_bit(vis_bits, blin);
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    int x = bb[0] + (o & 1), y = bb[1] + ((o >> 1) & 1), z = bb[2] + (o >> 2);
+                    if (x < g.nb[0] && y < g.nb[1] && z < g.nb[2])
+                        set_bit(act_bits, (uint32_t)x + nb0 * ((uint32_t)y + nb1 * (uint32_t)z));
+                }
+            }
+            cnt += take;
+            if (take == need) {   // k blocks taken: stop on the last one
+                const int src = __ffs(__ballot_sync(full, idx == take - 1)) - 1;
+#pragma unroll
+                for (int a2 = 0; a2 < 3; ++a2) w.b[a2] = __shfl_sync(full, bb[a2], src);
+                flags |= kStep;
+                break;
+            }
+            // on to the block after T_exit (the lowest axis crossing then)
+            const int src = __ffs(__ballot_sync(full, valid && rep && !interior)) - 1;
+            bool inside = true;
+#pragma unroll
+            for (int a2 = 0; a2 < 3; ++a2) {
+                w.b[a2] = __shfl_sync(full, nbk[a2], src);
+                if (w.b[a2] < 0 || w.b[a2] >= g.tb[a2]) inside = false;
+            }
+            if (!inside) {
+                alive = false;
+                break;
+            }
+#pragma unroll
+            for (int a2 = 0; a2 < 3; ++a2) set_axis(w, g, a2);
+        }
+        if (!alive) flags |= kDone;
+        for (int j = cnt + lane; j < kk; j += 32) out[j] = kNone;
+        if (lane == 0) {
+            state_out[ray] = pack_state(w.b, flags);
+            tot_steps += (uint32_t)steps;
+            max_seen = max(max_seen, (uint32_t)steps);
+        }
+    }
+    if (lane == 0) {
+        if (tot_steps) atomicAdd(&ctr[C_STEPS], tot_steps);
+        if (max_seen) atomicMax(&ctr[C_MAXSTEPS], max_seen);
     }
 }
 
@@ -1739,6 +1958,10 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
 
     // (a) traversal with speculation, marking visible and active blocks
     traverse_kernel<<<grid_for(r->npix, 128, 16), 128, 0, s>>>(
+        make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
+        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr);
+    count_launch();
+    traverse_coop_kernel<<<device_sm_count() * 16, 128, 0, s>>>(
         make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
         r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr);
     count_launch();
