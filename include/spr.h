@@ -215,6 +215,12 @@ int spr_set_cache_budget(spr_renderer *r, size_t bytes);
 /* mode SPR_SPEC_FIXED with 1 <= k <= SPR_K_LIMIT, or SPR_SPEC_ADAPTIVE with
  * 1 <= k_max <= SPR_K_LIMIT (k ignored).  Restarts the render. */
 int spr_set_speculation(spr_renderer *r, int mode, int k, int k_max);
+/* Traversal tuning (no counterpart in the paper, results unchanged): passes
+ * with fewer than n_rays live rays walk one ray per warp, larger passes one
+ * ray per thread (default 16384; 0 = never one per warp).  Both walks visit
+ * the same blocks in the same order (Sec. 3.3).  Takes effect at the next
+ * render or pass. */
+int spr_set_warp_walk_threshold(spr_renderer *r, int64_t n_rays);
 /* empty the block cache (the next pass decodes from scratch) */
 int spr_reset_cache(spr_renderer *r);
 /* per-pass CUDA-event timing of the stages (adds host synchronisation) */

@@ -99,6 +99,7 @@ PROTOTYPES = {
     "spr_set_isovalue": ([_vp, ctypes.c_float], _i32),
     "spr_set_cache_budget": ([_vp, _sz], _i32),
     "spr_set_speculation": ([_vp, _i32, _i32, _i32], _i32),
+    "spr_set_warp_walk_threshold": ([_vp, _i64], _i32),
     "spr_reset_cache": ([_vp], _i32),
     "spr_set_profiling": ([_vp, _i32], _i32),
     "spr_render_pass": ([_vp, _vp, _vp], _i32),

@@ -235,6 +235,10 @@ def spr_set_speculation(r: Renderer, mode: int, k: int = 1, k_max: int = 64):
     check(load().spr_set_speculation(r.handle, int(mode), int(k), int(k_max)))
 
 
+def spr_set_warp_walk_threshold(r: Renderer, n_rays: int):
+    check(load().spr_set_warp_walk_threshold(r.handle, int(n_rays)))
+
+
 def spr_reset_cache(r: Renderer):
     check(load().spr_reset_cache(r.handle))
 

@@ -82,6 +82,7 @@ struct PassState {
     // recently used first, in the list selected by parity bit 1
     uint32_t fresh_lo, fresh_hi, n_used;
     uint32_t live_words;  // ceil(n_live / 32): words of the alive bitmap of this pass
+    uint32_t coop_below;  // passes with fewer live rays walk one ray per warp
     unsigned long long tot_decoded, tot_entries, tot_evicted, tot_hits;
 };
 
@@ -105,7 +106,7 @@ struct DevParams {
     uint32_t spec_mode, k_fixed, k_max, npix;
     uint32_t more;    // passes this call may run
     uint32_t reset;   // 1: empty the cache before ray generation
-    uint32_t pad;
+    uint32_t coop_below;
 };
 
 // occupancy of the three skipping levels for the current isovalue: one bit
@@ -495,12 +496,10 @@ struct EnterEmit {
 
 
 // ------------------------------------------------------------- traversal
-// Passes with fewer live rays than this walk one ray per warp
+// Passes with fewer live rays than PassState::coop_below (default 16384, set
+// with spr_set_warp_walk_threshold) walk one ray per warp
 // (traverse_coop_kernel); larger passes one ray per thread (traverse_kernel).
-#ifndef SPR_COOP_BELOW
-#define SPR_COOP_BELOW 16384
-#endif
-constexpr uint32_t kCoopBelow = SPR_COOP_BELOW;
+constexpr uint32_t kCoopBelowDefault = 16384;
 
 __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__restrict__ live0,
                                                        const uint32_t *__restrict__ live1,
@@ -513,7 +512,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
 {
     const VolGeom &g = P.g;
     const uint32_t nproc = ps->nproc;
-    if (nproc < kCoopBelow) return;   // few rays: traverse_coop_kernel walks them
+    if (nproc < ps->coop_below) return;   // few rays: traverse_coop_kernel walks them
     const int kk = (int)ps->kk;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
     const Cam cam = *P.camd;
@@ -617,7 +616,7 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
 {
     const VolGeom &g = P.g;
     const uint32_t nproc = ps->nproc;
-    if (nproc >= kCoopBelow) return;
+    if (nproc >= ps->coop_below) return;
     const int kk = (int)ps->kk;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
     const Cam cam = *P.camd;
@@ -1533,6 +1532,7 @@ __global__ void start_kernel(PassState *ps, const DevParams *p, uint32_t *ctr, u
             ps->k_fixed = p->k_fixed;
             ps->k_max = p->k_max;
             ps->npix = p->npix;
+            ps->coop_below = p->coop_below;
         }
     }
     if (!p->reset) return;
@@ -1560,6 +1560,7 @@ __global__ void config_kernel(PassState *ps, const DevParams *p)
     ps->k_fixed = p->k_fixed;
     ps->k_max = p->k_max;
     ps->npix = p->npix;
+    ps->coop_below = p->coop_below;
 }
 
 // after ray generation: the live list is list 0 and the pass count restarts
@@ -1622,6 +1623,7 @@ struct spr_renderer {
     bool has_cam = false;
     float iso = 0.5f;
     int spec_mode = SPR_SPEC_ADAPTIVE, k_fixed = 1, k_max = 64;
+    uint32_t coop_below = kCoopBelowDefault;
     int64_t n_slots = 0;
     bool profiling = false;
 
@@ -1835,7 +1837,7 @@ int write_params(spr_renderer *r, uint32_t more, uint32_t reset)
     h.npix = (uint32_t)r->npix;
     h.more = more;
     h.reset = reset;
-    h.pad = 0;
+    h.coop_below = r->coop_below;
     return SPR_OK;
 }
 
@@ -2461,6 +2463,16 @@ extern "C" int spr_set_speculation(spr_renderer *r, int mode, int k, int k_max)
     }
     r->spec_mode = mode;
     r->need_raygen = true;
+    r->params_dirty = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_set_warp_walk_threshold(spr_renderer *r, int64_t n_rays)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    if (n_rays < 0) return set_error(SPR_ERR_INVALID_ARG, "n_rays must be non-negative");
+    r->coop_below = (uint32_t)std::min<int64_t>(n_rays, 0xFFFFFFFFll);
     r->params_dirty = true;
     return SPR_OK;
 }

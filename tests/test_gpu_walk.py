@@ -1,0 +1,123 @@
+"""The two traversal kernels against each other and the oracle.
+
+Passes with few live rays walk one ray per warp (the blocks of an occupied
+coarse cell found at once from exactly ranked plane crossings), the others one
+ray per thread (step by step); both implement the walk of Sec. 3.3 and must
+visit the same blocks in the same order.  With either forced for every pass
+the framebuffers and the per-pass counters are identical, and both match the
+oracle."""
+import numpy as np
+import pytest
+
+import synth
+from test_gpu_render import Scene, compare, value_scene
+
+pytestmark = pytest.mark.gpu
+
+THREAD, WARP = 0, 1 << 31
+PASS_KEYS = ("k", "k_used", "retries", "n_active", "n_processed", "n_entries", "n_visible",
+             "n_requested", "n_decoded", "n_evicted", "n_term_hit", "n_term_miss", "n_active_after")
+
+
+@pytest.fixture(scope="module")
+def spr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2309_10212_gb300 as m
+    return m
+
+
+def render(spr, sc, walk, mode=None, k=1, k_max=64, slots=None):
+    import torch
+    v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    r = spr.spr_create_renderer(v, sc.W, sc.H)
+    spr.spr_set_camera(r, sc.cam)
+    spr.spr_set_isovalue(r, sc.iso)
+    nb = sc.ovol.fine.shape[0]
+    spr.spr_set_cache_budget(r, 256 * (slots if slots else max(8, nb)))
+    if mode == "fixed":
+        spr.spr_set_speculation(r, spr.SPR_SPEC_FIXED, k=k)
+    else:
+        spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=k_max)
+    spr.spr_set_warp_walk_threshold(r, walk)
+    rs, passes = spr.spr_render_to_convergence(r, 100000)
+    fb = spr.spr_read_framebuffer(r)
+    r.close()
+    v.close()
+    return fb, rs, passes
+
+
+def same(a, b):
+    fa, ra, pa = a
+    fb, rb, pb = b
+    for key in fa:
+        assert np.array_equal(fa[key], fb[key]), key
+    assert len(pa) == len(pb)
+    for x, y in zip(pa, pb):
+        for key in PASS_KEYS:
+            assert x[key] == y[key], (x["pass"], key, x[key], y[key])
+    assert ra["blocks_decoded"] == rb["blocks_decoded"]
+
+
+@pytest.mark.parametrize("dims,seed,W,H", [((33, 17, 26), 4, 64, 48), ((64, 64, 64), 5, 128, 96),
+                                           ((48, 40, 44), 21, 80, 64)])
+@pytest.mark.parametrize("spec", [("fixed", 1), ("fixed", 3), ("adaptive", 64)])
+def test_warp_walk_equals_thread_walk(spr, orc, dims, seed, W, H, spec):
+    sc = value_scene(orc, dims, seed, W, H)
+    mode, k = spec
+    kw = dict(mode="fixed", k=k) if mode == "fixed" else dict(k_max=k)
+    a = render(spr, sc, THREAD, **kw)
+    b = render(spr, sc, WARP, **kw)
+    same(a, b)
+    compare(sc, a[0])
+
+
+def test_tight_cache_overflow_both_walks(spr, orc):
+    """A cache of 24 slots forces k halving and ray windows in most passes."""
+    sc = value_scene(orc, (48, 40, 44), 21, 80, 64)
+    a = render(spr, sc, THREAD, slots=24)
+    b = render(spr, sc, WARP, slots=24)
+    same(a, b)
+    assert any(p["retries"] for p in a[2])
+    compare(sc, a[0])
+
+
+def test_diagonal_rays_both_walks(spr, orc):
+    """Eye on the volume's main diagonal, looking along it: the central rays
+    cross x, y and z block planes at the same instants (diagonal steps)."""
+    dims = (40, 40, 40)
+    vol = synth.volumes.value_noise(dims, seed=31, ref=40)
+    iso = float(np.float32(np.quantile(vol, 0.7)))
+    cam = synth.cameras.look_at((-12.0, -12.0, -12.0), (39.0, 39.0, 39.0), (0, 0, 1), 30.0, 64, 64)
+    sc = Scene(orc, dims, vol, 8, iso, cam, 64, 64)
+    for k in (1, 4):
+        a = render(spr, sc, THREAD, mode="fixed", k=k)
+        b = render(spr, sc, WARP, mode="fixed", k=k)
+        same(a, b)
+    compare(sc, a[0], max_amb=0.1)
+
+
+def test_eye_inside_both_walks(spr, orc):
+    dims = (32, 32, 32)
+    vol = synth.volumes.value_noise(dims, seed=8, ref=32)
+    iso = float(np.float32(np.quantile(vol, 0.8)))
+    cam = synth.cameras.look_at((15.5, 16.25, 14.0), (31, 31, 31), (0, 0, 1), 70.0, 64, 64)
+    sc = Scene(orc, dims, vol, 8, iso, cam, 64, 64)
+    a = render(spr, sc, THREAD, mode="fixed", k=2)
+    b = render(spr, sc, WARP, mode="fixed", k=2)
+    same(a, b)
+    compare(sc, a[0])
+
+
+def test_threshold_rejects_negative(spr, orc):
+    sc = value_scene(orc, (16, 16, 16), 2, 16, 16)
+    import torch
+    v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    r = spr.spr_create_renderer(v, 16, 16)
+    with pytest.raises(spr.SprError):
+        spr.spr_set_warp_walk_threshold(r, -1)
+    r.close()
+    v.close()
