@@ -1024,12 +1024,10 @@ struct CellF {
     }
 };
 
-// roots of f'(s) = 3 c3 s^2 + 2 c2 s + c1 inside (0, L), ascending; the
-// coefficients are re-derived in double precision when the discriminant is
-// ill-conditioned
-__device__ int deriv_roots(const CellF &f, float L, float out[2])
+// power-basis coefficients of f along the segment: f(s) - f(0) = c1 s + c2 s^2 + c3 s^3
+__device__ __forceinline__ void cubic_coeffs(const CellF &f, float &c1, float &c2, float &c3)
 {
-    float c1 = 0.f, c2 = 0.f, c3 = 0.f;
+    c1 = c2 = c3 = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const bool i = k & 1, j = (k >> 1) & 1, l = k >> 2;
@@ -1040,12 +1038,21 @@ __device__ int deriv_roots(const CellF &f, float L, float out[2])
         c2 += f.v[k] * (bx * by * az + bx * ay * bz + ax * by * bz);
         c3 += f.v[k] * (bx * by * bz);
     }
+}
+
+// roots of f'(s) = 3 c3 s^2 + 2 c2 s + c1 inside (0, L), ascending, in e0 and
+// e1 (returns how many); the coefficients are re-derived in double precision
+// when the discriminant is ill-conditioned
+__device__ __forceinline__ int deriv_roots(const CellF &f, float c1, float c2, float c3, float L, float &e0,
+                                           float &e1)
+{
     float a = 3.f * c3, b = 2.f * c2, c = c1;
     float disc = b * b - 4.f * a * c;
-    float r[2];
+    float r0 = 0.f, r1 = 0.f;
     int n = 0;
     if (fabsf(disc) < 1e-5f * (b * b + fabsf(4.f * a * c))) {
         double C1 = 0.0, C2 = 0.0, C3 = 0.0;
+#pragma unroll
         for (int k = 0; k < 8; ++k) {
             const bool i = k & 1, j = (k >> 1) & 1, l = k >> 2;
             double ax = i ? f.u[0] : 1.0 - f.u[0], bx = i ? f.d[0] : -(double)f.d[0];
@@ -1057,90 +1064,103 @@ __device__ int deriv_roots(const CellF &f, float L, float out[2])
         }
         double A = 3.0 * C3, B = 2.0 * C2, CC = C1;
         if (A == 0.0) {
-            if (B != 0.0) r[n++] = (float)(-CC / B);
+            if (B != 0.0) {
+                r0 = (float)(-CC / B);
+                n = 1;
+            }
         } else {
             double D = B * B - 4.0 * A * CC;
             if (D >= 0.0) {
                 double q = -0.5 * (B + (B >= 0.0 ? sqrt(D) : -sqrt(D)));
                 if (q != 0.0) {
-                    r[n++] = (float)(q / A);
-                    r[n++] = (float)(CC / q);
+                    r0 = (float)(q / A);
+                    r1 = (float)(CC / q);
+                    n = 2;
                 } else {
-                    r[n++] = 0.f;
+                    n = 1;
                 }
             }
         }
     } else if (a == 0.f) {
-        if (b != 0.f) r[n++] = -c / b;
+        if (b != 0.f) {
+            r0 = -c / b;
+            n = 1;
+        }
     } else if (disc > 0.f) {
         float q = -0.5f * (b + copysignf(sqrtf(disc), b));
         if (q != 0.f) {
-            r[n++] = q / a;
-            r[n++] = c / q;
+            r0 = q / a;
+            r1 = c / q;
+            n = 2;
         }
     }
-    int m = 0;
-    for (int t = 0; t < n; ++t)
-        if (r[t] > 0.f && r[t] < L) out[m++] = r[t];
-    if (m == 2 && out[0] > out[1]) {
-        float t = out[0];
-        out[0] = out[1];
-        out[1] = t;
+    // keep those inside (0, L), ascending
+    const bool in0 = n >= 1 && r0 > 0.f && r0 < L, in1 = n >= 2 && r1 > 0.f && r1 < L;
+    if (in0 && in1) {
+        e0 = fminf(r0, r1);
+        e1 = fmaxf(r0, r1);
+        return 2;
     }
-    return m;
+    if (in0 || in1) {
+        e0 = in0 ? r0 : r1;
+        return 1;
+    }
+    return 0;
+}
+
+// a root of f in [a, b] where f(a), f(b) differ in sign: Newton steps on the
+// trilinear f with the cubic's derivative, kept inside the shrinking bracket
+// (bisection when a step leaves it), until the step is below 1e-6 (1 + s) --
+// three orders of magnitude inside the depth tolerance
+__device__ __forceinline__ float refine_root(const CellF &f, float c1, float c2, float c3, float a, float b,
+                                             float fa, float fb)
+{
+    float s = a - fa * (b - a) / (fb - fa);   // secant start
+    if (!(s > a && s < b)) s = 0.5f * (a + b);
+    const bool neg_a = fa < 0.f;
+    for (int it = 0; it < 40; ++it) {
+        const float fs = f(s);
+        if (fs == 0.f) return s;
+        if ((fs < 0.f) == neg_a) a = s;
+        else b = s;
+        const float d = fmaf(fmaf(3.f * c3, s, 2.f * c2), s, c1);
+        float sn = s - fs / d;
+        if (!(sn > a && sn < b)) sn = 0.5f * (a + b);
+        const float tol = 1e-6f * (1.f + fabsf(sn));
+        if (fabsf(sn - s) <= tol || b - a <= tol) return sn;
+        s = sn;
+    }
+    return 0.5f * (a + b);
 }
 
 // first root of f on [0, L]: monotone pieces split at the roots of f', the
-// first piece that starts on a zero or changes sign, refined by Illinois
-// regula falsi
-__device__ bool first_root(const CellF &f, float L, float &s_hit)
+// first piece that starts on a zero or changes sign, refined by refine_root
+__device__ __forceinline__ bool first_root(const CellF &f, float L, float &s_hit)
 {
-    float pts[4];
-    float ext[2];
-    int ne = deriv_roots(f, L, ext);
-    int np = 0;
-    pts[np++] = 0.f;
-    for (int i = 0; i < ne; ++i) pts[np++] = ext[i];
-    pts[np++] = L;
+    float c1, c2, c3;
+    cubic_coeffs(f, c1, c2, c3);
+    float e0 = L, e1 = L;
+    const int ne = deriv_roots(f, c1, c2, c3, L, e0, e1);
     float fa = f(0.f);
     if (fa == 0.f) {
         s_hit = 0.f;
         return true;
     }
-    for (int i = 1; i < np; ++i) {
-        float sa = pts[i - 1], sb = pts[i];
-        float fb = f(sb);
+    float sa = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (i > ne) break;
+        const float sb = i == ne ? L : (i == 0 ? e0 : e1);
+        const float fb = f(sb);
         if (fb == 0.f) {
             s_hit = sb;
             return true;
         }
         if ((fb < 0.f) != (fa < 0.f)) {
-            float a = sa, b = sb, ya = fa, yb = fb;
-            int side = 0;
-            for (int it = 0; it < 60; ++it) {
-                float s = (a * yb - b * ya) / (yb - ya);
-                if (!(s > a && s < b)) s = 0.5f * (a + b);
-                float ys = f(s);
-                if (ys == 0.f) {
-                    a = b = s;
-                    break;
-                }
-                if ((ys < 0.f) == (ya < 0.f)) {
-                    a = s;
-                    ya = ys;
-                    if (side == -1) yb *= 0.5f;
-                    side = -1;
-                } else {
-                    b = s;
-                    yb = ys;
-                    if (side == 1) ya *= 0.5f;
-                    side = 1;
-                }
-                if (b - a <= 1e-7f * (1.f + b)) break;
-            }
-            s_hit = 0.5f * (a + b);
+            s_hit = refine_root(f, c1, c2, c3, sa, sb, fa, fb);
             return true;
         }
+        sa = sb;
         fa = fb;
     }
     return false;
@@ -1343,6 +1363,9 @@ __global__ void __launch_bounds__(128, 4) intersect_kernel(RT R, const uint32_t 
         uint32_t b = rbid[e];
         uint32_t i = e / kk, j = e - i * kk;
         uint32_t ray = live[i];
+        // a hit already recorded from an earlier block of this ray (smaller
+        // j) wins the atomicMin whatever this block holds
+        if ((uint32_t)(__ldcg(keys + ray) >> 52) < j) continue;
         Ray r;
         make_ray(r, cam.eye, cam.p00, cam.du, cam.dv, (int)(ray % R.P.W), (int)(ray / R.P.W));
         int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((uint32_t)g.nb[0] * g.nb[1]));
