@@ -1024,20 +1024,31 @@ struct CellF {
     }
 };
 
-// power-basis coefficients of f along the segment: f(s) - f(0) = c1 s + c2 s^2 + c3 s^3
+// power-basis coefficients of f along the segment: f(s) - f(0) = c1 s + c2 s^2 + c3 s^3.
+// The trilinear form is multiplied out one axis at a time: the four x-edge
+// interpolants are linear in s, the two y-interpolants of them quadratic, the
+// z-interpolant of those cubic.
 __device__ __forceinline__ void cubic_coeffs(const CellF &f, float &c1, float &c2, float &c3)
 {
-    c1 = c2 = c3 = 0.f;
+    float a[4], b[4];   // x-edge j + 2l: a + b s
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const bool i = k & 1, j = (k >> 1) & 1, l = k >> 2;
-        float ax = i ? f.u[0] : 1.f - f.u[0], bx = i ? f.d[0] : -f.d[0];
-        float ay = j ? f.u[1] : 1.f - f.u[1], by = j ? f.d[1] : -f.d[1];
-        float az = l ? f.u[2] : 1.f - f.u[2], bz = l ? f.d[2] : -f.d[2];
-        c1 += f.v[k] * (bx * ay * az + ax * by * az + ax * ay * bz);
-        c2 += f.v[k] * (bx * by * az + bx * ay * bz + ax * by * bz);
-        c3 += f.v[k] * (bx * by * bz);
+    for (int e = 0; e < 4; ++e) {
+        const float v0 = f.v[2 * e], dv = f.v[2 * e + 1] - v0;
+        a[e] = fmaf(dv, f.u[0], v0);
+        b[e] = dv * f.d[0];
     }
+    float p[2][3];   // y-interpolant at z level l: p0 + p1 s + p2 s^2
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const float da = a[2 * l + 1] - a[2 * l], db = b[2 * l + 1] - b[2 * l];
+        p[l][0] = fmaf(da, f.u[1], a[2 * l]);
+        p[l][1] = fmaf(da, f.d[1], fmaf(db, f.u[1], b[2 * l]));
+        p[l][2] = db * f.d[1];
+    }
+    const float r0 = p[1][0] - p[0][0], r1 = p[1][1] - p[0][1], r2 = p[1][2] - p[0][2];
+    c1 = fmaf(r0, f.d[2], fmaf(r1, f.u[2], p[0][1]));
+    c2 = fmaf(r1, f.d[2], fmaf(r2, f.u[2], p[0][2]));
+    c3 = r2 * f.d[2];
 }
 
 // roots of f'(s) = 3 c3 s^2 + 2 c2 s + c1 inside (0, L), ascending, in e0 and
