@@ -242,6 +242,85 @@ def run_reference(args, wl):
     return 0
 
 
+def run_study(args, wl):
+    """Speculation sweep (fixed k = 1..16, adaptive caps 16 and 64), resolution
+    scaling (640x360, 1280x720, 1920x1080) and blocks decoded against the
+    decode-every-active-block count of Sec. 5.3, on one workload.  Every
+    render starts from an empty cache; times are CUDA events around the
+    C-ABI calls, as in the bench line."""
+    import ctypes
+
+    import torch
+
+    from paper_2309_10212_gb300 import build
+    build.build()
+    import paper_2309_10212_gb300 as spr
+    from paper_2309_10212_gb300 import _lib
+    L = _lib.load()
+    stream = torch.cuda.Stream()
+    out = {"workload": wl["name"], "iso": wl["iso"], "dims": list(wl["dims"]), "rate": wl["rate"],
+           "cache_bytes": wl["cache_bytes"]}
+    with torch.cuda.stream(stream):
+        comp = compressed_on_device(wl, spr, torch)
+        vol = spr.spr_create_volume(wl["dims"], wl["rate"], comp, stream=stream)
+        act, need = spr.spr_count_active_blocks(vol, wl["iso"], stream=stream)
+        out["active_blocks"], out["needed_blocks"] = act, need
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        f3 = ctypes.c_float * 3
+        n_pose = min(wl["poses"], 16)
+
+        def measure(W, H, spec, k):
+            w2 = dict(wl, W=W, H=H)
+            r = spr.spr_create_renderer(vol, W, H)
+            spr.spr_set_cache_budget(r, wl["cache_bytes"])
+            if spec == "fixed":
+                spr.spr_set_speculation(r, spr.SPR_SPEC_FIXED, k=k)
+            else:
+                spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=k)
+            spr.spr_set_isovalue(r, wl["iso"])
+            cams = [tuple(f3(*[float(v) for v in c[key]]) for key in ("eye", "p00", "du", "dv"))
+                    for c in (pose(w2, i) for i in range(n_pose))]
+            rows = []
+            for rep in range(2):          # the first round warms up
+                for i in range(n_pose):
+                    flush.fill_(i & 255)
+                    rs = _lib.RenderStats()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    _lib.check(L.spr_reset_cache(r.handle))
+                    _lib.check(L.spr_set_camera(r.handle, *cams[i]))
+                    _lib.check(L.spr_render_to_convergence(r.handle, ctypes.c_void_p(stream.cuda_stream),
+                                                           4096, ctypes.byref(rs), None))
+                    b.record(stream)
+                    b.synchronize()
+                    if rep:
+                        d = rs.as_dict()
+                        d["ms"] = a.elapsed_time(b)
+                        rows.append(d)
+            r.close()
+            mean = lambda key: statistics.mean(x[key] for x in rows)   # noqa: E731
+            return {"W": W, "H": H, "spec": spec, "k": k, "poses": n_pose,
+                    "ms": round(mean("ms"), 4), "passes": round(mean("passes"), 2),
+                    "ms_per_pass": round(mean("ms") / max(mean("passes"), 1e-9), 4),
+                    "blocks_decoded": round(mean("blocks_decoded"), 1),
+                    "decoded_vs_needed": round(mean("blocks_decoded") / max(need, 1), 4),
+                    "entries": round(mean("entries"), 1),
+                    "utilization_per_pass": round(mean("entries") / max(mean("passes"), 1e-9) / (W * H), 4)}
+
+        out["k_sweep"] = [measure(wl["W"], wl["H"], "fixed", k) for k in (1, 2, 4, 8, 16)]
+        out["k_sweep"] += [measure(wl["W"], wl["H"], "adaptive", k) for k in (16, 64)]
+        spec = wl["spec"]
+        out["resolution"] = [measure(W, H, spec, wl["k"]) for W, H in ((640, 360), (1280, 720), (1920, 1080))]
+        vol.close()
+    with open(args.study, "w") as f:
+        json.dump(out, f, indent=1)
+    best = min(out["k_sweep"], key=lambda x: x["ms"])
+    print(json.dumps({"study": args.study, "active_blocks": act, "needed_blocks": need,
+                      "best": {k: best[k] for k in ("spec", "k", "ms", "passes", "blocks_decoded")}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -252,6 +331,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--dump", default="", help="write per-pass details to this JSON file")
+    ap.add_argument("--study", default="",
+                    help="instead of the bench line: write the speculation sweep, resolution "
+                         "scaling and decode-all-active comparison to this JSON file")
     ap.add_argument("--k-max", type=int, default=0,
                     help="override the workload's speculation limit (k sweeps; 0 keeps it)")
     args = ap.parse_args()
@@ -261,6 +343,8 @@ def main():
         wl["name"] = wl["name"].rsplit("k<=", 1)[0] + f"k<={args.k_max}" if "k<=" in wl["name"] else wl["name"]
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.study:
+        return run_study(args, wl)
     if args.warmup < 3:
         args.warmup = 3
 

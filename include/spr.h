@@ -140,6 +140,16 @@ int spr_volume_ranges(const spr_volume *vol, float *fine_host, float *coarse_hos
 /* block-grid and coarse-grid sizes; either pointer may be NULL */
 int spr_volume_shape(const spr_volume *vol, int64_t nb[3], int64_t nc[3]);
 
+/* The decode-everything-active alternative the progressive method is
+ * measured against (Sec. 5.3 compares with a renderer that decompresses
+ * every block the isovalue can touch): *n_active = blocks whose fine range
+ * holds iso; *n_needed = those and their +x/+y/+z face, edge and corner
+ * neighbours, whose values enter the active blocks' cells (what such a
+ * renderer must decode).  Either pointer may be NULL; synchronises
+ * `stream`. */
+int spr_count_active_blocks(const spr_volume *vol, float iso, int64_t *n_active, int64_t *n_needed,
+                            spr_stream stream);
+
 /* --------------------------------------------------------------- renderer */
 #define SPR_SPEC_FIXED    0   /* k = the given count every pass                */
 #define SPR_SPEC_ADAPTIVE 1   /* k = min(k_max, floor(w*h / N_Act)) (Sec. 4)   */

@@ -92,6 +92,7 @@ PROTOTYPES = {
     "spr_create_volume": ([_vp, _vp, _sz, _i32, _vp, _vp], _i32),
     "spr_destroy_volume": ([_vp], _i32),
     "spr_volume_ranges": ([_vp, _vp, _vp, _vp], _i32),
+    "spr_count_active_blocks": ([_vp, ctypes.c_float, _vp, _vp, _vp], _i32),
     "spr_volume_shape": ([_vp, _vp, _vp], _i32),
     "spr_create_renderer": ([_vp, _i32, _i32, _vp], _i32),
     "spr_destroy_renderer": ([_vp], _i32),

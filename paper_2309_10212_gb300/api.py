@@ -186,6 +186,15 @@ def spr_volume_ranges(vol: Volume, stream=None):
     return fine, coarse
 
 
+def spr_count_active_blocks(vol: Volume, iso: float, stream=None):
+    """(active, needed): blocks whose range holds iso, and those plus their
+    +x/+y/+z neighbours (what decoding every active block costs)."""
+    a, n = ctypes.c_int64(), ctypes.c_int64()
+    check(load().spr_count_active_blocks(vol.handle, float(iso), ctypes.byref(a), ctypes.byref(n),
+                                         _stream(stream)))
+    return a.value, n.value
+
+
 # --------------------------------------------------------------- renderer
 class Renderer:
     def __init__(self, handle, vol: Volume, W: int, H: int):

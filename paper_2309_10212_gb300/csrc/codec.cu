@@ -384,6 +384,69 @@ extern "C" int spr_volume_ranges(const spr_volume *v, float *fine_host, float *c
     return SPR_OK;
 }
 
+namespace spr {
+// per block: is its fine range holding the isovalue (active), and is it
+// active or the +x/+y/+z face, edge or corner neighbour of an active block
+// (needed: its values enter an active block's cells)
+__global__ void count_active_kernel(const float2 *__restrict__ fine, VolGeom g, float iso,
+                                    unsigned long long *counts)
+{
+    const int64_t nb0 = g.nb[0], nb1 = g.nb[1], nb2 = g.nb[2];
+    unsigned long long na = 0, nn = 0;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < g.nblocks;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = b % nb0, y = (b / nb0) % nb1, z = b / (nb0 * nb1);
+        bool need = false;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            const int64_t xs = x - (o & 1), ys = y - ((o >> 1) & 1), zs = z - (o >> 2);
+            if (xs < 0 || ys < 0 || zs < 0) continue;
+            const float2 r = fine[xs + nb0 * (ys + nb1 * zs)];
+            const bool act = r.x <= iso && iso <= r.y;
+            if (o == 0) na += act;
+            need = need || act;
+        }
+        nn += need;
+        (void)nb2;
+    }
+    for (int off = 16; off; off >>= 1) {
+        na += __shfl_down_sync(0xFFFFFFFFu, na, off);
+        nn += __shfl_down_sync(0xFFFFFFFFu, nn, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (na) atomicAdd(&counts[0], na);
+        if (nn) atomicAdd(&counts[1], nn);
+    }
+}
+}  // namespace spr
+
+extern "C" int spr_count_active_blocks(const spr_volume *v, float iso, int64_t *n_active, int64_t *n_needed,
+                                       spr_stream stream)
+{
+    clear_error();
+    if (!v || !std::isfinite(iso)) return set_error(SPR_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = as_stream(stream);
+    DevBuf counts;
+    SPR_TRY(buf_alloc(counts, 2 * sizeof(unsigned long long), s));
+    unsigned long long h[2] = {0, 0};
+    int rc = SPR_OK;
+    cudaError_t e = cudaMemsetAsync(counts.p, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        count_active_kernel<<<grid_for(v->g.nblocks, 256, 8), 256, 0, s>>>(v->fine.as<float2>(), v->g, iso,
+                                                                           counts.as<unsigned long long>());
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, counts.p, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = set_error(SPR_ERR_CUDA, "count_active: %s", cudaGetErrorString(e));
+    buf_free(counts, s);
+    if (rc == SPR_OK) {
+        if (n_active) *n_active = (int64_t)h[0];
+        if (n_needed) *n_needed = (int64_t)h[1];
+    }
+    return rc;
+}
+
 extern "C" int spr_volume_shape(const spr_volume *v, int64_t nb[3], int64_t nc[3])
 {
     clear_error();
