@@ -217,8 +217,22 @@ int spr_destroy_renderer(spr_renderer *r);
  * traversal predicates rely on.  Restarts the render. */
 int spr_set_camera(spr_renderer *r, const float eye[3], const float p00[3], const float du[3],
                    const float dv[3]);
-/* isovalue (finite); restarts the render (the cache contents are kept) */
+/* isovalue (finite) of every view; restarts the render (the cache contents
+ * are kept) */
 int spr_set_isovalue(spr_renderer *r, float iso);
+/* Batched rendering (no counterpart in the paper, which renders one view):
+ * n_views (1..64) views of the volume are rendered as one wavefront -- their
+ * rays share the passes, the speculation budget (k = min(k_max,
+ * floor(n_views*w*h / N_Act))) and the block cache, so a block decoded for
+ * one view serves all.  Each view's image equals its single-view render.
+ * The framebuffer holds the views stacked top to bottom (height * n_views
+ * rows); ray / pixel ids are view * w * h + y * w + x.  Reallocates the
+ * per-pixel buffers and restarts the render; every view needs a camera
+ * (spr_set_camera sets view 0, spr_set_view any). */
+int spr_set_view_count(spr_renderer *r, int n_views);
+/* camera (as spr_set_camera) and isovalue of view `view` < n_views */
+int spr_set_view(spr_renderer *r, int view, const float eye[3], const float p00[3], const float du[3],
+                 const float dv[3], float iso);
 /* cache budget in bytes; slots = bytes / 256, at least 8, else
  * SPR_ERR_CACHE_TOO_SMALL.  Empties the cache and restarts the render. */
 int spr_set_cache_budget(spr_renderer *r, size_t bytes);

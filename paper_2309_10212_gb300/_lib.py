@@ -97,6 +97,8 @@ PROTOTYPES = {
     "spr_create_renderer": ([_vp, _i32, _i32, _vp], _i32),
     "spr_destroy_renderer": ([_vp], _i32),
     "spr_set_camera": ([_vp, _vp, _vp, _vp, _vp], _i32),
+    "spr_set_view_count": ([_vp, _i32], _i32),
+    "spr_set_view": ([_vp, _i32, _vp, _vp, _vp, _vp, ctypes.c_float], _i32),
     "spr_set_isovalue": ([_vp, ctypes.c_float], _i32),
     "spr_set_cache_budget": ([_vp, _sz], _i32),
     "spr_set_speculation": ([_vp, _i32, _i32, _i32], _i32),

@@ -232,6 +232,16 @@ def spr_set_camera(r: Renderer, eye, p00=None, du=None, dv=None):
     check(load().spr_set_camera(r.handle, _f3(eye), _f3(p00), _f3(du), _f3(dv)))
 
 
+def spr_set_view_count(r: Renderer, n_views: int):
+    check(load().spr_set_view_count(r.handle, int(n_views)))
+
+
+def spr_set_view(r: Renderer, view: int, cam: dict, iso: float):
+    """cam: a dict with eye, p00, du, dv (as synth.cameras makes)."""
+    check(load().spr_set_view(r.handle, int(view), _f3(cam["eye"]), _f3(cam["p00"]), _f3(cam["du"]),
+                              _f3(cam["dv"]), float(iso)))
+
+
 def spr_set_isovalue(r: Renderer, iso: float):
     check(load().spr_set_isovalue(r.handle, float(iso)))
 
@@ -293,8 +303,10 @@ def spr_get_framebuffer(r: Renderer) -> dict:
 
 
 def spr_read_framebuffer(r: Renderer, stream=None) -> dict:
-    """Host copies (numpy) of the framebuffer."""
-    n = r.W * r.H
+    """Host copies (numpy) of the framebuffer (all views, stacked)."""
+    fb = _lib.Framebuffer()
+    check(load().spr_get_framebuffer(r.handle, ctypes.byref(fb)))
+    n = fb.width * fb.height
     out = dict(depth=np.empty(n, np.float32), rgba=np.empty(n, np.uint32),
                block=np.empty(n, np.uint32), cell=np.empty(n, np.uint64),
                final_pass=np.empty(n, np.int32), status=np.empty(n, np.uint8))

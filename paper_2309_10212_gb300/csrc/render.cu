@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <new>
 
@@ -100,13 +101,20 @@ __device__ __forceinline__ void lru_reset(PassState *ps)
 // Per-render parameters in device memory, copied from a pinned host block by
 // the first node of the render's start graph (so the captured graphs stay
 // valid when the camera, isovalue, speculation or pass limit change).
-struct DevParams {
+// one view of a batch: its camera and isovalue
+struct View {
     Cam cam;
     float iso;
+};
+constexpr int kMaxViews = 64;
+
+struct DevParams {
     uint32_t spec_mode, k_fixed, k_max, npix;
     uint32_t more;    // passes this call may run
     uint32_t reset;   // 1: empty the cache before ray generation
     uint32_t coop_below;
+    uint32_t n_views;
+    View views[kMaxViews];   // the first n_views are copied
 };
 
 // occupancy of the three skipping levels for the current isovalue: one bit
@@ -128,11 +136,22 @@ struct Geo {
     VolGeom g;
     const float2 *fine;
     const float2 *coarse;
-    const Cam *camd;
-    const float *isod;
-    int W;
+    const View *views;     // n_views records (device)
+    int W, H;
+    int64_t WH;            // pixels per view; ray id = view * WH + y * W + x
+    int64_t fstride, sstride;   // brick-mask words per view (coarse, super)
     Occ occ;
 };
+
+// the view and pixel of a ray id
+__device__ __forceinline__ void ray_pixel(const Geo &P, uint32_t ray, int &view, int &px, int &py)
+{
+    const uint32_t v = (uint32_t)(ray / (uint64_t)P.WH);
+    const uint32_t p = ray - v * (uint32_t)P.WH;
+    view = (int)v;
+    px = (int)(p % (uint32_t)P.W);
+    py = (int)(p / (uint32_t)P.W);
+}
 
 
 
@@ -403,7 +422,7 @@ __global__ void smask_kernel(const unsigned long long *__restrict__ fmask, VolGe
 // neighbours.  The live lists keep this order from pass to pass.
 constexpr int kRayTileW = 8, kRayTileH = 4;
 
-inline int64_t tiled_ray_count(int W, int H)
+__host__ __device__ inline int64_t tiled_ray_count(int W, int H)
 {
     return (int64_t)((W + kRayTileW - 1) / kRayTileW) * ((H + kRayTileH - 1) / kRayTileH) * 32;
 }
@@ -430,13 +449,16 @@ __global__ void __launch_bounds__(256) raygen_kernel(Geo P, int H, uint64_t *__r
                                                      int64_t n_tiled, PassState *ps, const uint32_t *lru_reset_flag)
 {
     if (lru_reset_flag && blockIdx.x == 0 && threadIdx.x == 0 && *lru_reset_flag) lru_reset(ps);
-    const Cam cam = *P.camd;
     const VolGeom &g = P.g;
+    const int64_t tpv = tiled_ray_count(P.W, H);   // tiled positions per view
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiled;
          t += (int64_t)gridDim.x * blockDim.x) {   // n_tiled is a multiple of 32: whole warps iterate
-        const int64_t p = tiled_pixel(t, P.W, H);
+        const int64_t view = t / tpv;
+        const int64_t pv = tiled_pixel(t - view * tpv, P.W, H);
         bool in = false;
-        if (p >= 0) {
+        if (pv >= 0) {
+            const int64_t p = view * P.WH + pv;   // ray id
+            const Cam &cam = P.views[view].cam;
             keys[p] = kNoKey;
             depth[p] = INFINITY;
             rgba[p] = 0u;
@@ -444,7 +466,7 @@ __global__ void __launch_bounds__(256) raygen_kernel(Geo P, int H, uint64_t *__r
             cell[p] = kNoKey;
             final_pass[p] = 0;
             Ray r;
-            make_ray(r, cam.eye, cam.p00, cam.du, cam.dv, (int)(p % P.W), (int)(p / P.W));
+            make_ray(r, cam.eye, cam.p00, cam.du, cam.dv, (int)(pv % P.W), (int)(pv / P.W));
             Tq tin{0.f, 1.f}, tout{0.f, 1.f};
             bool have_out = false, outside = false;
             for (int a = 0; a < 3; ++a) {
@@ -484,13 +506,16 @@ struct BitCount {
     __device__ uint32_t operator()(int64_t i) const { return (bits[i >> 5] >> (i & 31)) & 1u; }
 };
 
-// live list 0 from the enter bitmap: position t -> its pixel
+// live list 0 from the enter bitmap: tiled position t -> its ray id
 struct EnterEmit {
     uint32_t *out;
     int W, H;
+    int64_t WH;
     __device__ void operator()(int64_t t, uint32_t pre, uint32_t c) const
     {
-        if (c) out[pre] = (uint32_t)tiled_pixel(t, W, H);
+        if (!c) return;
+        const int64_t tpv = tiled_ray_count(W, H), view = t / tpv;
+        out[pre] = (uint32_t)(view * WH + tiled_pixel(t - view * tpv, W, H));
     }
 };
 
@@ -515,7 +540,6 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
     if (nproc < ps->coop_below) return;   // few rays: traverse_coop_kernel walks them
     const int kk = (int)ps->kk;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
-    const Cam cam = *P.camd;
     // every step moves at least one block index monotonically, so a walk
     // never takes more steps than this; exceeding it is an internal error
     const int max_steps = 2 * (g.tb[0] + g.tb[1] + g.tb[2]) + 8;
@@ -525,7 +549,13 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t ray = live[i];
         Walk w;
-        make_ray(w.r, cam.eye, cam.p00, cam.du, cam.dv, (int)(ray % P.W), (int)(ray / P.W));
+        int view, px, py;
+        ray_pixel(P, ray, view, px, py);
+        {
+            const Cam &cam = P.views[view].cam;
+            make_ray(w.r, cam.eye, cam.p00, cam.du, cam.dv, px, py);
+        }
+        const unsigned long long *fm = P.occ.fmask + view * P.fstride, *sm = P.occ.smask + view * P.sstride;
         const uint64_t st = state_in[ray];
         w.b[0] = (int)(st & 0xFFFF);
         w.b[1] = (int)((st >> 16) & 0xFFFF);
@@ -551,7 +581,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
             const int *b = w.b;
             uint32_t sc = (uint32_t)(b[0] >> 4) + ns0 * ((uint32_t)(b[1] >> 4) + ns1 * (uint32_t)(b[2] >> 4));
             if (sc != cur_s) {
-                smask = __ldg(P.occ.smask + sc);
+                smask = __ldg(sm + sc);
                 cur_s = sc;
             }
             if (!((smask >> (((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) & 1ull)) {
@@ -560,7 +590,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
             }
             uint32_t c = (uint32_t)(b[0] >> 2) + nc0 * ((uint32_t)(b[1] >> 2) + nc1 * (uint32_t)(b[2] >> 2));
             if (c != cur_c) {
-                fmask = __ldg(P.occ.fmask + c);
+                fmask = __ldg(fm + c);
                 cur_c = c;
             }
             if ((fmask >> ((b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) & 1ull) {
@@ -619,7 +649,6 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
     if (nproc >= ps->coop_below) return;
     const int kk = (int)ps->kk;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
-    const Cam cam = *P.camd;
     const int max_steps = 2 * (g.tb[0] + g.tb[1] + g.tb[2]) + 8;
     const uint32_t nb0 = g.nb[0], nb1 = g.nb[1], nc0 = g.nc[0], nc1 = g.nc[1];
     const uint32_t ns0 = P.occ.ns[0], ns1 = P.occ.ns[1];
@@ -633,7 +662,13 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const uint32_t ray = live[i];
         Walk w;
-        make_ray(w.r, cam.eye, cam.p00, cam.du, cam.dv, (int)(ray % P.W), (int)(ray / P.W));
+        int view, px, py;
+        ray_pixel(P, ray, view, px, py);
+        {
+            const Cam &cam = P.views[view].cam;
+            make_ray(w.r, cam.eye, cam.p00, cam.du, cam.dv, px, py);
+        }
+        const unsigned long long *fm = P.occ.fmask + view * P.fstride, *sm = P.occ.smask + view * P.sstride;
         const uint64_t st = state_in[ray];
         w.b[0] = (int)(st & 0xFFFF);
         w.b[1] = (int)((st >> 16) & 0xFFFF);
@@ -661,8 +696,8 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
                 (uint32_t)(b[0] >> 2) + nc0 * ((uint32_t)(b[1] >> 2) + nc1 * (uint32_t)(b[2] >> 2));
             // both masks in flight at once (the coarse one is unused when the
             // super mask says the cell is empty)
-            const unsigned long long smask = __ldg(P.occ.smask + sc);
-            const unsigned long long fmask = __ldg(P.occ.fmask + c);
+            const unsigned long long smask = __ldg(sm + sc);
+            const unsigned long long fmask = __ldg(fm + c);
             if (!((smask >> (((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) & 1ull)) {
                 alive = skip_level(w, g, smask ? 4 : 16, smask ? g.tc : P.occ.ts);
                 continue;
@@ -1361,8 +1396,6 @@ __global__ void __launch_bounds__(128, 4) intersect_kernel(RT R, const uint32_t 
     if (ctr[C_OVERFLOW]) return;
     const uint32_t kk = ps->kk;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
-    const Cam cam = *R.P.camd;
-    const float iso = *R.P.isod;
     const uint32_t n = ctr[C_NENT];
     const VolGeom &g = R.P.g;
     for (;;) {
@@ -1378,7 +1411,11 @@ __global__ void __launch_bounds__(128, 4) intersect_kernel(RT R, const uint32_t 
         // j) wins the atomicMin whatever this block holds
         if ((uint32_t)(__ldcg(keys + ray) >> 52) < j) continue;
         Ray r;
-        make_ray(r, cam.eye, cam.p00, cam.du, cam.dv, (int)(ray % R.P.W), (int)(ray / R.P.W));
+        int view, px, py;
+        ray_pixel(R.P, ray, view, px, py);
+        const View &vw = R.P.views[view];
+        const float iso = vw.iso;
+        make_ray(r, vw.cam.eye, vw.cam.p00, vw.cam.du, vw.cam.dv, px, py);
         int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((uint32_t)g.nb[0] * g.nb[1]));
         uint64_t payload;
         if (intersect_block(R, r, iso, bx, by, bz, payload)) atomicMin(keys + ray, ((uint64_t)j << 52) | payload);
@@ -1652,10 +1689,11 @@ using namespace spr;
 struct spr_renderer {
     spr_volume *vol = nullptr;
     int W = 0, H = 0;
-    int64_t npix = 0;
-    Cam cam{};
-    bool has_cam = false;
-    float iso = 0.5f;
+    int64_t npix = 0;             // rays of all views: n_views * W * H
+    int n_views = 1;
+    View views[kMaxViews] = {};   // camera and isovalue per view
+    uint64_t cam_set = 0;         // bit v: view v has a camera
+    float iso = 0.5f;             // isovalue given to views by spr_set_isovalue
     int spec_mode = SPR_SPEC_ADAPTIVE, k_fixed = 1, k_max = 64;
     uint32_t coop_below = kCoopBelowDefault;
     int64_t n_slots = 0;
@@ -1683,7 +1721,7 @@ struct spr_renderer {
     int64_t launches = 0;         // kernels launched since the last render started
     DevBuf occ_fine, occ_super;   // brick masks per coarse cell and per super cell
     Occ occ{};
-    float occ_iso = NAN;
+    float occ_iso[kMaxViews];     // isovalue each view's brick masks were built for
     // look-back scratch, one set per branch of a pass that can run a scan
     // while another branch runs one: [0] main (grouping, resolve, ray
     // generation), [1] cache, [2] LRU order
@@ -1792,7 +1830,8 @@ int ensure_entry_buffers(spr_renderer *r, cudaStream_t s)
 
 int ensure_scan_scratch(spr_renderer *r, cudaStream_t s)
 {
-    int64_t biggest = std::max({tiled_ray_count(r->W, r->H), r->n_slots, r->nwords, r->cap_entries, r->cap_act,
+    int64_t biggest = std::max({tiled_ray_count(r->W, r->H) * r->n_views, r->n_slots, r->nwords, r->cap_entries,
+                                r->cap_act,
                                 (int64_t)1});
     size_t need = sizeof(unsigned long long) * (scan_tiles(biggest) + 1);
     if (r->scan_status[0].bytes >= need) return SPR_OK;
@@ -1835,9 +1874,12 @@ Geo make_geo(const spr_renderer *r)
     P.g = r->vol->g;
     P.fine = r->vol->fine.as<float2>();
     P.coarse = r->vol->coarse.as<float2>();
-    P.camd = &r->camd.as<DevParams>()->cam;
-    P.isod = &r->camd.as<DevParams>()->iso;
+    P.views = r->camd.as<DevParams>()->views;
     P.W = r->W;
+    P.H = r->H;
+    P.WH = (int64_t)r->W * r->H;
+    P.fstride = r->vol->g.ncoarse;
+    P.sstride = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
     P.occ = r->occ;
     return P;
 }
@@ -1845,17 +1887,26 @@ Geo make_geo(const spr_renderer *r)
 // occupancy bitmaps for the current isovalue (recomputed when it changes)
 int update_occupancy(spr_renderer *r, cudaStream_t s)
 {
-    if (r->occ_iso == r->iso) return SPR_OK;
     const VolGeom &g = r->vol->g;
-    int64_t ns = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
-    fmask_kernel<<<grid_for(g.ncoarse, 128, 16), 128, 0, s>>>(r->vol->fine.as<float2>(), g, r->iso,
-                                                              r->occ_fine.as<unsigned long long>());
-    smask_kernel<<<grid_for(ns, 128, 16), 128, 0, s>>>(r->occ_fine.as<unsigned long long>(), g, r->occ,
-                                                       r->occ_super.as<unsigned long long>());
-    count_launch(2);
-    SPR_CUDA_TRY(cudaGetLastError());
-    r->occ_iso = r->iso;
+    const int64_t ns = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
+    for (int v = 0; v < r->n_views; ++v) {
+        const float iso = r->views[v].iso;
+        if (r->occ_iso[v] == iso) continue;
+        unsigned long long *fm = r->occ_fine.as<unsigned long long>() + v * g.ncoarse;
+        unsigned long long *sm = r->occ_super.as<unsigned long long>() + v * ns;
+        fmask_kernel<<<grid_for(g.ncoarse, 128, 16), 128, 0, s>>>(r->vol->fine.as<float2>(), g, iso, fm);
+        smask_kernel<<<grid_for(ns, 128, 16), 128, 0, s>>>(fm, g, r->occ, sm);
+        count_launch(2);
+        SPR_CUDA_TRY(cudaGetLastError());
+        r->occ_iso[v] = iso;
+    }
     return SPR_OK;
+}
+
+// bytes of the parameter block that are copied: the header and n_views views
+inline size_t params_bytes(const spr_renderer *r)
+{
+    return offsetof(DevParams, views) + sizeof(View) * (size_t)r->n_views;
 }
 
 // Fill the pinned parameter block (after the previous copy out of it ran).
@@ -1863,8 +1914,8 @@ int write_params(spr_renderer *r, uint32_t more, uint32_t reset)
 {
     SPR_CUDA_TRY(cudaEventSynchronize(r->ev_upload));
     DevParams &h = *r->h_params;
-    h.cam = r->cam;
-    h.iso = r->iso;
+    h.n_views = (uint32_t)r->n_views;
+    for (int v = 0; v < r->n_views; ++v) h.views[v] = r->views[v];
     h.spec_mode = (uint32_t)r->spec_mode;
     h.k_fixed = (uint32_t)r->k_fixed;
     h.k_max = (uint32_t)r->k_max;
@@ -1881,7 +1932,7 @@ int upload_params(spr_renderer *r, cudaStream_t s)
 {
     if (!r->params_dirty) return SPR_OK;
     SPR_TRY(write_params(r, 0u, 0u));
-    SPR_CUDA_TRY(cudaMemcpyAsync(r->camd.p, r->h_params, sizeof(DevParams), cudaMemcpyHostToDevice, s));
+    SPR_CUDA_TRY(cudaMemcpyAsync(r->camd.p, r->h_params, params_bytes(r), cudaMemcpyHostToDevice, s));
     SPR_CUDA_TRY(cudaEventRecord(r->ev_upload, s));
     config_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), r->camd.as<DevParams>());
     count_launch();
@@ -1898,7 +1949,7 @@ int enqueue_raygen_body(spr_renderer *r, cudaStream_t s, const DevParams *dp)
 {
     uint32_t *ctr = r->ctr.as<uint32_t>();
     if (!dp) SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
-    const int64_t n_tiled = tiled_ray_count(r->W, r->H);
+    const int64_t n_tiled = tiled_ray_count(r->W, r->H) * r->n_views;
     raygen_kernel<<<grid_for(n_tiled, 256, 8), 256, 0, s>>>(
         make_geo(r), r->H, r->state_in.as<uint64_t>(), r->status.as<uint8_t>(), r->keys.as<uint64_t>(),
         r->fb_depth.as<float>(), r->fb_rgba.as<uint32_t>(), r->fb_block.as<uint32_t>(), r->fb_cell.as<uint64_t>(),
@@ -1908,7 +1959,8 @@ int enqueue_raygen_body(spr_renderer *r, cudaStream_t s, const DevParams *dp)
     SPR_CUDA_TRY(cudaGetLastError());
     SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], ctr + C_SCANFLAGS, n_tiled, nullptr,
                         BitCount{r->lbits.as<uint32_t>(), nullptr},
-                        EnterEmit{r->live[0].as<uint32_t>(), r->W, r->H}, ctr + C_NLIVE, s));
+                        EnterEmit{r->live[0].as<uint32_t>(), r->W, r->H, (int64_t)r->W * r->H}, ctr + C_NLIVE,
+                        s));
     after_raygen_kernel<<<1, 32, 0, s>>>(r->ps.as<PassState>(), ctr, r->d_hps, dp ? &dp->more : nullptr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
@@ -2106,7 +2158,8 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
 int check_ready(spr_renderer *r)
 {
     if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
-    if (!r->has_cam) return set_error(SPR_ERR_INVALID_ARG, "no camera set");
+    const uint64_t all = r->n_views == 64 ? ~0ull : ((1ull << r->n_views) - 1);
+    if ((r->cam_set & all) != all) return set_error(SPR_ERR_INVALID_ARG, "a view has no camera");
     if (r->n_slots < 8) return set_error(SPR_ERR_CACHE_TOO_SMALL, "cache budget below 8 slots");
     return SPR_OK;
 }
@@ -2226,6 +2279,35 @@ int build_prof_graph(spr_renderer *r)
     return SPR_OK;
 }
 
+// Buffers sized by the rays of all views: per-ray state, live lists, keys,
+// framebuffer, the enter/alive bitmap and the brick masks (one set per view).
+// Frees the previous ones first.
+int alloc_view_buffers(spr_renderer *r)
+{
+    cudaStream_t s = nullptr;
+    DevBuf *bufs[] = {&r->state_in, &r->state_out, &r->status, &r->live[0], &r->live[1], &r->keys,
+                      &r->fb_depth, &r->fb_rgba, &r->fb_block, &r->fb_cell, &r->fb_final, &r->lbits,
+                      &r->occ_fine, &r->occ_super};
+    for (DevBuf *b : bufs) buf_free(*b, s);
+    const int64_t np = r->npix;
+    const int64_t ns = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
+    int rc;
+    if ((rc = buf_alloc(r->state_in, 8 * np, s)) || (rc = buf_alloc(r->state_out, 8 * np, s)) ||
+        (rc = buf_alloc(r->status, np, s)) || (rc = buf_alloc(r->live[0], 4 * np, s)) ||
+        (rc = buf_alloc(r->live[1], 4 * np, s)) || (rc = buf_alloc(r->keys, 8 * np, s)) ||
+        (rc = buf_alloc(r->fb_depth, 4 * np, s)) || (rc = buf_alloc(r->fb_rgba, 4 * np, s)) ||
+        (rc = buf_alloc(r->fb_block, 4 * np, s)) || (rc = buf_alloc(r->fb_cell, 8 * np, s)) ||
+        (rc = buf_alloc(r->fb_final, 4 * np, s)) ||
+        (rc = buf_alloc(r->lbits, 4 * (tiled_ray_count(r->W, r->H) * r->n_views / 32 + 1), s)) ||
+        (rc = buf_alloc(r->occ_fine, 8 * r->vol->g.ncoarse * r->n_views, s)) ||
+        (rc = buf_alloc(r->occ_super, 8 * ns * r->n_views, s)))
+        return rc;
+    r->occ.fmask = r->occ_fine.as<unsigned long long>();
+    r->occ.smask = r->occ_super.as<unsigned long long>();
+    for (int v = 0; v < kMaxViews; ++v) r->occ_iso[v] = NAN;
+    return SPR_OK;
+}
+
 // The start of a render as one graph: copy the parameter block, apply the
 // speculation settings, empty the cache if asked, generate rays (with_raygen)
 // and set the pass limit.  Kernels in it: 4 with ray generation, else 2.
@@ -2240,7 +2322,7 @@ int build_start_graph(spr_renderer *r, bool with_raygen)
     SPR_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int64_t saved = r->launches;
     int rc = SPR_OK;
-    cudaError_t e = cudaMemcpyAsync(dp, r->h_params, sizeof(DevParams), cudaMemcpyHostToDevice, cs);
+    cudaError_t e = cudaMemcpyAsync(dp, r->h_params, params_bytes(r), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) {
         start_kernel<<<grid_for(r->n_slots, 256, 8), 256, 0, cs>>>(ps, dp, r->ctr.as<uint32_t>(),
                                                                   r->slot_blk.as<uint32_t>(),
@@ -2327,21 +2409,18 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
     r->nwords = (vol->g.nblocks + 31) / 32;
     r->n_slots = (int64_t)(256u << 20) / 256;
     cudaStream_t s = nullptr;
-    const int64_t np = r->npix;
     int rc = SPR_OK;
-    if ((rc = buf_alloc(r->state_in, 8 * np, s)) || (rc = buf_alloc(r->state_out, 8 * np, s)) ||
-        (rc = buf_alloc(r->status, np, s)) || (rc = buf_alloc(r->live[0], 4 * np, s)) ||
-        (rc = buf_alloc(r->live[1], 4 * np, s)) || (rc = buf_alloc(r->keys, 8 * np, s)) ||
-        (rc = buf_alloc(r->fb_depth, 4 * np, s)) || (rc = buf_alloc(r->fb_rgba, 4 * np, s)) ||
-        (rc = buf_alloc(r->fb_block, 4 * np, s)) || (rc = buf_alloc(r->fb_cell, 8 * np, s)) ||
-        (rc = buf_alloc(r->fb_final, 4 * np, s)) || (rc = buf_alloc(r->vis_bits, 4 * r->nwords, s)) ||
+    for (int v = 0; v < kMaxViews; ++v) {
+        r->views[v].iso = r->iso;
+        r->occ_iso[v] = NAN;
+    }
+    if ((rc = buf_alloc(r->vis_bits, 4 * r->nwords, s)) ||
         (rc = buf_alloc(r->act_bits, 4 * r->nwords, s)) || (rc = buf_alloc(r->vis_wpre, 4 * r->nwords, s)) ||
         (rc = buf_alloc(r->act_wpre, 4 * r->nwords, s)) ||
         (rc = buf_alloc(r->blk_slot, 4 * vol->g.nblocks, s)) || (rc = buf_alloc(r->scan_ticket[0], 64, s)) ||
         (rc = buf_alloc(r->scan_ticket[1], 64, s)) || (rc = buf_alloc(r->scan_ticket[2], 64, s)) ||
         (rc = buf_alloc(r->ctr, sizeof(uint32_t) * C_COUNT, s)) ||
         (rc = buf_alloc(r->ps, sizeof(PassState), s)) ||
-        (rc = buf_alloc(r->lbits, 4 * (tiled_ray_count(width, height) / 32 + 1), s)) ||
         (rc = buf_alloc(r->camd, sizeof(DevParams) + 16, s))) {
         free_all(r);
         delete r;
@@ -2380,15 +2459,10 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
         r->occ.ns[a] = (vol->g.nc[a] + 3) / 4;
         r->occ.ts[a] = (vol->g.tc[a] + 3) / 4;
     }
-    {
-        int64_t ns = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
-        if ((rc = buf_alloc(r->occ_fine, 8 * vol->g.ncoarse, s)) || (rc = buf_alloc(r->occ_super, 8 * ns, s))) {
-            free_all(r);
-            delete r;
-            return rc;
-        }
-        r->occ.fmask = r->occ_fine.as<unsigned long long>();
-        r->occ.smask = r->occ_super.as<unsigned long long>();
+    if ((rc = alloc_view_buffers(r))) {
+        free_all(r);
+        delete r;
+        return rc;
     }
     int64_t slots = r->n_slots;
     r->n_slots = 0;
@@ -2416,11 +2490,9 @@ static bool basis_ok(float x)
     return std::isfinite(x) && (a == 0.f || (a >= 0x1p-40f && a <= 0x1p40f));
 }
 
-extern "C" int spr_set_camera(spr_renderer *r, const float eye[3], const float p00[3], const float du[3],
-                              const float dv[3])
+static int check_camera(const float eye[3], const float p00[3], const float du[3], const float dv[3])
 {
-    clear_error();
-    if (!r || !eye || !p00 || !du || !dv) return set_error(SPR_ERR_INVALID_ARG, "NULL camera argument");
+    if (!eye || !p00 || !du || !dv) return set_error(SPR_ERR_INVALID_ARG, "NULL camera argument");
     for (int a = 0; a < 3; ++a) {
         double e = eye[a];
         if (!std::isfinite(eye[a]) || std::fabs(e) >= 16384.0 || e * 256.0 != std::floor(e * 256.0))
@@ -2429,13 +2501,65 @@ extern "C" int spr_set_camera(spr_renderer *r, const float eye[3], const float p
         if (!basis_ok(p00[a]) || !basis_ok(du[a]) || !basis_ok(dv[a]))
             return set_error(SPR_ERR_INVALID_ARG, "camera basis component %d outside {0} or [2^-40, 2^40]", a);
     }
+    return SPR_OK;
+}
+
+extern "C" int spr_set_view_count(spr_renderer *r, int n_views)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    if (n_views < 1 || n_views > kMaxViews)
+        return set_error(SPR_ERR_INVALID_ARG, "n_views = %d outside [1, %d]", n_views, kMaxViews);
+    const int64_t np = (int64_t)r->W * r->H * n_views;
+    if (np > (int64_t)1 << 28) return set_error(SPR_ERR_INVALID_ARG, "views x width x height above 2^28 rays");
+    if (r->spec_mode == SPR_SPEC_FIXED && np * r->k_fixed > 0x7FFFFFFFll)
+        return set_error(SPR_ERR_INVALID_ARG, "views x width x height x k exceeds 2^31 entries");
+    if (n_views == r->n_views) return SPR_OK;
+    cudaDeviceSynchronize();
+    drop_graph(r);
+    r->n_views = n_views;
+    r->npix = np;
+    int rc = alloc_view_buffers(r);
+    r->need_raygen = true;
+    r->params_dirty = true;
+    return rc;
+}
+
+extern "C" int spr_set_view(spr_renderer *r, int view, const float eye[3], const float p00[3], const float du[3],
+                            const float dv[3], float iso)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    if (view < 0 || view >= r->n_views)
+        return set_error(SPR_ERR_INVALID_ARG, "view %d outside [0, %d)", view, r->n_views);
+    if (!std::isfinite(iso)) return set_error(SPR_ERR_INVALID_ARG, "bad isovalue");
+    SPR_TRY(check_camera(eye, p00, du, dv));
     for (int a = 0; a < 3; ++a) {
-        r->cam.eye[a] = eye[a];
-        r->cam.p00[a] = p00[a];
-        r->cam.du[a] = du[a];
-        r->cam.dv[a] = dv[a];
+        r->views[view].cam.eye[a] = eye[a];
+        r->views[view].cam.p00[a] = p00[a];
+        r->views[view].cam.du[a] = du[a];
+        r->views[view].cam.dv[a] = dv[a];
     }
-    r->has_cam = true;
+    r->views[view].iso = iso;
+    r->cam_set |= 1ull << view;
+    r->need_raygen = true;
+    r->params_dirty = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_set_camera(spr_renderer *r, const float eye[3], const float p00[3], const float du[3],
+                              const float dv[3])
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_camera(eye, p00, du, dv));
+    for (int a = 0; a < 3; ++a) {
+        r->views[0].cam.eye[a] = eye[a];
+        r->views[0].cam.p00[a] = p00[a];
+        r->views[0].cam.du[a] = du[a];
+        r->views[0].cam.dv[a] = dv[a];
+    }
+    r->cam_set |= 1ull;
     r->need_raygen = true;
     r->params_dirty = true;
     return SPR_OK;
@@ -2446,6 +2570,7 @@ extern "C" int spr_set_isovalue(spr_renderer *r, float iso)
     clear_error();
     if (!r || !std::isfinite(iso)) return set_error(SPR_ERR_INVALID_ARG, "bad isovalue");
     r->iso = iso;
+    for (int v = 0; v < kMaxViews; ++v) r->views[v].iso = iso;
     r->need_raygen = true;
     r->params_dirty = true;
     return SPR_OK;
@@ -2632,7 +2757,7 @@ extern "C" int spr_get_framebuffer(spr_renderer *r, spr_framebuffer *out)
     clear_error();
     if (!r || !out) return set_error(SPR_ERR_INVALID_ARG, "NULL argument");
     out->width = r->W;
-    out->height = r->H;
+    out->height = r->H * r->n_views;   // the views stacked top to bottom
     out->depth = r->fb_depth.as<float>();
     out->rgba = r->fb_rgba.as<uint32_t>();
     out->block = r->fb_block.as<uint32_t>();

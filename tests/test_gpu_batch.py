@@ -1,0 +1,103 @@
+"""Batched rendering: several views (camera, isovalue) of one volume in one
+wavefront with a shared cache.  Each view's image must equal its single-view
+render (the batch only changes which pass a pixel finishes in), and match the
+oracle; the shared cache decodes no more blocks than the views rendered one
+by one."""
+import numpy as np
+import pytest
+
+import synth
+from test_gpu_render import Scene, compare
+
+pytestmark = pytest.mark.gpu
+
+FB_KEYS = ("depth", "rgba", "block", "cell", "status")
+
+
+@pytest.fixture(scope="module")
+def spr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2309_10212_gb300 as m
+    return m
+
+
+def views_of(orc, dims, seed, n, W, H, isos):
+    vol = synth.volumes.value_noise(dims, seed=seed, ref=max(dims))
+    scenes = []
+    for v in range(n):
+        iso = float(np.float32(np.quantile(vol, isos[v % len(isos)])))
+        cam = synth.cameras.random_pose(dims, seed=seed + 10 * v + 1, W=W, H=H, distance_factor=1.6)
+        scenes.append(Scene(orc, dims, vol, 8, iso, cam, W, H))
+    return scenes
+
+
+def render_batch(spr, scenes, slots=None, **spec):
+    import torch
+    sc0 = scenes[0]
+    v = spr.spr_create_volume(sc0.dims, sc0.rate, torch.from_numpy(sc0.comp).cuda())
+    r = spr.spr_create_renderer(v, sc0.W, sc0.H)
+    nb = sc0.ovol.fine.shape[0]
+    spr.spr_set_cache_budget(r, 256 * (slots if slots else max(8, nb)))
+    if spec.get("mode") == "fixed":
+        spr.spr_set_speculation(r, spr.SPR_SPEC_FIXED, k=spec["k"])
+    else:
+        spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=spec.get("k_max", 64))
+    spr.spr_set_view_count(r, len(scenes))
+    for i, sc in enumerate(scenes):
+        spr.spr_set_view(r, i, sc.cam, sc.iso)
+    rs, passes = spr.spr_render_to_convergence(r, 100000)
+    fb = spr.spr_read_framebuffer(r)
+    r.close()
+    v.close()
+    n = sc0.W * sc0.H
+    return [{k: fb[k][i * n:(i + 1) * n] for k in fb} for i in range(len(scenes))], rs, passes
+
+
+@pytest.mark.parametrize("spec", [dict(mode="fixed", k=1), dict(mode="fixed", k=3), dict(k_max=64)])
+def test_batch_views_equal_single_renders(spr, orc, spec):
+    scenes = views_of(orc, (40, 36, 32), 7, 4, 64, 48, (0.4, 0.6))
+    batch, rs, _ = render_batch(spr, scenes, **spec)
+    decoded_single = 0
+    for sc, fb in zip(scenes, batch):
+        single, rs1, _ = render_batch(spr, [sc], **spec)
+        for key in FB_KEYS:
+            assert np.array_equal(fb[key], single[0][key]), key
+        compare(sc, fb)
+        decoded_single += rs1["blocks_decoded"]
+    assert rs["converged"] == 1
+    assert rs["blocks_decoded"] <= decoded_single
+
+
+def test_batch_tight_cache(spr, orc):
+    """24 slots for 3 views: the overflow rule halves k and the ray window
+    over the combined live list; images are unchanged."""
+    scenes = views_of(orc, (48, 40, 44), 21, 3, 48, 40, (0.62,))
+    batch, rs, passes = render_batch(spr, scenes, slots=24)
+    assert any(p["retries"] for p in passes)
+    for sc, fb in zip(scenes, batch):
+        single, _, _ = render_batch(spr, [sc])
+        for key in FB_KEYS:
+            assert np.array_equal(fb[key], single[0][key]), key
+        compare(sc, fb)
+
+
+def test_view_count_limits(spr, orc):
+    import torch
+    sc = views_of(orc, (16, 16, 16), 2, 1, 16, 16, (0.5,))[0]
+    v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    r = spr.spr_create_renderer(v, 16, 16)
+    for bad in (0, 65):
+        with pytest.raises(spr.SprError):
+            spr.spr_set_view_count(r, bad)
+    spr.spr_set_view_count(r, 2)
+    spr.spr_set_view(r, 0, sc.cam, sc.iso)
+    with pytest.raises(spr.SprError):      # view 1 has no camera
+        spr.spr_render_to_convergence(r, 100)
+    with pytest.raises(spr.SprError):
+        spr.spr_set_view(r, 2, sc.cam, sc.iso)
+    r.close()
+    v.close()
