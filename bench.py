@@ -308,6 +308,52 @@ def run_study(args, wl):
                     "entries": round(mean("entries"), 1),
                     "utilization_per_pass": round(mean("entries") / max(mean("passes"), 1e-9) / (W * H), 4)}
 
+        # batched views: B orbit poses in one wavefront with a shared cache,
+        # against the same poses rendered one by one
+        if wl["poses"] >= 4:
+            from paper_2309_10212_gb300 import tune
+            out["batch"] = []
+            for B in (1, 2, 4, 8, 16):
+                r = spr.spr_create_renderer(vol, wl["W"], wl["H"])
+                spr.spr_set_cache_budget(r, wl["cache_bytes"])
+                spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=wl["k"])
+                spr.spr_set_isovalue(r, wl["iso"])
+                spr.spr_set_view_count(r, B)
+                times, dec, npass, att = [], [], [], []
+                for rep in range(3):
+                    flush.fill_(rep & 255)
+                    for v in range(B):          # (re)starts the render; host only
+                        spr.spr_set_view(r, v, pose(wl, v), wl["iso"])
+                    rs = _lib.RenderStats()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    _lib.check(L.spr_reset_cache(r.handle))
+                    _lib.check(L.spr_render_to_convergence(r.handle, ctypes.c_void_p(stream.cuda_stream), 4096,
+                                                           ctypes.byref(rs), None))
+                    b.record(stream)
+                    b.synchronize()
+                    if rep:
+                        times.append(a.elapsed_time(b))
+                        dec.append(rs.blocks_decoded)
+                        npass.append(rs.passes)
+                        att.append(rs.kernel_launches)
+                r.close()
+                out["batch"].append({"views": B, "ms": round(statistics.mean(times), 4),
+                                     "ms_per_view": round(statistics.mean(times) / B, 4),
+                                     "blocks_decoded_per_view": round(statistics.mean(dec) / B, 1),
+                                     "passes": round(statistics.mean(npass), 2),
+                                     "kernel_launches": round(statistics.mean(att), 1)})
+            # the autotuner on the first four poses
+            r = spr.spr_create_renderer(vol, wl["W"], wl["H"])
+            spr.spr_set_cache_budget(r, wl["cache_bytes"])
+            spr.spr_set_isovalue(r, wl["iso"])
+            spr.spr_set_camera(r, pose(wl, 0))
+            res = tune.autotune(r, [pose(wl, i) for i in range(4)], k_max=(4, 8, 16, 32, 64),
+                                warp_walk=(4096, 16384, 65536), stream=stream)
+            r.close()
+            out["autotune"] = res
+
         out["k_sweep"] = [measure(wl["W"], wl["H"], "fixed", k) for k in (1, 2, 4, 8, 16)]
         out["k_sweep"] += [measure(wl["W"], wl["H"], "adaptive", k) for k in (16, 64)]
         spec = wl["spec"]

@@ -101,3 +101,26 @@ def test_view_count_limits(spr, orc):
         spr.spr_set_view(r, 2, sc.cam, sc.iso)
     r.close()
     v.close()
+
+
+def test_autotune_picks_a_candidate_and_keeps_the_image(spr, orc):
+    import torch
+    from paper_2309_10212_gb300 import tune
+    scenes = views_of(orc, (40, 36, 32), 7, 2, 64, 48, (0.5,))
+    sc = scenes[0]
+    want, _, _ = render_batch(spr, [sc])
+    v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    r = spr.spr_create_renderer(v, sc.W, sc.H)
+    spr.spr_set_cache_budget(r, 256 * sc.ovol.fine.shape[0])
+    spr.spr_set_isovalue(r, sc.iso)
+    spr.spr_set_camera(r, sc.cam)
+    res = tune.autotune(r, [s.cam for s in scenes], k_max=(2, 64), warp_walk=(0, 1 << 20))
+    assert (res["k_max"], res["warp_walk"]) in [(2, 0), (2, 1 << 20), (64, 0), (64, 1 << 20)]
+    assert len(res["table"]) == 4
+    spr.spr_set_camera(r, sc.cam)
+    spr.spr_render_to_convergence(r, 100000)
+    got = spr.spr_read_framebuffer(r)
+    r.close()
+    v.close()
+    for key in FB_KEYS:
+        assert np.array_equal(got[key], want[0][key]), key
