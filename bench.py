@@ -367,6 +367,142 @@ def run_study(args, wl):
     return 0
 
 
+SERVE_VOLUMES = [
+    # (name, dims, generator, cache bytes per view)
+    ("256^3 u8 Gaussian blobs (100)", (256, 256, 256), "blobs256", int(0.10 * 256 ** 3 * 4)),
+    ("1024^3 u8 Gaussian blobs (800)", (1024, 1024, 1024), "blobs1024", int(0.10 * 1024 ** 3 * 4)),
+    ("2048x2048x1920 u8 mixing layer", (2048, 2048, 1920), "paper", 1 << 30),
+]
+SERVE_RES = [(640, 360), (1280, 720), (1920, 1080)]
+
+
+def serve_trace(n, rate_hz, seed=11):
+    """n requests: Poisson arrivals (mean rate_hz), a volume and a resolution
+    uniform over the three, a random camera and an isovalue uniform in
+    [0.2, 0.8] (rounded to float32)."""
+    import numpy as np
+
+    import synth
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate_hz, size=n)
+    t = np.cumsum(gaps) - gaps[0]
+    out = []
+    for i in range(n):
+        vi = int(rng.integers(0, len(SERVE_VOLUMES)))
+        W, H = SERVE_RES[int(rng.integers(0, len(SERVE_RES)))]
+        iso = float(np.float32(rng.uniform(0.2, 0.8)))
+        dims = SERVE_VOLUMES[vi][1]
+        cam = synth.cameras.random_pose(dims, seed=1000 + i, W=W, H=H,
+                                        distance_factor=float(rng.uniform(1.3, 2.0)))
+        out.append(dict(t=float(t[i]), vol=vi, W=W, H=H, iso=iso, cam=cam))
+    return out
+
+
+def run_serve(args):
+    """The render service (config: 256 requests arriving as a Poisson process
+    at 20/s over three resident volumes, resolutions 640x360 / 1280x720 /
+    1920x1080, random cameras, isovalues in [0.2, 0.8], an 8 GB device
+    memory budget for the pooled renderers).  Reports p50/p99 time to first
+    pass and to final image, then the same requests as a burst (all queued at
+    once) with and without overlap and batching."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2309_10212_gb300 import build
+    build.build()
+    import paper_2309_10212_gb300 as spr
+    out = {"config": "256 requests, Poisson 20/s, volumes " + ", ".join(v[0] for v in SERVE_VOLUMES) +
+                     ", resolutions 640x360/1280x720/1920x1080, iso U[0.2,0.8], 8 GB memory budget"}
+    t0 = time.perf_counter()
+    vols = []
+    for name, dims, gen, cache in SERVE_VOLUMES:
+        if gen == "paper":
+            comp = compressed_on_device(WORKLOADS["paper"], spr, torch)
+        else:
+            n = 100 if dims[0] == 256 else 800
+            u8 = synth.volumes.gaussian_blobs(dims, seed=6 if dims[0] == 256 else 7, n=n, device="cuda")
+            comp = spr.spr_encode_u8(u8, 2)
+            del u8
+        vols.append((spr.spr_create_volume(dims, 2, comp), cache))
+        del comp
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    out["setup_s"] = round(time.perf_counter() - t0, 1)
+    trace = serve_trace(args.serve_requests, args.serve_rate)
+
+    def run(trace, max_inflight, max_batch, k_max, realtime, memory=8 << 30, server=None):
+        srv = server or spr.spr_server_create(memory, max_inflight=max_inflight, max_batch=max_batch,
+                                              k_max=k_max)
+        if server is None:
+            srv.ids = [spr.spr_server_add_volume(srv, v, c) for v, c in vols]
+        res = {}
+        info0 = spr.spr_server_info(srv)
+        base = spr.spr_server_clock(srv)
+        i = 0
+        while len(res) < len(trace):
+            now = spr.spr_server_clock(srv) - base
+            while i < len(trace) and (not realtime or trace[i]["t"] <= now):
+                q = trace[i]
+                t_arr = base + q["t"] if realtime else -1.0
+                spr.spr_server_submit(srv, srv.ids[q["vol"]], q["cam"], q["iso"], q["W"], q["H"],
+                                      t_arrival=t_arr)
+                i += 1
+            for r_ in spr.spr_server_poll(srv):
+                res[r_["id"]] = r_
+        info = spr.spr_server_info(srv)
+        rows = [res[k] for k in sorted(res)]
+        assert all(r_["status"] == 0 for r_ in rows), [r_ for r_ in rows if r_["status"]][:3]
+        ttfp = np.array([r_["t_first_pass"] - r_["t_arrival"] for r_ in rows]) * 1e3
+        fin = np.array([r_["t_done"] - r_["t_arrival"] for r_ in rows]) * 1e3
+        span = max(r_["t_done"] for r_ in rows) - min(r_["t_arrival"] for r_ in rows)
+        # blocks decoded per request: a batch's count is shared by its requests
+        dec = sum(r_["blocks_decoded"] / r_["batch"] for r_ in rows)
+        return srv, {"max_inflight": max_inflight, "max_batch": max_batch, "k_max": k_max,
+                     "requests": len(rows), "makespan_s": round(span, 4),
+                     "requests_per_s": round(len(rows) / span, 2),
+                     "ttfp_ms_p50": round(float(np.percentile(ttfp, 50)), 3),
+                     "ttfp_ms_p99": round(float(np.percentile(ttfp, 99)), 3),
+                     "final_ms_p50": round(float(np.percentile(fin, 50)), 3),
+                     "final_ms_p99": round(float(np.percentile(fin, 99)), 3),
+                     "mean_batch": round(float(np.mean([r_["batch"] for r_ in rows])), 2),
+                     "blocks_decoded_per_request": round(dec / len(rows), 1),
+                     "renders": info["renders"] - info0["renders"],
+                     "renderers_created": info["renderers_created"] - info0["renderers_created"],
+                     "renderers_destroyed": info["renderers_destroyed"] - info0["renderers_destroyed"],
+                     "memory_used_gb": round(info["memory_used"] / 1e9, 2)}
+
+    # autotune the speculation cap on a burst of the first 48 requests
+    tune_rows = []
+    for k_max in (16, 32, 64):
+        srv, row = run(trace[:48], 4, 8, k_max, False)
+        _, row = run(trace[:48], 4, 8, k_max, False, server=srv)   # warm pool
+        srv.close()
+        tune_rows.append(row)
+    k_best = min(tune_rows, key=lambda r_: r_["makespan_s"])["k_max"]
+    out["autotune_k_max"] = {"table": [{k: r_[k] for k in ("k_max", "makespan_s")} for r_ in tune_rows],
+                             "chosen": k_best}
+    # Poisson arrivals in real time; the pool is warmed by the same requests
+    # as a burst first (renderer creation and graph capture excluded)
+    srv, _ = run(trace, 4, 8, k_best, False)
+    _, out["poisson"] = run(trace, 4, 8, k_best, True, server=srv)
+    _, out["burst_batched"] = run(trace, 4, 8, k_best, False, server=srv)
+    srv.close()
+    srv, _ = run(trace, 1, 1, k_best, False)
+    _, out["burst_plain"] = run(trace, 1, 1, k_best, False, server=srv)
+    srv.close()
+    srv, _ = run(trace, 4, 1, k_best, False)
+    _, out["burst_overlap_only"] = run(trace, 4, 1, k_best, False, server=srv)
+    srv.close()
+    for v, _ in vols:
+        v.close()
+    with open(args.serve, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps({"serve": args.serve, "poisson": out["poisson"],
+                      "burst_batched": out["burst_batched"], "burst_plain": out["burst_plain"]}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,6 +516,11 @@ def main():
     ap.add_argument("--study", default="",
                     help="instead of the bench line: write the speculation sweep, resolution "
                          "scaling and decode-all-active comparison to this JSON file")
+    ap.add_argument("--serve", default="",
+                    help="instead of the bench line: run the render service on a Poisson request "
+                         "trace and write latency percentiles to this JSON file")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--k-max", type=int, default=0,
                     help="override the workload's speculation limit (k sweeps; 0 keeps it)")
     args = ap.parse_args()
@@ -391,6 +532,8 @@ def main():
         return run_reference(args, wl)
     if args.study:
         return run_study(args, wl)
+    if args.serve:
+        return run_serve(args)
     if args.warmup < 3:
         args.warmup = 3
 

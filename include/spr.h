@@ -226,9 +226,12 @@ int spr_set_isovalue(spr_renderer *r, float iso);
  * floor(n_views*w*h / N_Act))) and the block cache, so a block decoded for
  * one view serves all.  Each view's image equals its single-view render.
  * The framebuffer holds the views stacked top to bottom (height * n_views
- * rows); ray / pixel ids are view * w * h + y * w + x.  Reallocates the
- * per-pixel buffers and restarts the render; every view needs a camera
- * (spr_set_camera sets view 0, spr_set_view any). */
+ * rows); ray / pixel ids are view * w * h + y * w + x.  The per-pixel
+ * buffers and captured graphs grow to the largest count set so far (that
+ * reallocation synchronises the device); a count within that capacity
+ * reuses them (views past n_views generate no rays).  Restarts the render;
+ * every view needs a camera (spr_set_camera sets view 0, spr_set_view
+ * any). */
 int spr_set_view_count(spr_renderer *r, int n_views);
 /* camera (as spr_set_camera) and isovalue of view `view` < n_views */
 int spr_set_view(spr_renderer *r, int view, const float eye[3], const float p00[3], const float du[3],
@@ -273,6 +276,122 @@ int spr_get_framebuffer(spr_renderer *r, spr_framebuffer *out);
 int spr_read_framebuffer(spr_renderer *r, spr_stream stream, float *depth, uint32_t *rgba,
                          uint32_t *block, uint64_t *cell, int32_t *final_pass,
                          uint8_t *status);
+
+/* ------------------------------------------------------ asynchronous render */
+/* The render of spr_render_to_convergence (without profiling) enqueued on
+ * `stream` without waiting: ray generation when the render restarts, then
+ * passes until no ray is live or max_passes ran.  Until spr_render_collect,
+ * the renderer accepts only spr_render_query, spr_render_collect,
+ * spr_get_framebuffer and spr_destroy_renderer (other calls return
+ * SPR_ERR_INVALID_ARG); the framebuffer is complete once `stream` reaches
+ * the end of the render.  Renders of different renderers submitted on
+ * different streams overlap on the device.  With profiling on:
+ * SPR_ERR_INVALID_ARG. */
+int spr_render_submit(spr_renderer *r, spr_stream stream, int max_passes);
+/* Non-blocking progress of a submitted render: *passes_done = passes
+ * completed so far (read from the pass-state mirror the device writes into
+ * mapped host memory after every pass, the progressive display of Sec. 3),
+ * *done = 1 when the device has finished the render (either may be NULL).
+ * Without a submitted render: 0 passes, done. */
+int spr_render_query(spr_renderer *r, int32_t *passes_done, int32_t *done);
+/* Wait for the submitted render and report it as spr_render_to_convergence
+ * does (same statuses, e.g. SPR_ERR_NOT_CONVERGED). */
+int spr_render_collect(spr_renderer *r, spr_render_stats *out, spr_pass_stats *per_pass);
+/* device bytes the renderer holds now (buffers grown by earlier renders
+ * included) */
+int spr_renderer_memory(const spr_renderer *r, size_t *device_bytes);
+/* device bytes a renderer of this shape holds after its first render:
+ * n_views views of width x height, cache_bytes of block cache, speculation
+ * mode and fixed k (ignored when adaptive) */
+int spr_renderer_memory_estimate(const spr_volume *vol, int width, int height, int n_views,
+                                 size_t cache_bytes, int spec_mode, int k, size_t *device_bytes);
+
+/* ----------------------------------------------------------------- serving */
+/*
+ * A render service (no counterpart in the paper, which renders one view at a
+ * time): requests -- a volume, an image size, a camera and an isovalue --
+ * are queued and admitted while an in-flight slot (one CUDA stream each, at
+ * most max_inflight) is free and the device memory budget holds the renderer
+ * the request needs.  Renderers (block cache, wavefront buffers and captured
+ * pass graphs) are pooled and reused across requests, so a volume's cache
+ * stays warm between requests; when the budget is short, idle renderers are
+ * released, least recently used first (those no queued request wants go
+ * first); a request whose shape has a busy renderer waits for it instead of
+ * releasing others.  Queued requests of the same volume and image size are
+ * merged, oldest first and up to max_batch and the renderer's view capacity,
+ * into one batched render (spr_set_view_count): one wavefront, one
+ * speculation budget, one cache.  Requests of one shape start in arrival
+ * order; the oldest request that can start does, so a shape whose
+ * renderers are busy does not hold up the others.  Every result equals the
+ * request's single-view render (the
+ * image does not depend on the cache state, the speculation count or the
+ * batch).  The scheduler runs on the calling host thread inside
+ * spr_server_poll; one thread uses a server at a time.  Creating a pooled
+ * renderer allocates device memory and synchronises the device, so the
+ * first request of each (volume, size, batch) shape waits for the renders
+ * in flight.
+ */
+typedef struct spr_server spr_server;
+
+typedef struct {
+    size_t  memory_bytes;   /* budget for the pooled renderers' device memory */
+    int32_t max_inflight;   /* renders on the device at once, 1..64           */
+    int32_t max_batch;      /* requests merged into one render, 1..64         */
+    int32_t spec_mode;      /* SPR_SPEC_FIXED or SPR_SPEC_ADAPTIVE            */
+    int32_t k, k_max;       /* as spr_set_speculation                          */
+    int32_t max_passes;     /* per render                                      */
+} spr_server_desc;
+
+typedef struct {
+    int32_t volume;             /* id from spr_server_add_volume                */
+    int32_t width, height;
+    float   eye[3], p00[3], du[3], dv[3];   /* as spr_set_camera              */
+    float   iso;
+    double  t_arrival;          /* seconds on spr_server_clock; < 0: now        */
+    /* caller-owned device buffers of width*height entries (any may be NULL),
+     * filled by the device when the request completes (as spr_framebuffer) */
+    float    *depth;
+    uint32_t *rgba;
+    uint32_t *block;
+    uint8_t  *status;
+} spr_request;
+
+typedef struct {
+    int64_t id;
+    int32_t status;             /* SPR_OK or the render's error                 */
+    int32_t passes;             /* passes of its render                         */
+    int32_t batch;              /* requests in its render                       */
+    int32_t reserved;
+    double  t_arrival, t_admit, t_first_pass, t_done;  /* spr_server_clock     */
+    int64_t blocks_decoded;     /* of its render (shared by the batch)          */
+    int64_t entries;            /* ray-block entries of its render              */
+    float   ms_device;          /* device time of its render                    */
+} spr_result;
+
+typedef struct {
+    int64_t pending, in_flight, renderers;
+    size_t  memory_used;        /* device bytes of the pooled renderers         */
+    int64_t renders, requests_done, renderers_created, renderers_destroyed;
+} spr_server_stats;
+
+int spr_server_create(const spr_server_desc *desc, spr_server **out);
+/* waits for the renders in flight, then releases every pooled renderer */
+int spr_server_destroy(spr_server *s);
+/* Register a resident volume (it must outlive the server);
+ * cache_bytes_per_view (>= 8 slots) sizes the block cache of its renders:
+ * a render of n views gets n times that. */
+int spr_server_add_volume(spr_server *s, spr_volume *vol, size_t cache_bytes_per_view,
+                          int32_t *volume_id);
+/* seconds since the server was created (a monotonic clock) */
+double spr_server_clock(const spr_server *s);
+/* Queue a request (copied); *id (may be NULL) numbers requests 0, 1, ... */
+int spr_server_submit(spr_server *s, const spr_request *req, int64_t *id);
+/* Never blocks: notes first passes, completes finished renders, admits
+ * queued requests, and returns up to max_out completed requests' results in
+ * completion order (*n_out of them).  A request that can never fit the
+ * budget completes with SPR_ERR_OUT_OF_MEMORY. */
+int spr_server_poll(spr_server *s, spr_result *out, int max_out, int *n_out);
+int spr_server_info(const spr_server *s, spr_server_stats *out);
 
 /* --------------------------------------------------------------- scan */
 /* Exclusive prefix sum of n uint32 values (device in/out; in == out allowed),

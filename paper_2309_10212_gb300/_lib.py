@@ -76,6 +76,42 @@ class Framebuffer(ctypes.Structure):
                 ("final_pass", ctypes.c_void_p), ("status", ctypes.c_void_p)]
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("memory_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("spec_mode", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("k_max", ctypes.c_int32), ("max_passes", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("volume", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("eye", ctypes.c_float * 3), ("p00", ctypes.c_float * 3),
+                ("du", ctypes.c_float * 3), ("dv", ctypes.c_float * 3), ("iso", ctypes.c_float),
+                ("t_arrival", ctypes.c_double), ("depth", ctypes.c_void_p),
+                ("rgba", ctypes.c_void_p), ("block", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_first_pass", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("blocks_decoded", ctypes.c_int64), ("entries", ctypes.c_int64),
+                ("ms_device", ctypes.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("renderers", ctypes.c_int64), ("memory_used", ctypes.c_size_t),
+                ("renders", ctypes.c_int64), ("requests_done", ctypes.c_int64),
+                ("renderers_created", ctypes.c_int64), ("renderers_destroyed", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                            ctypes.c_void_p)
@@ -112,6 +148,18 @@ PROTOTYPES = {
     "spr_exclusive_scan_u32": ([_vp, _vp, _i64, _vp, _vp], _i32),
     "spr_debug_scan_withhold": ([_vp, _vp, _i64, _i64, _i64, _vp], _i32),
     "spr_exclusive_scan_u32_noalloc": ([_vp, _vp, _i64, _vp, _vp], _i32),
+    "spr_render_submit": ([_vp, _vp, _i32], _i32),
+    "spr_render_query": ([_vp, _vp, _vp], _i32),
+    "spr_render_collect": ([_vp, _vp, _vp], _i32),
+    "spr_renderer_memory": ([_vp, _vp], _i32),
+    "spr_renderer_memory_estimate": ([_vp, _i32, _i32, _i32, _sz, _i32, _i32, _vp], _i32),
+    "spr_server_create": ([_vp, _vp], _i32),
+    "spr_server_destroy": ([_vp], _i32),
+    "spr_server_add_volume": ([_vp, _vp, _sz, _vp], _i32),
+    "spr_server_clock": ([_vp], ctypes.c_double),
+    "spr_server_submit": ([_vp, _vp, _vp], _i32),
+    "spr_server_poll": ([_vp, _vp, _i32, _vp], _i32),
+    "spr_server_info": ([_vp, _vp], _i32),
 }
 
 _lock = threading.Lock()

@@ -316,6 +316,136 @@ def spr_read_framebuffer(r: Renderer, stream=None) -> dict:
     return out
 
 
+# ---------------------------------------------------- asynchronous render
+def spr_render_submit(r: Renderer, max_passes: int = 10000, stream=None):
+    """Enqueue a whole render on `stream` without waiting."""
+    check(load().spr_render_submit(r.handle, _stream(stream), int(max_passes)))
+
+
+def spr_render_query(r: Renderer):
+    """(passes completed so far, device finished) of a submitted render."""
+    p, d = ctypes.c_int32(), ctypes.c_int32()
+    check(load().spr_render_query(r.handle, ctypes.byref(p), ctypes.byref(d)))
+    return p.value, bool(d.value)
+
+
+def spr_render_collect(r: Renderer, allow_partial: bool = False):
+    """Wait for the submitted render; returns (render stats, [pass stats])."""
+    rs = _lib.RenderStats()
+    per = (_lib.PassStats * 4096)()
+    status = load().spr_render_collect(r.handle, ctypes.byref(rs), per)
+    if not (allow_partial and status == _lib.SPR_ERR_NOT_CONVERGED):
+        check(status)
+    return rs.as_dict(), [per[i].as_dict() for i in range(min(rs.passes, 4096))]
+
+
+def spr_renderer_memory(r: Renderer) -> int:
+    n = ctypes.c_size_t()
+    check(load().spr_renderer_memory(r.handle, ctypes.byref(n)))
+    return n.value
+
+
+def spr_renderer_memory_estimate(vol: Volume, W: int, H: int, n_views: int, cache_bytes: int,
+                                 mode: int = SPR_SPEC_ADAPTIVE, k: int = 1) -> int:
+    n = ctypes.c_size_t()
+    check(load().spr_renderer_memory_estimate(vol.handle, int(W), int(H), int(n_views),
+                                              int(cache_bytes), int(mode), int(k), ctypes.byref(n)))
+    return n.value
+
+
+# ---------------------------------------------------------------- serving
+class Server:
+    """A render service (spr_server_*): queued requests admitted by free
+    streams and device memory, merged into batched renders, overlapped on
+    the device.  `outputs` keeps the caller's result tensors alive until the
+    request completes."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.outputs = {}
+        self.volumes = []
+
+    def close(self):
+        if self.handle:
+            check(load().spr_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spr_server_create(memory_bytes: int, max_inflight: int = 4, max_batch: int = 8,
+                      mode: int = SPR_SPEC_ADAPTIVE, k: int = 1, k_max: int = 64,
+                      max_passes: int = 100000) -> Server:
+    d = _lib.ServerDesc(int(memory_bytes), int(max_inflight), int(max_batch), int(mode), int(k),
+                        int(k_max), int(max_passes))
+    h = ctypes.c_void_p()
+    check(load().spr_server_create(ctypes.byref(d), ctypes.byref(h)))
+    return Server(h)
+
+
+def spr_server_destroy(s: Server):
+    s.close()
+
+
+def spr_server_add_volume(s: Server, vol: Volume, cache_bytes_per_view: int) -> int:
+    i = ctypes.c_int32()
+    check(load().spr_server_add_volume(s.handle, vol.handle, int(cache_bytes_per_view),
+                                       ctypes.byref(i)))
+    s.volumes.append(vol)
+    return i.value
+
+
+def spr_server_clock(s: Server) -> float:
+    return load().spr_server_clock(s.handle)
+
+
+def spr_server_submit(s: Server, volume: int, cam: dict, iso: float, W: int, H: int,
+                      t_arrival: float = -1.0, outputs: dict | None = None) -> int:
+    """Queue a request; `outputs` maps depth/rgba/block/status to CUDA tensors
+    of W*H entries that receive the image.  Returns the request id."""
+    q = _lib.Request()
+    q.volume, q.width, q.height = int(volume), int(W), int(H)
+    q.eye[:] = [float(x) for x in np.asarray(cam["eye"], np.float32)]
+    q.p00[:] = [float(x) for x in np.asarray(cam["p00"], np.float32)]
+    q.du[:] = [float(x) for x in np.asarray(cam["du"], np.float32)]
+    q.dv[:] = [float(x) for x in np.asarray(cam["dv"], np.float32)]
+    q.iso = float(iso)
+    q.t_arrival = float(t_arrival)
+    outputs = outputs or {}
+    for name in ("depth", "rgba", "block", "status"):
+        t = outputs.get(name)
+        if t is not None:
+            assert t.numel() >= W * H
+            setattr(q, name, _dev_ptr(t).value)
+    i = ctypes.c_int64()
+    check(load().spr_server_submit(s.handle, ctypes.byref(q), ctypes.byref(i)))
+    if outputs:
+        s.outputs[i.value] = outputs
+    return i.value
+
+
+def spr_server_poll(s: Server, max_out: int = 256) -> list:
+    """Advance the service; returns the results of requests completed since
+    the last poll (dicts)."""
+    out = (_lib.Result * max_out)()
+    n = ctypes.c_int()
+    check(load().spr_server_poll(s.handle, out, int(max_out), ctypes.byref(n)))
+    res = [out[i].as_dict() for i in range(n.value)]
+    for r in res:
+        s.outputs.pop(r["id"], None)
+    return res
+
+
+def spr_server_info(s: Server) -> dict:
+    st = _lib.ServerStats()
+    check(load().spr_server_info(s.handle, ctypes.byref(st)))
+    return st.as_dict()
+
+
 # -------------------------------------------------------------- allocator
 _keep = []
 

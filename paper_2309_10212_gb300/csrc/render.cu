@@ -446,15 +446,19 @@ __global__ void __launch_bounds__(256) raygen_kernel(Geo P, int H, uint64_t *__r
                                                      float *__restrict__ depth, uint32_t *__restrict__ rgba,
                                                      uint32_t *__restrict__ block, uint64_t *__restrict__ cell,
                                                      int32_t *__restrict__ final_pass, uint32_t *__restrict__ enter,
-                                                     int64_t n_tiled, PassState *ps, const uint32_t *lru_reset_flag)
+                                                     int64_t n_tiled, PassState *ps, const uint32_t *lru_reset_flag,
+                                                     const uint32_t *n_views_dev, uint32_t n_views_host)
 {
     if (lru_reset_flag && blockIdx.x == 0 && threadIdx.x == 0 && *lru_reset_flag) lru_reset(ps);
     const VolGeom &g = P.g;
     const int64_t tpv = tiled_ray_count(P.W, H);   // tiled positions per view
+    // views at or beyond the active count (a renderer sized for more views)
+    // generate no rays and leave their pixels untouched
+    const int64_t n_act = (int64_t)(n_views_dev ? *n_views_dev : n_views_host) * tpv;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiled;
          t += (int64_t)gridDim.x * blockDim.x) {   // n_tiled is a multiple of 32: whole warps iterate
         const int64_t view = t / tpv;
-        const int64_t pv = tiled_pixel(t - view * tpv, P.W, H);
+        const int64_t pv = t < n_act ? tiled_pixel(t - view * tpv, P.W, H) : -1;
         bool in = false;
         if (pv >= 0) {
             const int64_t p = view * P.WH + pv;   // ray id
@@ -1689,8 +1693,10 @@ using namespace spr;
 struct spr_renderer {
     spr_volume *vol = nullptr;
     int W = 0, H = 0;
-    int64_t npix = 0;             // rays of all views: n_views * W * H
-    int n_views = 1;
+    int64_t npix = 0;             // rays of the active views: n_views * W * H
+    int n_views = 1;              // active views (views >= n_views generate no rays)
+    int view_cap = 1;             // views the buffers and captured graphs are sized for
+    int64_t npix_cap = 0;         // view_cap * W * H
     View views[kMaxViews] = {};   // camera and isovalue per view
     uint64_t cam_set = 0;         // bit v: view v has a camera
     float iso = 0.5f;             // isovalue given to views by spr_set_isovalue
@@ -1748,6 +1754,12 @@ struct spr_renderer {
     cudaGraphExec_t gexec = nullptr;
     cudaGraphExec_t gprof = nullptr;  // one attempt with event nodes between stages
     int graph_kernels = 0;        // kernels in one pass of the body
+    // a render enqueued by spr_render_submit and not yet collected
+    bool busy = false;
+    cudaStream_t sub_stream = nullptr;
+    bool sub_fresh = false;
+    int sub_first = 0;            // passes completed before the submitted render
+    PassState sub_before{};       // pass state before it (totals of a continued render)
 };
 
 namespace {
@@ -1803,7 +1815,7 @@ void free_all(spr_renderer *r)
 int64_t entries_needed(const spr_renderer *r)
 {
     int64_t k = r->spec_mode == SPR_SPEC_FIXED ? r->k_fixed : 1;
-    return std::max<int64_t>(1, r->npix * k);
+    return std::max<int64_t>(1, r->npix_cap * k);
 }
 
 int ensure_entry_buffers(spr_renderer *r, cudaStream_t s)
@@ -1830,7 +1842,7 @@ int ensure_entry_buffers(spr_renderer *r, cudaStream_t s)
 
 int ensure_scan_scratch(spr_renderer *r, cudaStream_t s)
 {
-    int64_t biggest = std::max({tiled_ray_count(r->W, r->H) * r->n_views, r->n_slots, r->nwords, r->cap_entries,
+    int64_t biggest = std::max({tiled_ray_count(r->W, r->H) * r->view_cap, r->n_slots, r->nwords, r->cap_entries,
                                 r->cap_act,
                                 (int64_t)1});
     size_t need = sizeof(unsigned long long) * (scan_tiles(biggest) + 1);
@@ -1903,10 +1915,12 @@ int update_occupancy(spr_renderer *r, cudaStream_t s)
     return SPR_OK;
 }
 
-// bytes of the parameter block that are copied: the header and n_views views
+// bytes of the parameter block that are copied: the header and view_cap
+// views (the start graph's copy node keeps its size while the active count
+// changes within the capacity; views past n_views are not read)
 inline size_t params_bytes(const spr_renderer *r)
 {
-    return offsetof(DevParams, views) + sizeof(View) * (size_t)r->n_views;
+    return offsetof(DevParams, views) + sizeof(View) * (size_t)r->view_cap;
 }
 
 // Fill the pinned parameter block (after the previous copy out of it ran).
@@ -1949,12 +1963,12 @@ int enqueue_raygen_body(spr_renderer *r, cudaStream_t s, const DevParams *dp)
 {
     uint32_t *ctr = r->ctr.as<uint32_t>();
     if (!dp) SPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * C_COUNT, s));
-    const int64_t n_tiled = tiled_ray_count(r->W, r->H) * r->n_views;
+    const int64_t n_tiled = tiled_ray_count(r->W, r->H) * r->view_cap;
     raygen_kernel<<<grid_for(n_tiled, 256, 8), 256, 0, s>>>(
         make_geo(r), r->H, r->state_in.as<uint64_t>(), r->status.as<uint8_t>(), r->keys.as<uint64_t>(),
         r->fb_depth.as<float>(), r->fb_rgba.as<uint32_t>(), r->fb_block.as<uint32_t>(), r->fb_cell.as<uint64_t>(),
         r->fb_final.as<int32_t>(), r->lbits.as<uint32_t>(), n_tiled, r->ps.as<PassState>(),
-        dp ? &dp->reset : nullptr);
+        dp ? &dp->reset : nullptr, dp ? &dp->n_views : nullptr, (uint32_t)r->n_views);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], ctr + C_SCANFLAGS, n_tiled, nullptr,
@@ -2045,7 +2059,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     count_launch();
 
     // (a) traversal with speculation, marking visible and active blocks
-    traverse_kernel<<<grid_for(r->npix, 128, 16), 128, 0, s>>>(
+    traverse_kernel<<<grid_for(r->npix_cap, 128, 16), 128, 0, s>>>(
         make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
         r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr);
     count_launch();
@@ -2133,14 +2147,14 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     if (events) SPR_CUDA_TRY(record(r->ev[5], s, capturing));
 
     // (f) resolve hits and exits, compact the live rays in order, end the pass
-    resolve_kernel<<<grid_for(r->npix, 256, 8), 256, 0, s>>>(
+    resolve_kernel<<<grid_for(r->npix_cap, 256, 8), 256, 0, s>>>(
         live0, live1, ps, g.dims[0], g.dims[1], g, r->keys.as<unsigned long long>(), r->rbid.as<uint32_t>(),
         r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(), r->status.as<uint8_t>(), r->fb_depth.as<float>(),
         r->fb_rgba.as<uint32_t>(), r->fb_block.as<uint32_t>(), r->fb_cell.as<uint64_t>(), r->fb_final.as<int32_t>(),
         r->lbits.as<uint32_t>(), ctr);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
-    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, r->npix, &ps->n_live,
+    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, r->npix_cap, &ps->n_live,
                         BitCount{r->lbits.as<uint32_t>(), ctr + C_OVERFLOW}, LiveEmit{live0, live1, ps},
                         ctr + C_NLIVE, s));
     if (fork) {   // the LRU order must be complete before the pass ends
@@ -2289,7 +2303,7 @@ int alloc_view_buffers(spr_renderer *r)
                       &r->fb_depth, &r->fb_rgba, &r->fb_block, &r->fb_cell, &r->fb_final, &r->lbits,
                       &r->occ_fine, &r->occ_super};
     for (DevBuf *b : bufs) buf_free(*b, s);
-    const int64_t np = r->npix;
+    const int64_t np = r->npix_cap;
     const int64_t ns = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
     int rc;
     if ((rc = buf_alloc(r->state_in, 8 * np, s)) || (rc = buf_alloc(r->state_out, 8 * np, s)) ||
@@ -2298,9 +2312,9 @@ int alloc_view_buffers(spr_renderer *r)
         (rc = buf_alloc(r->fb_depth, 4 * np, s)) || (rc = buf_alloc(r->fb_rgba, 4 * np, s)) ||
         (rc = buf_alloc(r->fb_block, 4 * np, s)) || (rc = buf_alloc(r->fb_cell, 8 * np, s)) ||
         (rc = buf_alloc(r->fb_final, 4 * np, s)) ||
-        (rc = buf_alloc(r->lbits, 4 * (tiled_ray_count(r->W, r->H) * r->n_views / 32 + 1), s)) ||
-        (rc = buf_alloc(r->occ_fine, 8 * r->vol->g.ncoarse * r->n_views, s)) ||
-        (rc = buf_alloc(r->occ_super, 8 * ns * r->n_views, s)))
+        (rc = buf_alloc(r->lbits, 4 * (tiled_ray_count(r->W, r->H) * r->view_cap / 32 + 1), s)) ||
+        (rc = buf_alloc(r->occ_fine, 8 * r->vol->g.ncoarse * r->view_cap, s)) ||
+        (rc = buf_alloc(r->occ_super, 8 * ns * r->view_cap, s)))
         return rc;
     r->occ.fmask = r->occ_fine.as<unsigned long long>();
     r->occ.smask = r->occ_super.as<unsigned long long>();
@@ -2394,6 +2408,13 @@ int build_graph(spr_renderer *r)
 
 }  // namespace
 
+// settings and synchronous renders wait until a submitted render is collected
+static int check_idle(const spr_renderer *r)
+{
+    if (r->busy) return set_error(SPR_ERR_INVALID_ARG, "a submitted render has not been collected");
+    return SPR_OK;
+}
+
 extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_renderer **out)
 {
     clear_error();
@@ -2406,6 +2427,7 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
     r->W = width;
     r->H = height;
     r->npix = (int64_t)width * height;
+    r->npix_cap = r->npix;
     r->nwords = (vol->g.nblocks + 31) / 32;
     r->n_slots = (int64_t)(256u << 20) / 256;
     cudaStream_t s = nullptr;
@@ -2508,6 +2530,7 @@ extern "C" int spr_set_view_count(spr_renderer *r, int n_views)
 {
     clear_error();
     if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
     if (n_views < 1 || n_views > kMaxViews)
         return set_error(SPR_ERR_INVALID_ARG, "n_views = %d outside [1, %d]", n_views, kMaxViews);
     const int64_t np = (int64_t)r->W * r->H * n_views;
@@ -2515,14 +2538,19 @@ extern "C" int spr_set_view_count(spr_renderer *r, int n_views)
     if (r->spec_mode == SPR_SPEC_FIXED && np * r->k_fixed > 0x7FFFFFFFll)
         return set_error(SPR_ERR_INVALID_ARG, "views x width x height x k exceeds 2^31 entries");
     if (n_views == r->n_views) return SPR_OK;
-    cudaDeviceSynchronize();
-    drop_graph(r);
-    r->n_views = n_views;
-    r->npix = np;
-    int rc = alloc_view_buffers(r);
     r->need_raygen = true;
     r->params_dirty = true;
-    return rc;
+    if (n_views <= r->view_cap) {
+        // within the allocated views: buffers and captured graphs stay
+        r->n_views = n_views;
+        r->npix = np;
+        return SPR_OK;
+    }
+    cudaDeviceSynchronize();
+    drop_graph(r);
+    r->n_views = r->view_cap = n_views;
+    r->npix = r->npix_cap = np;
+    return alloc_view_buffers(r);
 }
 
 extern "C" int spr_set_view(spr_renderer *r, int view, const float eye[3], const float p00[3], const float du[3],
@@ -2530,6 +2558,7 @@ extern "C" int spr_set_view(spr_renderer *r, int view, const float eye[3], const
 {
     clear_error();
     if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
     if (view < 0 || view >= r->n_views)
         return set_error(SPR_ERR_INVALID_ARG, "view %d outside [0, %d)", view, r->n_views);
     if (!std::isfinite(iso)) return set_error(SPR_ERR_INVALID_ARG, "bad isovalue");
@@ -2552,6 +2581,7 @@ extern "C" int spr_set_camera(spr_renderer *r, const float eye[3], const float p
 {
     clear_error();
     if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
     SPR_TRY(check_camera(eye, p00, du, dv));
     for (int a = 0; a < 3; ++a) {
         r->views[0].cam.eye[a] = eye[a];
@@ -2569,6 +2599,7 @@ extern "C" int spr_set_isovalue(spr_renderer *r, float iso)
 {
     clear_error();
     if (!r || !std::isfinite(iso)) return set_error(SPR_ERR_INVALID_ARG, "bad isovalue");
+    SPR_TRY(check_idle(r));
     r->iso = iso;
     for (int v = 0; v < kMaxViews; ++v) r->views[v].iso = iso;
     r->need_raygen = true;
@@ -2580,6 +2611,7 @@ extern "C" int spr_set_cache_budget(spr_renderer *r, size_t bytes)
 {
     clear_error();
     if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
     int64_t slots = (int64_t)(bytes / 256);
     if (slots < 8) return set_error(SPR_ERR_CACHE_TOO_SMALL, "cache budget of %zu bytes is below 8 slots", bytes);
     if (slots > 0x7FFFFFFFll) return set_error(SPR_ERR_INVALID_ARG, "cache budget too large");
@@ -2608,9 +2640,10 @@ extern "C" int spr_set_speculation(spr_renderer *r, int mode, int k, int k_max)
 {
     clear_error();
     if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
     if (mode == SPR_SPEC_FIXED) {
         if (k < 1 || k > SPR_K_LIMIT) return set_error(SPR_ERR_INVALID_ARG, "k = %d outside [1, %d]", k, SPR_K_LIMIT);
-        if (r->npix * (int64_t)k > 0x7FFFFFFFll)
+        if (r->npix_cap * (int64_t)k > 0x7FFFFFFFll)
             return set_error(SPR_ERR_INVALID_ARG, "width*height*k exceeds 2^31 entries");
         r->k_fixed = k;
     } else if (mode == SPR_SPEC_ADAPTIVE) {
@@ -2630,6 +2663,7 @@ extern "C" int spr_set_warp_walk_threshold(spr_renderer *r, int64_t n_rays)
 {
     clear_error();
     if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
     if (n_rays < 0) return set_error(SPR_ERR_INVALID_ARG, "n_rays must be non-negative");
     r->coop_below = (uint32_t)std::min<int64_t>(n_rays, 0xFFFFFFFFll);
     r->params_dirty = true;
@@ -2640,6 +2674,7 @@ extern "C" int spr_reset_cache(spr_renderer *r)
 {
     clear_error();
     if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
     r->cache_dirty = true;
     return SPR_OK;
 }
@@ -2648,13 +2683,108 @@ extern "C" int spr_set_profiling(spr_renderer *r, int on)
 {
     clear_error();
     if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
     r->profiling = on != 0;
     return SPR_OK;
 }
 
+namespace {
+
+// The whole render on the device, enqueued without waiting: the start graph
+// (parameters, cache reset, ray generation, pass limit), then one launch of
+// the pass graph whose while node runs passes until none is live.  Only
+// first-time clears and the brick masks of a new isovalue are launched
+// outside the graphs.  ev[0] marks the end of the render on `s`.
+int submit_render(spr_renderer *r, cudaStream_t s, int max_passes)
+{
+    SPR_TRY(check_ready(r));
+    if (max_passes < 1) return set_error(SPR_ERR_INVALID_ARG, "max_passes must be positive");
+    if (r->profiling) return set_error(SPR_ERR_INVALID_ARG, "profiled renders are host-driven: turn profiling off");
+    const bool fresh = r->need_raygen;
+    SPR_TRY(ensure_entry_buffers(r, s));
+    SPR_TRY(ensure_scan_scratch(r, s));
+    struct Scope {
+        Scope(int64_t *p) { g_launch_counter = p; }
+        ~Scope() { g_launch_counter = nullptr; }
+    } scope(&r->launches);
+    if (fresh) r->launches = 0;
+    if (r->cache_dirty && !r->cache_init) SPR_TRY(reset_cache(r, s));
+    const uint32_t reset = r->cache_dirty ? 1u : 0u;
+    if (fresh) SPR_TRY(update_occupancy(r, s));
+    SPR_TRY(clear_bits_if_dirty(r, s));
+    SPR_TRY(build_start_graph(r, fresh));
+    SPR_TRY(build_graph(r));
+    SPR_TRY(write_params(r, (uint32_t)max_passes, reset));
+    if (fresh) {
+        // no kernel of this renderer is in flight (the last render was
+        // collected): start the mirror's pass count at zero, so that a query
+        // before ray generation has run sees no pass of this render
+        *(volatile uint32_t *)&r->h_ps->pass = 0u;
+    }
+    r->sub_before = *r->h_ps;
+    SPR_CUDA_TRY(cudaEventRecord(r->ev[7], s));
+    SPR_CUDA_TRY(cudaGraphLaunch(fresh ? r->gstart : r->glimit, s));
+    SPR_CUDA_TRY(cudaEventRecord(r->ev_upload, s));
+    SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
+    r->launches += fresh ? 4 : 2;
+    r->cache_dirty = false;
+    r->params_dirty = false;
+    if (fresh) {
+        r->need_raygen = false;
+        r->pass = 0;
+    }
+    r->sub_fresh = fresh;
+    r->sub_first = r->pass;
+    SPR_CUDA_TRY(cudaGraphLaunch(r->gexec, s));
+    SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
+    r->sub_stream = s;
+    r->busy = true;
+    return SPR_OK;
+}
+
+// Wait for a submitted render and fill its statistics.
+int collect_render(spr_renderer *r, spr_render_stats *out, spr_pass_stats *per_pass)
+{
+    if (!r->busy) return set_error(SPR_ERR_INVALID_ARG, "no render was submitted");
+    r->busy = false;
+    const int first = r->sub_first;
+    const bool fresh = r->sub_fresh;
+    const PassState &before = r->sub_before;
+    SPR_TRY(read_state(r, r->sub_stream));
+    spr_render_stats rs;
+    memset(&rs, 0, sizeof rs);
+    const int passes = r->pass - first;
+    const PassState &after = *r->h_ps;
+    const bool same = !fresh;   // totals restart at ray generation
+    rs.blocks_decoded = (int64_t)(after.tot_decoded - (same ? before.tot_decoded : 0));
+    rs.entries = (int64_t)(after.tot_entries - (same ? before.tot_entries : 0));
+    rs.evictions = (int64_t)(after.tot_evicted - (same ? before.tot_evicted : 0));
+    rs.n_hits = (int64_t)(after.tot_hits - (same ? before.tot_hits : 0));
+    int64_t attempts = (int64_t)after.attempts - (same ? (int64_t)before.attempts : 0);
+    int nrec = std::max(0, std::min(first + passes, spr_renderer::kRecCap) - first);
+    if (per_pass && nrec > 0) memcpy(per_pass, r->h_recs + first, sizeof(spr_pass_stats) * nrec);
+    r->launches += (int64_t)r->graph_kernels * std::max<int64_t>(attempts, 1);
+    float t_all = 0.f, t_ray = 0.f;
+    cudaEventElapsedTime(&t_all, r->ev[7], r->ev[0]);
+    cudaEventElapsedTime(&t_ray, r->ev[7], r->ev[1]);
+    rs.ms_raygen = fresh ? t_ray : 0.f;
+    rs.ms_total = t_all;
+    rs.passes = passes;
+    rs.n_rays = r->n_enter;
+    rs.converged = r->n_live == 0;
+    rs.bytes_decoded = rs.blocks_decoded * 256;
+    rs.kernel_launches = r->launches;
+    if (out) *out = rs;
+    if (!rs.converged) return set_error(SPR_ERR_NOT_CONVERGED, "%d passes left rays live", passes);
+    return SPR_OK;
+}
+
+}  // namespace
+
 extern "C" int spr_render_pass(spr_renderer *r, spr_stream stream, spr_pass_stats *out)
 {
     clear_error();
+    if (r) SPR_TRY(check_idle(r));
     return do_pass(r, as_stream(stream), out);
 }
 
@@ -2663,6 +2793,7 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
 {
     clear_error();
     SPR_TRY(check_ready(r));
+    SPR_TRY(check_idle(r));
     if (max_passes < 1) return set_error(SPR_ERR_INVALID_ARG, "max_passes must be positive");
     cudaStream_t s = as_stream(stream);
     spr_render_stats rs;
@@ -2688,59 +2819,8 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
         rs.ms_raygen = fresh ? r->ms_raygen : 0.f;
         rs.ms_total = ms + rs.ms_raygen;
     } else {
-        // the whole render on the device: ray generation, then one graph
-        // launch whose while node runs passes until none is live
-        // parameters, cache reset, ray generation and the pass limit travel
-        // in the start graph; only first-time clears and occupancy masks for
-        // a new isovalue are launched from here
-        SPR_TRY(ensure_entry_buffers(r, s));
-        SPR_TRY(ensure_scan_scratch(r, s));
-        struct Scope {
-            Scope(int64_t *p) { g_launch_counter = p; }
-            ~Scope() { g_launch_counter = nullptr; }
-        } scope(&r->launches);
-        if (fresh) r->launches = 0;
-        if (r->cache_dirty && !r->cache_init) SPR_TRY(reset_cache(r, s));
-        const uint32_t reset = r->cache_dirty ? 1u : 0u;
-        if (fresh) SPR_TRY(update_occupancy(r, s));
-        SPR_TRY(clear_bits_if_dirty(r, s));
-        SPR_TRY(build_start_graph(r, fresh));
-        SPR_TRY(build_graph(r));
-        SPR_TRY(write_params(r, (uint32_t)max_passes, reset));
-        SPR_CUDA_TRY(cudaEventRecord(r->ev[7], s));
-        SPR_CUDA_TRY(cudaGraphLaunch(fresh ? r->gstart : r->glimit, s));
-        SPR_CUDA_TRY(cudaEventRecord(r->ev_upload, s));
-        SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));
-        r->launches += fresh ? 4 : 2;
-        r->cache_dirty = false;
-        r->params_dirty = false;
-        if (fresh) {
-            r->need_raygen = false;
-            r->pass = 0;
-        }
-        int first = r->pass;
-        const PassState before = *r->h_ps;
-        SPR_CUDA_TRY(cudaGraphLaunch(r->gexec, s));
-        SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
-        SPR_TRY(read_state(r, s));
-        passes = r->pass - first;
-        const PassState &after = *r->h_ps;
-        const bool same = !fresh;   // totals restart at ray generation
-        rs.blocks_decoded = (int64_t)(after.tot_decoded - (same ? before.tot_decoded : 0));
-        rs.entries = (int64_t)(after.tot_entries - (same ? before.tot_entries : 0));
-        rs.evictions = (int64_t)(after.tot_evicted - (same ? before.tot_evicted : 0));
-        rs.n_hits = (int64_t)(after.tot_hits - (same ? before.tot_hits : 0));
-        int64_t attempts = (int64_t)after.attempts - (same ? (int64_t)before.attempts : 0);
-        int nrec = std::max(0, std::min(first + passes, spr_renderer::kRecCap) - first);
-        if (per_pass && nrec > 0) {
-            memcpy(per_pass, r->h_recs + first, sizeof(spr_pass_stats) * nrec);
-        }
-        r->launches += (int64_t)r->graph_kernels * std::max<int64_t>(attempts, 1);
-        float t_all = 0.f, t_ray = 0.f;
-        cudaEventElapsedTime(&t_all, r->ev[7], r->ev[0]);
-        cudaEventElapsedTime(&t_ray, r->ev[7], r->ev[1]);
-        rs.ms_raygen = fresh ? t_ray : 0.f;
-        rs.ms_total = t_all;
+        SPR_TRY(submit_render(r, s, max_passes));
+        return collect_render(r, out, per_pass);
     }
     rs.passes = passes;
     rs.n_rays = r->n_enter;
@@ -2749,6 +2829,87 @@ extern "C" int spr_render_to_convergence(spr_renderer *r, spr_stream stream, int
     rs.kernel_launches = r->launches;
     if (out) *out = rs;
     if (!rs.converged) return set_error(SPR_ERR_NOT_CONVERGED, "%d passes left rays live", passes);
+    return SPR_OK;
+}
+
+extern "C" int spr_render_submit(spr_renderer *r, spr_stream stream, int max_passes)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
+    return submit_render(r, as_stream(stream), max_passes);
+}
+
+extern "C" int spr_render_query(spr_renderer *r, int32_t *passes_done, int32_t *done)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    if (!r->busy) {
+        if (passes_done) *passes_done = 0;
+        if (done) *done = 1;
+        return SPR_OK;
+    }
+    // the pass count is the mirror that end_pass_kernel writes to mapped
+    // host memory after every pass; read after the event, so that a finished
+    // render reports its final count
+    cudaError_t e = cudaEventQuery(r->ev[0]);
+    const uint32_t p = *(volatile const uint32_t *)&r->h_ps->pass;
+    if (e != cudaSuccess && e != cudaErrorNotReady)
+        return set_error(SPR_ERR_CUDA, "render query: %s", cudaGetErrorString(e));
+    if (passes_done) *passes_done = (int32_t)std::max<int64_t>(0, (int64_t)p - r->sub_first);
+    if (done) *done = e == cudaSuccess ? 1 : 0;
+    return SPR_OK;
+}
+
+extern "C" int spr_render_collect(spr_renderer *r, spr_render_stats *out, spr_pass_stats *per_pass)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    return collect_render(r, out, per_pass);
+}
+
+extern "C" int spr_renderer_memory(const spr_renderer *r, size_t *device_bytes)
+{
+    clear_error();
+    if (!r || !device_bytes) return set_error(SPR_ERR_INVALID_ARG, "NULL argument");
+    const DevBuf *bufs[] = {&r->state_in, &r->state_out, &r->status, &r->live[0], &r->live[1], &r->keys,
+                            &r->fb_depth, &r->fb_rgba, &r->fb_block, &r->fb_cell, &r->fb_final, &r->rbid,
+                            &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre, &r->act_wpre,
+                            &r->ivis, &r->iact, &r->nbrays, &r->obrays, &r->cache, &r->blk_slot,
+                            &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
+                            &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
+                            &r->scan_ticket[1], &r->scan_ticket[2], &r->ctr, &r->occ_fine, &r->occ_super,
+                            &r->ps, &r->camd, &r->lbits};
+    size_t n = 0;
+    for (const DevBuf *b : bufs) n += b->bytes;
+    *device_bytes = n;
+    return SPR_OK;
+}
+
+extern "C" int spr_renderer_memory_estimate(const spr_volume *vol, int width, int height, int n_views,
+                                            size_t cache_bytes, int spec_mode, int k, size_t *device_bytes)
+{
+    clear_error();
+    if (!vol || !device_bytes || width < 1 || height < 1 || n_views < 1 || n_views > kMaxViews || k < 1)
+        return set_error(SPR_ERR_INVALID_ARG, "bad estimate arguments");
+    const VolGeom &g = vol->g;
+    const int64_t np = (int64_t)width * height * n_views;
+    const int64_t nwords = (g.nblocks + 31) / 32;
+    const int64_t slots = (int64_t)(cache_bytes / 256);
+    const int64_t cap = std::max<int64_t>(1, np * (spec_mode == SPR_SPEC_FIXED ? k : 1));
+    const int64_t act = std::min<int64_t>(g.nblocks, 8 * cap);
+    int64_t ns = 1;
+    for (int a = 0; a < 3; ++a) ns *= (g.nc[a] + 3) / 4;
+    const int64_t scan_items = std::max({tiled_ray_count(width, height) * n_views, slots, nwords, cap, act,
+                                         (int64_t)1});
+    int64_t n = 16 * nwords + 4 * g.nblocks                        // block bitmaps, block -> slot
+                + 57 * np + 4 * (tiled_ray_count(width, height) * n_views / 32 + 1)   // per ray, bitmap
+                + 8 * (g.ncoarse + ns) * n_views                   // brick masks
+                + 269 * slots                                       // cache slots and their tables
+                + 24 * cap + 8 + 12 * act                           // entries, requests
+                + 3 * 8 * (scan_tiles(scan_items) + 1) + 3 * 64     // look-back scratch
+                + (int64_t)(sizeof(uint32_t) * C_COUNT + sizeof(PassState) + sizeof(DevParams) + 16);
+    *device_bytes = (size_t)n;
     return SPR_OK;
 }
 

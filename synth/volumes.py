@@ -117,6 +117,34 @@ def uniform_hash01(seed: int, n: int, start: int = 0) -> np.ndarray:
     return h.astype(np.float64) / 4294967296.0
 
 
+def _mul32_t(h, c: int):
+    """(h * c) mod 2^32 for int64 tensors h < 2^32, in 16-bit halves so that
+    no product leaves the int64 range."""
+    lo, hi = h & 0xFFFF, h >> 16
+    return ((lo * c) + (((hi * c) & 0xFFFF) << 16)) & 0xFFFFFFFF
+
+
+def fmix32_t(h):
+    """fmix32 on an int64 torch tensor of 32-bit values (same results)."""
+    h = h & 0xFFFFFFFF
+    h = h ^ (h >> 16)
+    h = _mul32_t(h, 0x85EBCA6B)
+    h = h ^ (h >> 13)
+    h = _mul32_t(h, 0xC2B2AE35)
+    return h ^ (h >> 16)
+
+
+def uniform_hash01_t(seed: int, n: int, start: int, device):
+    """uniform_hash01 computed with torch on `device` (float32 results equal
+    the numpy version's after .astype(np.float32))."""
+    torch = _torch()
+    idx = torch.arange(start, start + n, dtype=torch.int64, device=device)
+    s0 = int(fmix32(np.uint64(seed) ^ np.uint64(0x51ED27)))
+    h = fmix32_t((idx & 0xFFFFFFFF) ^ s0)
+    h = fmix32_t(h ^ (idx >> 32))
+    return (h.to(torch.float64) / 4294967296.0).to(torch.float32)
+
+
 def gaussian_blobs(dims=(512, 512, 512), seed: int = 2, n: int = 200, noise: float = 0.1,
                    device=None, return_u8: bool = True):
     """Medium workload: sum of `n` axis-aligned anisotropic Gaussians (centre
@@ -143,9 +171,16 @@ def gaussian_blobs(dims=(512, 512, 512), seed: int = 2, n: int = 200, noise: flo
             g[2].view(-1, 1, 1) * g[1].view(1, -1, 1) * g[0].view(1, 1, -1))
     # per-voxel noise, generated slab by slab from a counter-based hash
     plane = Dx * Dy
-    for z in range(Dz):
-        u = uniform_hash01(seed, plane, start=z * plane).astype(np.float32)
-        vol[z] += noise * torch.from_numpy(u).to(dev).view(Dy, Dx)
+    if dev.type == "cuda":
+        step = max(1, (1 << 24) // plane)
+        for z in range(0, Dz, step):
+            z1 = min(Dz, z + step)
+            u = uniform_hash01_t(seed, plane * (z1 - z), z * plane, dev)
+            vol[z:z1] += noise * u.view(z1 - z, Dy, Dx)
+    else:
+        for z in range(Dz):
+            u = uniform_hash01(seed, plane, start=z * plane).astype(np.float32)
+            vol[z] += noise * torch.from_numpy(u).to(dev).view(Dy, Dx)
     vol /= vol.max()
     u8 = torch.round(vol * 255.0).clamp_(0, 255).to(torch.uint8)
     if not return_u8:

@@ -124,3 +124,37 @@ def test_autotune_picks_a_candidate_and_keeps_the_image(spr, orc):
     v.close()
     for key in FB_KEYS:
         assert np.array_equal(got[key], want[0][key]), key
+
+
+def test_view_count_within_capacity(spr, orc):
+    """A renderer sized for 4 views renders 2, then 3, then 4 views without
+    reallocating: views past the active count generate no rays, and every
+    active view equals its single-view render."""
+    import torch
+    scenes = views_of(orc, (36, 32, 28), 9, 4, 48, 40, (0.45, 0.6))
+    sc0 = scenes[0]
+    v = spr.spr_create_volume(sc0.dims, sc0.rate, torch.from_numpy(sc0.comp).cuda())
+    r = spr.spr_create_renderer(v, sc0.W, sc0.H)
+    spr.spr_set_cache_budget(r, 256 * sc0.ovol.fine.shape[0])
+    singles = [render_batch(spr, [sc])[0][0] for sc in scenes]
+    spr.spr_set_view_count(r, 4)
+    mem = None
+    n = sc0.W * sc0.H
+    for nv, order in ((4, (0, 1, 2, 3)), (2, (3, 1)), (3, (2, 0, 1)), (1, (1,))):
+        spr.spr_set_view_count(r, nv)
+        for i, s in enumerate(order):
+            spr.spr_set_view(r, i, scenes[s].cam, scenes[s].iso)
+        rs, _ = spr.spr_render_to_convergence(r, 100000)
+        assert rs["n_rays"] == sum(int((singles[s]["status"] != 2).sum()) +
+                                   int(((singles[s]["status"] == 2) & (singles[s]["final_pass"] > 0)).sum())
+                                   for s in order)
+        fb = spr.spr_read_framebuffer(r)
+        assert fb["depth"].size == nv * n
+        for i, s in enumerate(order):
+            for key in FB_KEYS:
+                assert np.array_equal(fb[key][i * n:(i + 1) * n], singles[s][key]), (nv, i, key)
+        # entry buffers and scan scratch are sized at the first render
+        mem = mem or spr.spr_renderer_memory(r)
+        assert spr.spr_renderer_memory(r) == mem
+    r.close()
+    v.close()
