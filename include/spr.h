@@ -153,7 +153,14 @@ int spr_count_active_blocks(const spr_volume *vol, float iso, int64_t *n_active,
 /* --------------------------------------------------------------- renderer */
 #define SPR_SPEC_FIXED    0   /* k = the given count every pass                */
 #define SPR_SPEC_ADAPTIVE 1   /* k = min(k_max, floor(w*h / N_Act)) (Sec. 4)   */
+/* Per-ray speculation: every live ray takes its own count k_i in [1, k_max]
+ * each pass (the paper's future work, Sec. 6: a per-ray speculation count).
+ * The image does not depend on the counts; only the passes and the blocks
+ * decoded do. */
+#define SPR_SPEC_HASHED   2   /* k_i = 1 + hash(ray, pass) mod k_max: a model-free per-ray count */
+#define SPR_SPEC_LEARNED  3   /* k_i from the renderer's policy MLP (spr_set_policy)              */
 #define SPR_K_LIMIT       4096
+#define SPR_K_PER_RAY_LIMIT 64
 
 typedef struct {
     int32_t pass;           /* 1-based pass index since the last reset          */
@@ -239,8 +246,12 @@ int spr_set_view(spr_renderer *r, int view, const float eye[3], const float p00[
 /* cache budget in bytes; slots = bytes / 256, at least 8, else
  * SPR_ERR_CACHE_TOO_SMALL.  Empties the cache and restarts the render. */
 int spr_set_cache_budget(spr_renderer *r, size_t bytes);
-/* mode SPR_SPEC_FIXED with 1 <= k <= SPR_K_LIMIT, or SPR_SPEC_ADAPTIVE with
- * 1 <= k_max <= SPR_K_LIMIT (k ignored).  Restarts the render. */
+/* mode SPR_SPEC_FIXED with 1 <= k <= SPR_K_LIMIT, SPR_SPEC_ADAPTIVE with
+ * 1 <= k_max <= SPR_K_LIMIT (k ignored), or a per-ray mode with 1 <= k_max
+ * <= SPR_K_PER_RAY_LIMIT (SPR_SPEC_LEARNED needs a policy set first).  In a
+ * per-ray mode a pass that overflows the cache is redone with every count
+ * capped at half the previous cap, then (at 1) with half the rays.
+ * Restarts the render. */
 int spr_set_speculation(spr_renderer *r, int mode, int k, int k_max);
 /* Traversal tuning (no counterpart in the paper, results unchanged): passes
  * with fewer than n_rays live rays walk one ray per warp, larger passes one
@@ -392,6 +403,71 @@ int spr_server_submit(spr_server *s, const spr_request *req, int64_t *id);
  * budget completes with SPR_ERR_OUT_OF_MEMORY. */
 int spr_server_poll(spr_server *s, spr_result *out, int max_out, int *n_out);
 int spr_server_info(const spr_server *s, spr_server_stats *out);
+
+/* ---------------------------------------------------- learned speculation */
+/*
+ * The paper's future work (Sec. 6) suggests choosing the speculation count
+ * per ray.  SPR_SPEC_LEARNED takes it from a small perceptron: 12 features
+ * of each live ray at the start of a pass (pass index / 8; the current
+ * block's position in the block grid, 3; the unit ray direction, 3; the
+ * distance from the eye to the current block's centre over the volume
+ * diagonal; the occupied fraction of its coarse cell's blocks and of its
+ * super cell's coarse cells; the isovalue; the fraction of rays still live)
+ * -> 64 -> 64 (ReLU) -> 2 outputs: y0 = the predicted log2 of the visible
+ * blocks the ray still needs (up to and including its hit block), y1 = an
+ * upper quantile of it.  The ray's count is k = ceil(2^(y0 + margin))
+ * clamped to [1, min(k_max, the attempt's cap)].  Inference runs on the
+ * tensor cores (tcgen05.mma, bf16 weights and activations, fp32
+ * accumulation, 128 rays per tile).  The image does not depend on the
+ * policy.
+ *
+ * Parameters: SPR_POLICY_PARAMS floats, row-major PyTorch Linear layout:
+ * W1[64][12], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].
+ */
+#define SPR_POLICY_FEATURES 12
+#define SPR_POLICY_PARAMS 5122
+
+/* host parameters (copied) and margin; synchronises the device */
+int spr_set_policy(spr_renderer *r, const float *params, float margin);
+
+/* Training traces.  While set, every pass records, for the live rays whose
+ * id hashes to 0 mod sample_mod, a sample: features[12] (fp32, as the policy
+ * sees them), the ray id and the visible blocks the ray took in earlier
+ * passes, appended to the caller's device buffers (capacity samples; later
+ * ones are dropped).  features = NULL turns tracing off.  Restarts the
+ * render. */
+int spr_set_trace(spr_renderer *r, float *features, uint32_t *rays, uint32_t *consumed,
+                  int64_t capacity, uint32_t sample_mod);
+/* After a converged render: label the samples recorded since the previous
+ * call (or spr_set_trace) -- the visible blocks the ray still needed at the
+ * sample, at least 1 -- into labels[i] (device, same indexing as the
+ * samples); *n_samples = samples recorded so far.  Synchronises `stream`. */
+int spr_trace_labels(spr_renderer *r, uint32_t *labels, int64_t *n_samples, spr_stream stream);
+
+/* The policy on n feature rows (device, n x 12 fp32) -> out (device, n x 2
+ * fp32), by the renderer's tensor-core kernel.  Synchronises `stream`. */
+int spr_policy_forward(const float *params, const float *features, int64_t n, float *out,
+                       spr_stream stream);
+/* Mean loss over n samples (device features and labels) and its gradient
+ * (host, SPR_POLICY_PARAMS floats), fp32: the loss is (y0 - t)^2 +
+ * pinball_tau(t - y1) with t = log2(min(label, 64)); loss[0], loss[1] (host,
+ * may be NULL) receive its two terms.  Synchronises `stream`. */
+int spr_policy_grad(const float *params, const float *features, const uint32_t *labels, int64_t n,
+                    float tau, float *grad, double *loss, spr_stream stream);
+
+typedef struct {
+    int32_t  epochs;
+    int32_t  batch;         /* samples per Adam step                          */
+    float    lr, beta1, beta2, eps;
+    float    tau;           /* quantile of the second output, in (0, 1)       */
+    uint32_t seed;          /* sample order                                   */
+} spr_train_desc;
+
+/* Train params (host, in/out) on n samples with Adam over the loss of
+ * spr_policy_grad; loss_per_epoch (host, may be NULL) receives the mean
+ * first term per epoch.  Synchronises `stream`. */
+int spr_policy_train(const float *features, const uint32_t *labels, int64_t n, float *params,
+                     const spr_train_desc *d, float *loss_per_epoch, spr_stream stream);
 
 /* --------------------------------------------------------------- scan */
 /* Exclusive prefix sum of n uint32 values (device in/out; in == out allowed),

@@ -25,7 +25,10 @@ SPR_ERR_NO_DEVICE = -8
 SPR_ERR_DEVICE_ERROR = -9
 SPR_SPEC_FIXED = 0
 SPR_SPEC_ADAPTIVE = 1
+SPR_SPEC_HASHED = 2
+SPR_SPEC_LEARNED = 3
 SPR_K_LIMIT = 4096
+SPR_K_PER_RAY_LIMIT = 64
 SPR_CODEC_FRC4 = 1
 
 
@@ -112,6 +115,16 @@ class ServerStats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+SPR_POLICY_FEATURES = 12
+SPR_POLICY_PARAMS = 5122
+
+
+class TrainDesc(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("tau", ctypes.c_float), ("seed", ctypes.c_uint32)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                            ctypes.c_void_p)
@@ -160,6 +173,12 @@ PROTOTYPES = {
     "spr_server_submit": ([_vp, _vp, _vp], _i32),
     "spr_server_poll": ([_vp, _vp, _i32, _vp], _i32),
     "spr_server_info": ([_vp, _vp], _i32),
+    "spr_set_policy": ([_vp, _vp, ctypes.c_float], _i32),
+    "spr_set_trace": ([_vp, _vp, _vp, _vp, _i64, ctypes.c_uint32], _i32),
+    "spr_trace_labels": ([_vp, _vp, _vp, _vp], _i32),
+    "spr_policy_forward": ([_vp, _vp, _i64, _vp, _vp], _i32),
+    "spr_policy_grad": ([_vp, _vp, _vp, _i64, ctypes.c_float, _vp, _vp, _vp], _i32),
+    "spr_policy_train": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], _i32),
 }
 
 _lock = threading.Lock()

@@ -10,8 +10,8 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (SPR_CODEC_FRC4, SPR_K_LIMIT, SPR_SPEC_ADAPTIVE, SPR_SPEC_FIXED,  # noqa: F401
-                   SprError, check, load)
+from ._lib import (SPR_CODEC_FRC4, SPR_K_LIMIT, SPR_K_PER_RAY_LIMIT, SPR_SPEC_ADAPTIVE,  # noqa: F401
+                   SPR_SPEC_FIXED, SPR_SPEC_HASHED, SPR_SPEC_LEARNED, SprError, check, load)
 
 
 def _torch():
@@ -351,6 +351,90 @@ def spr_renderer_memory_estimate(vol: Volume, W: int, H: int, n_views: int, cach
     check(load().spr_renderer_memory_estimate(vol.handle, int(W), int(H), int(n_views),
                                               int(cache_bytes), int(mode), int(k), ctypes.byref(n)))
     return n.value
+
+
+# ---------------------------------------------------- learned speculation
+SPR_POLICY_FEATURES = _lib.SPR_POLICY_FEATURES
+SPR_POLICY_PARAMS = _lib.SPR_POLICY_PARAMS
+
+
+def _params(params):
+    p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+    assert p.size == SPR_POLICY_PARAMS, "expected %d parameters" % SPR_POLICY_PARAMS
+    return p
+
+
+def spr_set_policy(r: Renderer, params, margin: float = 0.0):
+    """params: SPR_POLICY_PARAMS floats (W1[64][12], b1, W2[64][64], b2,
+    W3[2][64], b3)."""
+    p = _params(params)
+    check(load().spr_set_policy(r.handle, p.ctypes.data_as(ctypes.c_void_p), float(margin)))
+
+
+class Trace:
+    """Device buffers of a training trace (features, ray ids, blocks taken
+    before the sample, labels)."""
+
+    def __init__(self, capacity: int):
+        torch = _torch()
+        self.capacity = int(capacity)
+        self.features = torch.zeros((capacity, SPR_POLICY_FEATURES), dtype=torch.float32, device="cuda")
+        self.rays = torch.zeros(capacity, dtype=torch.int32, device="cuda")
+        self.consumed = torch.zeros(capacity, dtype=torch.int32, device="cuda")
+        self.labels = torch.zeros(capacity, dtype=torch.int32, device="cuda")
+        self.n = 0
+
+
+def spr_set_trace(r: Renderer, trace: "Trace | None", sample_mod: int = 1):
+    L = load()
+    if trace is None:
+        check(L.spr_set_trace(r.handle, None, None, None, 0, 1))
+        return
+    check(L.spr_set_trace(r.handle, _dev_ptr(trace.features), _dev_ptr(trace.rays),
+                          _dev_ptr(trace.consumed), trace.capacity, int(sample_mod)))
+
+
+def spr_trace_labels(r: Renderer, trace: Trace, stream=None) -> int:
+    n = ctypes.c_int64()
+    check(load().spr_trace_labels(r.handle, _dev_ptr(trace.labels), ctypes.byref(n), _stream(stream)))
+    trace.n = n.value
+    return n.value
+
+
+def spr_policy_forward(params, features, stream=None):
+    """features: CUDA float32 (n, 12); returns CUDA float32 (n, 2)."""
+    torch = _torch()
+    p = _params(params)
+    n = features.shape[0]
+    out = torch.empty((n, 2), dtype=torch.float32, device=features.device)
+    check(load().spr_policy_forward(p.ctypes.data_as(ctypes.c_void_p), _dev_ptr(features, torch.float32), n,
+                                    _dev_ptr(out), _stream(stream)))
+    return out
+
+
+def spr_policy_grad(params, features, labels, tau: float = 0.9, stream=None):
+    """(gradient as float32 numpy, (loss0, loss1)) of the mean loss."""
+    torch = _torch()
+    p = _params(params)
+    g = np.zeros(SPR_POLICY_PARAMS, np.float32)
+    loss = (ctypes.c_double * 2)()
+    check(load().spr_policy_grad(p.ctypes.data_as(ctypes.c_void_p), _dev_ptr(features, torch.float32),
+                                 _dev_ptr(labels), features.shape[0], float(tau),
+                                 g.ctypes.data_as(ctypes.c_void_p), loss, _stream(stream)))
+    return g, (loss[0], loss[1])
+
+
+def spr_policy_train(features, labels, params, epochs: int = 5, batch: int = 8192, lr: float = 2e-3,
+                     tau: float = 0.9, seed: int = 1, stream=None):
+    """Adam on the policy loss; returns (trained params, mean loss per epoch)."""
+    torch = _torch()
+    p = _params(params).copy()
+    d = _lib.TrainDesc(int(epochs), int(batch), float(lr), 0.9, 0.999, 1e-8, float(tau), int(seed))
+    losses = np.zeros(epochs, np.float32)
+    check(load().spr_policy_train(_dev_ptr(features, torch.float32), _dev_ptr(labels), features.shape[0],
+                                  p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(d),
+                                  losses.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return p, losses
 
 
 # ---------------------------------------------------------------- serving

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libspr.so")
-SOURCES = ["api.cu", "codec.cu", "render.cu", "scan_noalloc.cu", "serve.cu"]
+SOURCES = ["api.cu", "codec.cu", "render.cu", "scan_noalloc.cu", "serve.cu", "policy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "-I" + os.path.join(ROOT, "include")]

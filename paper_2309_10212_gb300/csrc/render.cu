@@ -29,6 +29,7 @@
 
 #include "kernels.cuh"
 #include "scan.cuh"
+#include "mlp.cuh"
 #include "spr_common.cuh"
 
 namespace spr {
@@ -56,8 +57,32 @@ enum Ctr {
     C_MAXSTEPS,  // longest walk this pass
     C_NEEDUSED,  // victims taken from the used-slot list (the rest are fresh slots)
     C_QISECT,    // work queue of the intersection: entries handed out
+    C_KTOT,      // per-ray speculation: entries of the attempt (sum of the rays' k)
     C_COUNT = 20
 };
+
+// Per-ray speculation (modes SPR_SPEC_HASHED and SPR_SPEC_LEARNED): live
+// position i takes kray[i] entries starting at koff[i] (an exclusive scan of
+// kray), and every entry written records its position in eray.  With koff
+// null every ray takes PassState::kk entries at i * kk.
+struct Spec {
+    const uint32_t *kray, *koff;
+    uint32_t *eray;
+};
+
+// Training traces of the plain raycaster (spr_set_trace).  Per pass, live
+// rays with hash(ray) mod `mod` == 0 append (features, ray, blocks taken so
+// far); resolve keeps, per ray, the visible blocks taken (`taken`) and, when
+// the ray finishes, how many it needed in all (`need`: up to and including
+// the hit block, or every visible block of a miss).
+struct Trace {
+    float *feat;        // [cap][12]
+    uint32_t *ray, *cons;
+    uint32_t *count;    // samples appended (may pass cap; only cap are kept)
+    uint32_t cap, mod;
+    uint32_t *taken, *need;   // per ray
+};
+
 
 // The pass loop's state lives on the device, so that a pass (and a whole
 // render, as one graph launch) needs no host round trip: begin_pass_kernel
@@ -537,7 +562,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
                                                        uint64_t *__restrict__ state_out,
                                                        uint32_t *__restrict__ rbid,
                                                        uint32_t *vis_bits, uint32_t *act_bits,
-                                                       uint32_t *ctr)
+                                                       uint32_t *ctr, Spec S)
 {
     const VolGeom &g = P.g;
     const uint32_t nproc = ps->nproc;
@@ -565,7 +590,9 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
         w.b[1] = (int)((st >> 16) & 0xFFFF);
         w.b[2] = (int)((st >> 32) & 0xFFFF);
         uint64_t flags = st >> 48;
-        uint32_t *out = rbid + (uint64_t)i * kk;
+        const uint64_t off = S.koff ? S.koff[i] : (uint64_t)i * kk;
+        const int ki = S.koff ? (int)S.kray[i] : kk;
+        uint32_t *out = rbid + off;
         int cnt = 0;
         bool alive = !(flags & kDone);
         if (alive) {
@@ -599,6 +626,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
             }
             if ((fmask >> ((b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) & 1ull) {
                 uint32_t blin = (uint32_t)b[0] + nb0 * ((uint32_t)b[1] + nb1 * (uint32_t)b[2]);
+                if (S.eray) S.eray[off + cnt] = (uint32_t)i;
                 out[cnt++] = blin;
                 set_bit(vis_bits, blin);
 #pragma unroll
@@ -607,7 +635,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
                     if (x < g.nb[0] && y < g.nb[1] && z < g.nb[2])
                         set_bit(act_bits, (uint32_t)x + nb0 * ((uint32_t)y + nb1 * (uint32_t)z));
                 }
-                if (cnt == kk) {
+                if (cnt == ki) {
                     flags |= kStep;
                     break;
                 }
@@ -615,7 +643,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
             alive = walk_step(w, g);
         }
         if (!alive) flags |= kDone;
-        for (int j = cnt; j < kk; ++j) out[j] = kNone;
+        for (int j = cnt; j < ki; ++j) out[j] = kNone;
         state_out[ray] = pack_state(w.b, flags);
         warp_add(&ctr[C_STEPS], (uint32_t)steps);
         {
@@ -646,7 +674,7 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
                                                             uint64_t *__restrict__ state_out,
                                                             uint32_t *__restrict__ rbid,
                                                             uint32_t *vis_bits, uint32_t *act_bits,
-                                                            uint32_t *ctr)
+                                                            uint32_t *ctr, Spec S)
 {
     const VolGeom &g = P.g;
     const uint32_t nproc = ps->nproc;
@@ -678,7 +706,9 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
         w.b[1] = (int)((st >> 16) & 0xFFFF);
         w.b[2] = (int)((st >> 32) & 0xFFFF);
         uint64_t flags = st >> 48;
-        uint32_t *out = rbid + (uint64_t)i * kk;
+        const uint64_t off = S.koff ? S.koff[i] : (uint64_t)i * kk;
+        const int ki = S.koff ? (int)S.kray[i] : kk;
+        uint32_t *out = rbid + off;
         int cnt = 0;
         bool alive = !(flags & kDone);
         if (alive) {
@@ -791,11 +821,12 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
                 vis = (fmask >> ((bb[0] & 3) + 4 * (bb[1] & 3) + 16 * (bb[2] & 3))) & 1ull;
             }
             const unsigned vmask = __reduce_or_sync(full, vis ? (1u << pos) : 0u);
-            const int need = kk - cnt;
+            const int need = ki - cnt;
             const int take = min(need, __popc(vmask));
             const int idx = vis ? __popc(vmask & ((1u << pos) - 1u)) : 32;
             if (idx < take) {
                 const uint32_t blin = (uint32_t)bb[0] + nb0 * ((uint32_t)bb[1] + nb1 * (uint32_t)bb[2]);
+                if (S.eray) S.eray[off + cnt + idx] = (uint32_t)i;
                 out[cnt + idx] = blin;
                 set_bit(vis_bits, blin);
 #pragma unroll
@@ -829,7 +860,7 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
             for (int a2 = 0; a2 < 3; ++a2) set_axis(w, g, a2);
         }
         if (!alive) flags |= kDone;
-        for (int j = cnt + lane; j < kk; j += 32) out[j] = kNone;
+        for (int j = cnt + lane; j < ki; j += 32) out[j] = kNone;
         if (lane == 0) {
             state_out[ray] = pack_state(w.b, flags);
             tot_steps += (uint32_t)steps;
@@ -878,10 +909,10 @@ __device__ __forceinline__ uint32_t vis_rank(const uint32_t *bits, const uint32_
 
 __global__ void count_entries_kernel(const PassState *ps, const uint32_t *__restrict__ rbid, const uint32_t *vis_bits,
                                      const uint32_t *vis_wpre, uint32_t *nbrays, uint32_t *erank,
-                                     const uint32_t *ctr)
+                                     const uint32_t *ctr, Spec S)
 {
     if (ctr[C_OVERFLOW]) return;
-    const int64_t n = (int64_t)ps->nproc * ps->kk;
+    const int64_t n = S.koff ? (int64_t)ctr[C_KTOT] : (int64_t)ps->nproc * ps->kk;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         uint32_t b = rbid[e];
         if (b == kNone) continue;
@@ -903,10 +934,10 @@ struct ArrayEmit {
 
 __global__ void scatter_entries_kernel(const PassState *ps, const uint32_t *__restrict__ rbid, const uint32_t *vis_bits,
                                        const uint32_t *vis_wpre, const uint32_t *obrays,
-                                       const uint32_t *erank, uint32_t *E, const uint32_t *ctr)
+                                       const uint32_t *erank, uint32_t *E, const uint32_t *ctr, Spec S)
 {
     if (ctr[C_OVERFLOW]) return;
-    const int64_t n = (int64_t)ps->nproc * ps->kk;
+    const int64_t n = S.koff ? (int64_t)ctr[C_KTOT] : (int64_t)ps->nproc * ps->kk;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         uint32_t b = rbid[e];
         if (b == kNone) continue;
@@ -1395,7 +1426,7 @@ __global__ void __launch_bounds__(128, 4) intersect_kernel(RT R, const uint32_t 
                                                         const uint32_t *__restrict__ live0,
                                                         const uint32_t *__restrict__ live1,
                                                         const PassState *__restrict__ ps,
-                                                        unsigned long long *keys, uint32_t *ctr)
+                                                        unsigned long long *keys, uint32_t *ctr, Spec S)
 {
     if (ctr[C_OVERFLOW]) return;
     const uint32_t kk = ps->kk;
@@ -1409,7 +1440,14 @@ __global__ void __launch_bounds__(128, 4) intersect_kernel(RT R, const uint32_t 
         if (idx >= n) continue;
         uint32_t e = E[idx];
         uint32_t b = rbid[e];
-        uint32_t i = e / kk, j = e - i * kk;
+        uint32_t i, j;
+        if (S.koff) {
+            i = S.eray[e];
+            j = e - S.koff[i];
+        } else {
+            i = e / kk;
+            j = e - i * kk;
+        }
         uint32_t ray = live[i];
         // a hit already recorded from an earlier block of this ray (smaller
         // j) wins the atomicMin whatever this block holds
@@ -1440,7 +1478,8 @@ __global__ void __launch_bounds__(256) resolve_kernel(const uint32_t *__restrict
                                                       uint8_t *__restrict__ status, float *__restrict__ depth,
                                                       uint32_t *__restrict__ rgba, uint32_t *__restrict__ block,
                                                       uint64_t *__restrict__ cell, int32_t *__restrict__ final_pass,
-                                                      uint32_t *__restrict__ alive_bits, uint32_t *ctr)
+                                                      uint32_t *__restrict__ alive_bits, uint32_t *ctr, Spec S,
+                                                      Trace T)
 {
     if (ctr[C_OVERFLOW]) return;
     const uint32_t *live = (ps->parity & 1) ? live1 : live0;
@@ -1458,7 +1497,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(const uint32_t *__restrict
             state_in[ray] = st;
             if (key != kNoKey) {
                 uint32_t j = (uint32_t)(key >> 52);
-                uint32_t b = rbid[(uint64_t)i * kk + j];
+                uint32_t b = rbid[(S.koff ? (uint64_t)S.koff[i] : (uint64_t)i * kk) + j];
                 uint32_t lc = (uint32_t)((key >> 14) & 63u), grey = (uint32_t)((key >> 6) & 255u);
                 int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]),
                     bz = (int)(b / ((uint32_t)g.nb[0] * g.nb[1]));
@@ -1472,11 +1511,22 @@ __global__ void __launch_bounds__(256) resolve_kernel(const uint32_t *__restrict
                 keys[ray] = kNoKey;
                 alive = false;
                 ++nh;
+                if (T.taken) T.need[ray] = T.taken[ray] + j + 1u;
             } else if ((st >> 48) & kDone) {
                 final_pass[ray] = pass;
                 status[ray] = 2;
                 alive = false;
                 ++ng;
+                if (T.taken) {
+                    const uint64_t off = S.koff ? S.koff[i] : (uint64_t)i * kk;
+                    const uint32_t ki = S.koff ? S.kray[i] : kk;
+                    uint32_t c = 0;
+                    for (uint32_t q = 0; q < ki; ++q) c += rbid[off + q] != kNone;
+                    T.need[ray] = T.taken[ray] + c;
+                }
+            } else if (T.taken) {
+                // live on: it took exactly its count of visible blocks
+                T.taken[ray] += S.koff ? S.kray[i] : kk;
             }
         }
         const unsigned bits = __ballot_sync(0xFFFFFFFFu, alive);
@@ -1502,15 +1552,178 @@ struct LiveEmit {
     }
 };
 
+// ----------------------------------------------------- per-ray speculation
+__host__ __device__ inline bool per_ray_mode(uint32_t mode)
+{
+    return mode == SPR_SPEC_HASHED || mode == SPR_SPEC_LEARNED;
+}
+
+// SPR_SPEC_HASHED: live position i takes k = 1 + h(ray, pass) mod k_max
+// (capped by the attempt's kk), a deterministic per-ray count that exercises
+// the per-ray entry layout with no model.
+__global__ void hashed_k_kernel(const uint32_t *__restrict__ live0, const uint32_t *__restrict__ live1,
+                                const PassState *__restrict__ ps, uint32_t *__restrict__ kray)
+{
+    const uint32_t nproc = ps->nproc, kk = ps->kk, kmax = ps->k_max, pass = ps->pass;
+    const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nproc; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = live[i] * 0x9E3779B1u ^ (pass + 1u) * 0x85EBCA77u;
+        h ^= h >> 15;
+        h *= 0x2C1B3C6Du;
+        h ^= h >> 12;
+        kray[i] = min(kk, 1u + h % kmax);
+    }
+}
+
+// The 12 features of a live ray for the speculation policy (all in [0, 1]
+// or [-1, 1]): pass index / 8; the current block's position in the block
+// grid (3); the unit ray direction (3); the distance from the eye to the
+// current block's centre over the volume diagonal (how far the ray has
+// come); the fraction of occupied blocks in its coarse cell and of occupied
+// coarse cells in its super cell (the occupancy ahead); the isovalue; the
+// fraction of rays still live.
+__device__ __noinline__ void ray_features(const Geo &P, const PassState *ps, uint32_t ray, uint64_t st,
+                                          float f[mlp::kIn])
+{
+    const VolGeom &g = P.g;
+    int view, px, py;
+    ray_pixel(P, ray, view, px, py);
+    const View &vw = P.views[view];
+    Ray r;
+    make_ray(r, vw.cam.eye, vw.cam.p00, vw.cam.du, vw.cam.dv, px, py);
+    const int b0 = (int)(st & 0xFFFF), b1 = (int)((st >> 16) & 0xFFFF), b2 = (int)((st >> 32) & 0xFFFF);
+    const float dn = sqrtf(r.d[0] * r.d[0] + r.d[1] * r.d[1] + r.d[2] * r.d[2]);
+    const float ex = (float)(g.dims[0] - 1), ey = (float)(g.dims[1] - 1), ez = (float)(g.dims[2] - 1);
+    const float diag = sqrtf(ex * ex + ey * ey + ez * ez);
+    const float cx = 4.f * b0 + 2.f - r.e[0], cy = 4.f * b1 + 2.f - r.e[1], cz = 4.f * b2 + 2.f - r.e[2];
+    const uint32_t c = (uint32_t)(b0 >> 2) + (uint32_t)g.nc[0] * ((uint32_t)(b1 >> 2) + (uint32_t)g.nc[1] * (uint32_t)(b2 >> 2));
+    const uint32_t sc = (uint32_t)(b0 >> 4) + (uint32_t)P.occ.ns[0] * ((uint32_t)(b1 >> 4) + (uint32_t)P.occ.ns[1] * (uint32_t)(b2 >> 4));
+    f[0] = 0.125f * (float)ps->pass;
+    f[1] = (b0 + 0.5f) / (float)g.tb[0];
+    f[2] = (b1 + 0.5f) / (float)g.tb[1];
+    f[3] = (b2 + 0.5f) / (float)g.tb[2];
+    f[4] = r.d[0] / dn;
+    f[5] = r.d[1] / dn;
+    f[6] = r.d[2] / dn;
+    f[7] = sqrtf(cx * cx + cy * cy + cz * cz) / diag;
+    f[8] = (float)__popcll(P.occ.fmask[view * P.fstride + c]) * (1.f / 64.f);
+    f[9] = (float)__popcll(P.occ.smask[view * P.sstride + sc]) * (1.f / 64.f);
+    f[10] = vw.iso;
+    f[11] = (float)ps->n_live / (float)max(ps->npix, 1u);
+}
+
+// Speculation count from the policy's first output, the predicted log2 of
+// the visible blocks the ray still needs: k = ceil(2^(y + margin)), clamped
+// to [1, cap].
+__device__ __forceinline__ uint32_t policy_k(float y, float margin, uint32_t cap)
+{
+    const float z = fminf(fmaxf(y + margin, -1.f), 12.f);
+    return min(cap, max(1u, (uint32_t)ceilf(exp2f(z))));
+}
+
+// SPR_SPEC_LEARNED: features of 128 live rays per tile, the policy MLP on
+// the tensor cores (mlp.cuh), each ray's count.  params holds the fp32
+// parameter vector followed by the margin.  Persistent CTAs over the tiles.
+__global__ void __launch_bounds__(128) policy_kernel(Geo P, const uint32_t *__restrict__ live0,
+                                                     const uint32_t *__restrict__ live1,
+                                                     const PassState *__restrict__ ps,
+                                                     const uint64_t *__restrict__ state_in,
+                                                     const float *__restrict__ params, uint32_t *__restrict__ kray,
+                                                     uint32_t *ctr)
+{
+    __shared__ mlp::Smem S;
+    const uint32_t nproc = ps->nproc;
+    const int64_t ntiles = ((int64_t)nproc + mlp::kRows - 1) / mlp::kRows;
+    if ((int64_t)blockIdx.x >= ntiles) return;   // uniform per CTA: no TMEM taken
+    mlp::tile_setup(S, params);
+    const float margin = params[mlp::kParams];
+    const uint32_t cap = min(ps->kk, ps->k_max);
+    const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
+    uint32_t phase = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t i = tile * mlp::kRows + threadIdx.x;
+        float f[mlp::kIn];
+        if (i < nproc) {
+            const uint32_t ray = live[i];
+            ray_features(P, ps, ray, state_in[ray], f);
+        } else {
+#pragma unroll
+            for (int q = 0; q < mlp::kIn; ++q) f[q] = 0.f;
+        }
+        mlp::store_features(S, f);
+        float y[mlp::kOut];
+        if (!mlp::forward_tile(S, phase, y)) {
+            if (threadIdx.x == 0) atomicOr(&ctr[C_BAD], 8u);
+            // every ray of the remaining tiles still gets a count
+            for (int64_t t2 = tile; t2 < ntiles; t2 += gridDim.x) {
+                const int64_t i2 = t2 * mlp::kRows + threadIdx.x;
+                if (i2 < nproc) kray[i2] = 1u;
+            }
+            break;
+        }
+        if (i < nproc) kray[i] = policy_k(y[0], margin, cap);
+    }
+    mlp::tile_teardown(S);
+}
+
+__device__ __forceinline__ bool trace_pick(uint32_t ray, uint32_t mod)
+{
+    uint32_t h = ray * 0x9E3779B1u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    return mod <= 1 || h % mod == 0;
+}
+
+__global__ void __launch_bounds__(128) trace_kernel(Geo P, const uint32_t *__restrict__ live0,
+                                                    const uint32_t *__restrict__ live1,
+                                                    const PassState *__restrict__ ps,
+                                                    const uint64_t *__restrict__ state_in, Trace T)
+{
+    if (ps->retries != 0) return;   // one sample per ray and pass (the first attempt)
+    const uint32_t n = ps->n_live;
+    const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
+    const bool first = ps->pass == 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t ray = live[i];
+        if (first) {
+            T.taken[ray] = 0u;
+            T.need[ray] = 0u;
+        }
+        if (!trace_pick(ray, T.mod)) continue;
+        const uint32_t slot = atomicAdd(T.count, 1u);
+        if (slot >= T.cap) continue;
+        float f[mlp::kIn];
+        ray_features(P, ps, ray, state_in[ray], f);
+#pragma unroll
+        for (int q = 0; q < mlp::kIn; ++q) T.feat[(uint64_t)slot * mlp::kIn + q] = f[q];
+        T.ray[slot] = ray;
+        T.cons[slot] = first ? 0u : T.taken[ray];
+    }
+}
+
+// labels of samples [from, min(count, cap)): the visible blocks the ray
+// still needed at the sample = need - taken then, at least 1
+__global__ void trace_label_kernel(Trace T, uint32_t from, uint32_t *__restrict__ labels)
+{
+    const uint32_t n = min(*T.count, T.cap);
+    for (int64_t s = (int64_t)from + blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t need = T.need[T.ray[s]], c = T.cons[s];
+        labels[s] = need > c ? need - c : 1u;
+    }
+}
+
 // ------------------------------------------------------------ pass control
 __global__ void begin_pass_kernel(PassState *ps, uint32_t *ctr)
 {
     if (threadIdx.x < C_COUNT) ctr[threadIdx.x] = 0u;
     if (threadIdx.x == 0 && !ps->open) {
         uint32_t n = ps->n_live;
+        // per-ray modes: kk caps every ray's own count (halved on overflow)
         uint32_t k = ps->spec_mode == SPR_SPEC_FIXED
                          ? ps->k_fixed
-                         : max(1u, min(ps->k_max, ps->npix / max(n, 1u)));
+                         : (ps->spec_mode == SPR_SPEC_ADAPTIVE ? max(1u, min(ps->k_max, ps->npix / max(n, 1u)))
+                                                                : ps->k_max);
         ps->k = k;
         ps->kk = k;
         ps->nproc = n;
@@ -1719,6 +1932,15 @@ struct spr_renderer {
     DevBuf state_in, state_out, status, live[2], keys;
     DevBuf fb_depth, fb_rgba, fb_block, fb_cell, fb_final;
     DevBuf rbid, erank, E;
+    DevBuf kray, koff, eray;      // per-ray speculation (Spec)
+    bool policy_set = false;      // a policy MLP is loaded (SPR_SPEC_LEARNED)
+    DevBuf policy;                // fp32 parameters + margin
+    // training traces (spr_set_trace): caller buffers, per-ray bookkeeping
+    bool tracing = false;
+    float *tr_feat = nullptr;
+    uint32_t *tr_ray = nullptr, *tr_cons = nullptr;
+    uint32_t tr_cap = 0, tr_mod = 1, tr_from = 0;
+    DevBuf tr_count, tr_taken, tr_need;
     int64_t cap_entries = 0;
     DevBuf vis_bits, act_bits, vis_wpre, act_wpre, ivis, iact, nbrays, obrays;
     DevBuf lbits;   // enter bits at ray generation, alive bits at resolve (one per live position)
@@ -1789,7 +2011,8 @@ void free_all(spr_renderer *r)
                       &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
                       &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
                       &r->scan_ticket[1], &r->scan_ticket[2], &r->ctr, &r->occ_fine, &r->occ_super,
-                      &r->ps, &r->camd, &r->lbits};
+                      &r->ps, &r->camd, &r->lbits, &r->kray, &r->koff, &r->eray, &r->policy,
+                      &r->tr_count, &r->tr_taken, &r->tr_need};
     for (DevBuf *b : bufs) buf_free(*b, nullptr);
     if (r->h_ctr) cudaFreeHost(r->h_ctr);
     if (r->h_ps) cudaFreeHost(r->h_ps);
@@ -1814,7 +2037,7 @@ void free_all(spr_renderer *r)
 
 int64_t entries_needed(const spr_renderer *r)
 {
-    int64_t k = r->spec_mode == SPR_SPEC_FIXED ? r->k_fixed : 1;
+    int64_t k = r->spec_mode == SPR_SPEC_FIXED ? r->k_fixed : (per_ray_mode(r->spec_mode) ? r->k_max : 1);
     return std::max<int64_t>(1, r->npix_cap * k);
 }
 
@@ -1823,6 +2046,14 @@ int ensure_entry_buffers(spr_renderer *r, cudaStream_t s)
     int64_t cap = entries_needed(r);
     if (cap > 0x7FFFFFFFll)
         return set_error(SPR_ERR_INVALID_ARG, "width*height*k = %lld exceeds 2^31 entries", (long long)cap);
+    if (per_ray_mode(r->spec_mode) &&
+        (r->eray.bytes < sizeof(uint32_t) * (size_t)std::max(cap, r->cap_entries) ||
+         r->kray.bytes < sizeof(uint32_t) * (size_t)r->npix_cap)) {
+        drop_graph(r);
+        SPR_TRY(buf_reserve(r->eray, sizeof(uint32_t) * std::max(cap, r->cap_entries), s));
+        SPR_TRY(buf_reserve(r->kray, sizeof(uint32_t) * r->npix_cap, s));
+        SPR_TRY(buf_reserve(r->koff, sizeof(uint32_t) * r->npix_cap, s));
+    }
     if (cap <= r->cap_entries) return SPR_OK;
     drop_graph(r);
     SPR_TRY(buf_reserve(r->rbid, sizeof(uint32_t) * cap, s));
@@ -2039,6 +2270,35 @@ inline cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing)
 //
 // The bitmaps are cleared right after their last reader, ready for the next
 // attempt.
+int launch_policy(spr_renderer *r, cudaStream_t s)
+{
+    // persistent CTAs: at most two per SM (TMEM columns and shared memory
+    // leave room for other work), never more than there are tiles
+    const int64_t tiles = (r->npix_cap + mlp::kRows - 1) / mlp::kRows;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * device_sm_count()));
+    policy_kernel<<<grid, mlp::kRows, 0, s>>>(make_geo(r), r->live[0].as<uint32_t>(), r->live[1].as<uint32_t>(),
+                                              r->ps.as<PassState>(), r->state_in.as<uint64_t>(),
+                                              r->policy.as<float>(), r->kray.as<uint32_t>(), r->ctr.as<uint32_t>());
+    count_launch();
+    SPR_CUDA_TRY(cudaGetLastError());
+    return SPR_OK;
+}
+
+Trace make_trace(spr_renderer *r)
+{
+    Trace T{};
+    if (!r->tracing) return T;
+    T.feat = r->tr_feat;
+    T.ray = r->tr_ray;
+    T.cons = r->tr_cons;
+    T.count = r->tr_count.as<uint32_t>();
+    T.cap = r->tr_cap;
+    T.mod = r->tr_mod;
+    T.taken = r->tr_taken.as<uint32_t>();
+    T.need = r->tr_need.as<uint32_t>();
+    return T;
+}
+
 int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphConditionalHandle h, int use_h,
                     bool capturing = false)
 {
@@ -2058,14 +2318,37 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     begin_pass_kernel<<<1, 32, 0, s>>>(ps, ctr);
     count_launch();
 
+    // training traces: record this pass's samples before the walk moves on
+    const Trace T = make_trace(r);
+    if (T.taken) {
+        trace_kernel<<<grid_for(r->npix_cap, 128, 8), 128, 0, s>>>(make_geo(r), live0, live1, ps,
+                                                                   r->state_in.as<uint64_t>(), T);
+        count_launch();
+    }
+
+    // per-ray speculation: each live ray's count, then their offsets
+    Spec S{nullptr, nullptr, nullptr};
+    if (per_ray_mode(r->spec_mode)) {
+        S = Spec{r->kray.as<uint32_t>(), r->koff.as<uint32_t>(), r->eray.as<uint32_t>()};
+        if (r->spec_mode == SPR_SPEC_LEARNED)
+            SPR_TRY(launch_policy(r, s));
+        else {
+            hashed_k_kernel<<<grid_for(r->npix_cap, 256, 8), 256, 0, s>>>(live0, live1, ps, r->kray.as<uint32_t>());
+            count_launch();
+        }
+        SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, r->npix_cap, &ps->nproc,
+                            ArrayCount{r->kray.as<uint32_t>(), nullptr}, ArrayEmit{r->koff.as<uint32_t>()},
+                            ctr + C_KTOT, s));
+    }
+
     // (a) traversal with speculation, marking visible and active blocks
     traverse_kernel<<<grid_for(r->npix_cap, 128, 16), 128, 0, s>>>(
         make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
-        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr);
+        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
     count_launch();
     traverse_coop_kernel<<<device_sm_count() * 16, 128, 0, s>>>(
         make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
-        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr);
+        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     if (events) SPR_CUDA_TRY(record(r->ev[1], s, capturing));
@@ -2091,14 +2374,14 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     if (fork) SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_act, 0));
     count_entries_kernel<<<grid_for(cap, 256, 16), 256, 0, s>>>(
         ps, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
-        r->nbrays.as<uint32_t>(), r->erank.as<uint32_t>(), ctr);
+        r->nbrays.as<uint32_t>(), r->erank.as<uint32_t>(), ctr, S);
     count_launch();
     SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, cap, ctr + C_NVIS,
                         ArrayCount{r->nbrays.as<uint32_t>(), ctr + C_OVERFLOW},
                         ArrayEmit{r->obrays.as<uint32_t>()}, ctr + C_NENT, s));
     scatter_entries_kernel<<<grid_for(cap, 256, 16), 256, 0, s>>>(
         ps, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
-        r->obrays.as<uint32_t>(), r->erank.as<uint32_t>(), r->E.as<uint32_t>(), ctr);
+        r->obrays.as<uint32_t>(), r->erank.as<uint32_t>(), r->E.as<uint32_t>(), ctr, S);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     SPR_CUDA_TRY(cudaMemsetAsync(r->vis_bits.p, 0, sizeof(uint32_t) * r->nwords, s));
@@ -2141,7 +2424,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     // (e) intersect the entries, block by block
     RT R{make_geo(r), r->cache.as<float>(), r->blk_slot.as<uint32_t>()};
     intersect_kernel<<<r->grid_isect, 128, 0, s>>>(R, r->E.as<uint32_t>(), r->rbid.as<uint32_t>(), live0, live1, ps,
-                                                   r->keys.as<unsigned long long>(), ctr);
+                                                   r->keys.as<unsigned long long>(), ctr, S);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     if (events) SPR_CUDA_TRY(record(r->ev[5], s, capturing));
@@ -2151,7 +2434,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
         live0, live1, ps, g.dims[0], g.dims[1], g, r->keys.as<unsigned long long>(), r->rbid.as<uint32_t>(),
         r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(), r->status.as<uint8_t>(), r->fb_depth.as<float>(),
         r->fb_rgba.as<uint32_t>(), r->fb_block.as<uint32_t>(), r->fb_cell.as<uint64_t>(), r->fb_final.as<int32_t>(),
-        r->lbits.as<uint32_t>(), ctr);
+        r->lbits.as<uint32_t>(), ctr, S, T);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, r->npix_cap, &ps->n_live,
@@ -2650,9 +2933,20 @@ extern "C" int spr_set_speculation(spr_renderer *r, int mode, int k, int k_max)
         if (k_max < 1 || k_max > SPR_K_LIMIT)
             return set_error(SPR_ERR_INVALID_ARG, "k_max = %d outside [1, %d]", k_max, SPR_K_LIMIT);
         r->k_max = k_max;
+    } else if (per_ray_mode(mode)) {
+        if (k_max < 1 || k_max > SPR_K_PER_RAY_LIMIT)
+            return set_error(SPR_ERR_INVALID_ARG, "per-ray k_max = %d outside [1, %d]", k_max, SPR_K_PER_RAY_LIMIT);
+        if (r->npix_cap * (int64_t)k_max > 0x7FFFFFFFll)
+            return set_error(SPR_ERR_INVALID_ARG, "width*height*k_max exceeds 2^31 entries");
+        if (mode == SPR_SPEC_LEARNED && !r->policy_set)
+            return set_error(SPR_ERR_INVALID_ARG, "learned speculation needs a policy (spr_set_policy)");
+        r->k_max = k_max;
     } else {
         return set_error(SPR_ERR_INVALID_ARG, "unknown speculation mode %d", mode);
     }
+    // the captured pass graph holds the speculation layout and policy kernels
+    if (per_ray_mode(mode) != per_ray_mode(r->spec_mode) || (mode != r->spec_mode && per_ray_mode(mode)))
+        drop_graph(r);
     r->spec_mode = mode;
     r->need_raygen = true;
     r->params_dirty = true;
@@ -2879,7 +3173,8 @@ extern "C" int spr_renderer_memory(const spr_renderer *r, size_t *device_bytes)
                             &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
                             &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
                             &r->scan_ticket[1], &r->scan_ticket[2], &r->ctr, &r->occ_fine, &r->occ_super,
-                            &r->ps, &r->camd, &r->lbits};
+                            &r->ps, &r->camd, &r->lbits, &r->kray, &r->koff, &r->eray, &r->policy,
+                            &r->tr_count, &r->tr_taken, &r->tr_need};
     size_t n = 0;
     for (const DevBuf *b : bufs) n += b->bytes;
     *device_bytes = n;
@@ -2896,7 +3191,7 @@ extern "C" int spr_renderer_memory_estimate(const spr_volume *vol, int width, in
     const int64_t np = (int64_t)width * height * n_views;
     const int64_t nwords = (g.nblocks + 31) / 32;
     const int64_t slots = (int64_t)(cache_bytes / 256);
-    const int64_t cap = std::max<int64_t>(1, np * (spec_mode == SPR_SPEC_FIXED ? k : 1));
+    const int64_t cap = std::max<int64_t>(1, np * (spec_mode == SPR_SPEC_FIXED || per_ray_mode(spec_mode) ? k : 1));
     const int64_t act = std::min<int64_t>(g.nblocks, 8 * cap);
     int64_t ns = 1;
     for (int a = 0; a < 3; ++a) ns *= (g.nc[a] + 3) / 4;
@@ -2907,9 +3202,76 @@ extern "C" int spr_renderer_memory_estimate(const spr_volume *vol, int width, in
                 + 8 * (g.ncoarse + ns) * n_views                   // brick masks
                 + 269 * slots                                       // cache slots and their tables
                 + 24 * cap + 8 + 12 * act                           // entries, requests
+                + (per_ray_mode(spec_mode) ? 4 * cap + 8 * np : 0)  // per-ray counts, offsets, entry rays
                 + 3 * 8 * (scan_tiles(scan_items) + 1) + 3 * 64     // look-back scratch
                 + (int64_t)(sizeof(uint32_t) * C_COUNT + sizeof(PassState) + sizeof(DevParams) + 16);
     *device_bytes = (size_t)n;
+    return SPR_OK;
+}
+
+extern "C" int spr_set_policy(spr_renderer *r, const float *params, float margin)
+{
+    clear_error();
+    if (!r || !params) return set_error(SPR_ERR_INVALID_ARG, "NULL argument");
+    SPR_TRY(check_idle(r));
+    if (!std::isfinite(margin)) return set_error(SPR_ERR_INVALID_ARG, "margin must be finite");
+    for (int i = 0; i < mlp::kParams; ++i)
+        if (!std::isfinite(params[i])) return set_error(SPR_ERR_INVALID_ARG, "policy parameter %d is not finite", i);
+    if (!r->policy.p) SPR_TRY(buf_alloc(r->policy, sizeof(float) * (mlp::kParams + 1), nullptr));
+    // ordered after every earlier render of this renderer (they may read it)
+    SPR_CUDA_TRY(cudaDeviceSynchronize());
+    SPR_CUDA_TRY(cudaMemcpy(r->policy.p, params, sizeof(float) * mlp::kParams, cudaMemcpyHostToDevice));
+    SPR_CUDA_TRY(cudaMemcpy(r->policy.as<float>() + mlp::kParams, &margin, sizeof(float), cudaMemcpyHostToDevice));
+    r->policy_set = true;
+    r->need_raygen = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_set_trace(spr_renderer *r, float *features, uint32_t *rays, uint32_t *consumed, int64_t capacity,
+                             uint32_t sample_mod)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
+    const bool on = features != nullptr;
+    if (on && (!rays || !consumed || capacity < 1 || capacity > 0x7FFFFFFFll || sample_mod < 1))
+        return set_error(SPR_ERR_INVALID_ARG, "bad trace buffers");
+    if (on) {
+        SPR_TRY(buf_reserve(r->tr_taken, sizeof(uint32_t) * r->npix_cap, nullptr));
+        SPR_TRY(buf_reserve(r->tr_need, sizeof(uint32_t) * r->npix_cap, nullptr));
+        if (!r->tr_count.p) SPR_TRY(buf_alloc(r->tr_count, sizeof(uint32_t), nullptr));
+        SPR_CUDA_TRY(cudaMemset(r->tr_count.p, 0, sizeof(uint32_t)));
+    }
+    r->tr_feat = features;
+    r->tr_ray = rays;
+    r->tr_cons = consumed;
+    r->tr_cap = (uint32_t)capacity;
+    r->tr_mod = sample_mod;
+    r->tr_from = 0;
+    if (on != r->tracing || on) drop_graph(r);   // the pass graph holds the trace kernel and buffers
+    r->tracing = on;
+    r->need_raygen = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_trace_labels(spr_renderer *r, uint32_t *labels, int64_t *n_samples, spr_stream stream)
+{
+    clear_error();
+    if (!r || !labels || !n_samples) return set_error(SPR_ERR_INVALID_ARG, "NULL argument");
+    SPR_TRY(check_idle(r));
+    if (!r->tracing) return set_error(SPR_ERR_INVALID_ARG, "tracing is off");
+    if (r->n_live != 0 || r->need_raygen)
+        return set_error(SPR_ERR_INVALID_ARG, "labels need a converged render");
+    cudaStream_t s = as_stream(stream);
+    Trace T = make_trace(r);
+    trace_label_kernel<<<grid_for(r->tr_cap, 256, 8), 256, 0, s>>>(T, r->tr_from, labels);
+    SPR_CUDA_TRY(cudaGetLastError());
+    uint32_t count = 0;
+    SPR_CUDA_TRY(cudaMemcpyAsync(&count, r->tr_count.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    SPR_CUDA_TRY(cudaStreamSynchronize(s));
+    count = std::min(count, r->tr_cap);
+    r->tr_from = count;
+    *n_samples = count;
     return SPR_OK;
 }
 
