@@ -367,6 +367,177 @@ def run_study(args, wl):
     return 0
 
 
+def run_learned(args, wl):
+    """Learned speculation policy (config: the paper-scale volume, traces of
+    the plain raycaster from 64 random poses with isovalues in [0.2, 0.8],
+    evaluation on 32 held-out poses against the plain adaptive rule, every
+    image required to be bit-identical).  Renders start from an empty
+    cache; times are CUDA events around the C-ABI calls."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2309_10212_gb300 import build
+    build.build()
+    import paper_2309_10212_gb300 as spr
+    from paper_2309_10212_gb300 import _lib
+    L = _lib.load()
+    stream = torch.cuda.Stream()
+    out = {"workload": wl["name"], "train_poses": args.learn_train, "eval_poses": args.learn_eval}
+    rng = np.random.Generator(np.random.PCG64(21))
+    dims, W, H = wl["dims"], wl["W"], wl["H"]
+
+    def poses(n, seed0):
+        res = []
+        for i in range(n):
+            cam = synth.cameras.random_pose(dims, seed=seed0 + i, W=W, H=H,
+                                            distance_factor=float(rng.uniform(1.3, 2.0)))
+            res.append((cam, float(np.float32(rng.uniform(0.2, 0.8)))))
+        return res
+
+    train, held = poses(args.learn_train, 2000), poses(args.learn_eval, 3000)
+    f3 = ctypes.c_float * 3
+    with torch.cuda.stream(stream):
+        comp = compressed_on_device(wl, spr, torch)
+        vol = spr.spr_create_volume(dims, wl["rate"], comp, stream=stream)
+        del comp
+        r = spr.spr_create_renderer(vol, W, H)
+        spr.spr_set_cache_budget(r, wl["cache_bytes"])
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+        def one(cam, iso, keep=False):
+            flush.fill_(1)
+            rs = _lib.RenderStats()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            args_ = [f3(*[float(v) for v in cam[k]]) for k in ("eye", "p00", "du", "dv")]
+            a.record(stream)
+            _lib.check(L.spr_reset_cache(r.handle))
+            _lib.check(L.spr_set_camera(r.handle, *args_))
+            _lib.check(L.spr_set_isovalue(r.handle, ctypes.c_float(iso)))
+            _lib.check(L.spr_render_to_convergence(r.handle, ctypes.c_void_p(stream.cuda_stream), 4096,
+                                                   ctypes.byref(rs), None))
+            b.record(stream)
+            b.synchronize()
+            d = rs.as_dict()
+            d["ms"] = a.elapsed_time(b)
+            if keep:
+                fb = spr.spr_get_framebuffer(r)
+                d["image"] = {k: fb[k].clone() for k in ("depth", "rgba", "block", "cell", "status")}
+            return d
+
+        # 1. traces of the plain raycaster
+        spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=wl["k"])
+        cap = args.learn_samples
+        tr = spr.Trace(cap)
+        spr.spr_set_trace(r, tr, args.learn_mod)
+        t0 = time.perf_counter()
+        for cam, iso in train:
+            one(cam, iso)
+            spr.spr_trace_labels(r, tr, stream=stream)
+        spr.spr_set_trace(r, None)
+        n = tr.n
+        lab = tr.labels[:n].cpu().numpy()
+        out["trace"] = {"samples": n, "sample_mod": args.learn_mod, "s": round(time.perf_counter() - t0, 2),
+                        "label_mean": round(float(lab.mean()), 3),
+                        "label_p50": int(np.percentile(lab, 50)), "label_p90": int(np.percentile(lab, 90))}
+        # 2. training (hand-written kernels), seeded initial parameters
+        init = np.concatenate([np.ravel(x) for x in _init_params(5)]).astype(np.float32)
+        t0 = time.perf_counter()
+        params, losses = spr.spr_policy_train(tr.features[:n], tr.labels[:n], init, epochs=args.learn_epochs,
+                                              batch=8192, lr=2e-3, tau=0.9, seed=1, stream=stream)
+        torch.cuda.synchronize()
+        out["train"] = {"epochs": args.learn_epochs, "s": round(time.perf_counter() - t0, 3),
+                        "mse_log2_per_epoch": [round(float(x), 4) for x in losses]}
+        del tr
+        # 3. the margin on the first training poses, with and without the
+        # floor at the paper's uniform count
+        tune = []
+        for floor in (True, False):
+            for m in (-1.0, -0.5, 0.0, 0.5, 1.0, 2.0):
+                spr.spr_set_policy(r, params, m, floor=floor)
+                spr.spr_set_speculation(r, spr.SPR_SPEC_LEARNED, k_max=wl["k"])
+                for cam, iso in train[:2]:
+                    one(cam, iso)                          # warm-up
+                rows = [one(cam, iso) for cam, iso in train[:8]]
+                tune.append({"floor": floor, "margin": m, "ms": round(statistics.mean(x["ms"] for x in rows), 4),
+                             "passes": round(statistics.mean(x["passes"] for x in rows), 3),
+                             "blocks_decoded": round(statistics.mean(x["blocks_decoded"] for x in rows), 1)})
+        best = {f: min((t for t in tune if t["floor"] == f), key=lambda x: x["ms"]) for f in (True, False)}
+        fewest = min((t for t in tune if not t["floor"]), key=lambda x: x["blocks_decoded"])
+        out["margin"] = {"table": tune, "fastest_floor": best[True]["margin"],
+                         "fastest_no_floor": best[False]["margin"], "fewest_blocks_no_floor": fewest["margin"]}
+        # 4. held-out poses: plain against learned, images compared
+        arms = [("learned_floor", True, best[True]["margin"]),
+                ("learned_fewest_blocks", False, fewest["margin"])]
+        res = {"plain": []}
+        res.update({a[0]: [] for a in arms})
+        same = {a[0]: 0 for a in arms}
+        for cam, iso in held:
+            spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=wl["k"])
+            one(cam, iso)
+            a = one(cam, iso, keep=True)
+            for name, floor, m in arms:
+                spr.spr_set_policy(r, params, m, floor=floor)
+                spr.spr_set_speculation(r, spr.SPR_SPEC_LEARNED, k_max=wl["k"])
+                one(cam, iso)
+                b = one(cam, iso, keep=True)
+                same[name] += all(torch.equal(a["image"][k], b["image"][k]) for k in a["image"])
+                del b["image"]
+                res[name].append(b)
+            del a["image"]
+            res["plain"].append(a)
+
+        def summ(rows):
+            return {k: round(statistics.mean(x[k] for x in rows), 4)
+                    for k in ("ms", "passes", "blocks_decoded", "entries")}
+        out["plain"] = dict(summ(res["plain"]), rule="adaptive k<=%d" % wl["k"])
+        for name, floor, m in arms:
+            out[name] = dict(summ(res[name]), rule="learned count (<= 32, k_max %d)%s, margin %g" %
+                             (wl["k"], ", floored at the adaptive count" if floor else "", m),
+                             identical_images="%d/%d" % (same[name], len(held)))
+        out["identical_images"] = "%d/%d" % (min(same.values()), len(held))
+        # the tensor-core MLP alone on one row per pixel (features in HBM)
+        feats = torch.rand((W * H, 12), device="cuda")
+        spr.spr_policy_forward(params, feats, stream=stream)
+        ts = []
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            spr.spr_policy_forward(params, feats, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        out["mlp_forward"] = {"rows": W * H, "ms": round(statistics.median(ts), 4),
+                              "tflops": round(2 * W * H * (16 * 64 + 64 * 64 + 64 * 16) / (statistics.median(ts) / 1e3) / 1e12, 2),
+                              "timing": "median of 5 spr_policy_forward calls (includes its parameter copy and sync)"}
+        r.close()
+        vol.close()
+    with open(args.learned, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps({"learned": args.learned, "plain": out["plain"], "learned_floor": out["learned_floor"],
+                      "learned_fewest_blocks": out["learned_fewest_blocks"],
+                      "identical_images": out["identical_images"], "train": out["train"],
+                      "mlp_forward": out["mlp_forward"]}))
+    return 0
+
+
+def _init_params(seed):
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) layers of the 12-64-64-2
+    policy, in the C ABI's order (W1, b1, W2, b2, W3, b3)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for fan_out, fan_in in ((64, 12), (64, 64), (2, 64)):
+        bound = 1.0 / np.sqrt(fan_in)
+        parts.append(rng.uniform(-bound, bound, size=(fan_out, fan_in)))
+        parts.append(rng.uniform(-bound, bound, size=fan_out))
+    return parts
+
+
 SERVE_VOLUMES = [
     # (name, dims, generator, cache bytes per view)
     ("256^3 u8 Gaussian blobs (100)", (256, 256, 256), "blobs256", int(0.10 * 256 ** 3 * 4)),
@@ -519,6 +690,14 @@ def main():
     ap.add_argument("--serve", default="",
                     help="instead of the bench line: run the render service on a Poisson request "
                          "trace and write latency percentiles to this JSON file")
+    ap.add_argument("--learned", default="",
+                    help="instead of the bench line: train the speculation policy on traces of the "
+                         "workload and compare it with the plain rule on held-out poses")
+    ap.add_argument("--learn-train", type=int, default=64)
+    ap.add_argument("--learn-eval", type=int, default=32)
+    ap.add_argument("--learn-mod", type=int, default=16)
+    ap.add_argument("--learn-samples", type=int, default=24 << 20)
+    ap.add_argument("--learn-epochs", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--k-max", type=int, default=0,
@@ -534,6 +713,8 @@ def main():
         return run_study(args, wl)
     if args.serve:
         return run_serve(args)
+    if args.learned:
+        return run_learned(args, wl)
     if args.warmup < 3:
         args.warmup = 3
 

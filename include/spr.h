@@ -415,8 +415,13 @@ int spr_server_info(const spr_server *s, spr_server_stats *out);
  * super cell's coarse cells; the isovalue; the fraction of rays still live)
  * -> 64 -> 64 (ReLU) -> 2 outputs: y0 = the predicted log2 of the visible
  * blocks the ray still needs (up to and including its hit block), y1 = an
- * upper quantile of it.  The ray's count is k = ceil(2^(y0 + margin))
- * clamped to [1, min(k_max, the attempt's cap)].  Inference runs on the
+ * upper quantile of it (trained as the tau-quantile).  The ray's count is
+ * min(ceil(2^(y1 + margin)), 32), capped at min(k_max, the attempt's cap);
+ * with SPR_POLICY_FLOOR it is never below the paper's uniform count
+ * min(k_max, floor(w*h / N_Act)): no ray then advances less per pass than
+ * under the plain rule, so a learned render never takes more passes than
+ * the plain one (without cache overflow), and the policy decides how much
+ * further each ray speculates.  Inference runs on the
  * tensor cores (tcgen05.mma, bf16 weights and activations, fp32
  * accumulation, 128 rays per tile).  The image does not depend on the
  * policy.
@@ -427,8 +432,11 @@ int spr_server_info(const spr_server *s, spr_server_stats *out);
 #define SPR_POLICY_FEATURES 12
 #define SPR_POLICY_PARAMS 5122
 
-/* host parameters (copied) and margin; synchronises the device */
-int spr_set_policy(spr_renderer *r, const float *params, float margin);
+#define SPR_POLICY_FLOOR 1   /* counts never below the paper's uniform count */
+
+/* host parameters (copied), margin and flags (0 or SPR_POLICY_FLOOR);
+ * synchronises the device */
+int spr_set_policy(spr_renderer *r, const float *params, float margin, int flags);
 
 /* Training traces.  While set, every pass records, for the live rays whose
  * id hashes to 0 mod sample_mod, a sample: features[12] (fp32, as the policy

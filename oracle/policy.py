@@ -14,7 +14,8 @@ product library.
 * ``loss`` / ``grad``: the training loss per sample with t = log2(min(label,
   64)), (y0 - t)^2 + pinball_tau(t - y1), averaged over the samples, and its
   gradient by the chain rule through the layers.
-* ``policy_k``: the count k = ceil(2^(y0 + margin)) clamped to [1, cap].
+* ``policy_k``: the count max(min(ceil(2^(y1 + margin)), 32), floor_k)
+  clamped to cap, where floor_k is the paper's uniform count for the pass.
 * ``labels_from_pixels``: the visible blocks a ray still needs after taking
   ``consumed`` of them: up to and including its hit block (the hit's index in
   the ray's visible-block list + 1), or every visible block of a miss.
@@ -113,9 +114,10 @@ def grad(params, X, labels, tau: float):
     return pack(gW1, gb1, gW2, gb2, gW3, gb3)
 
 
-def policy_k(y0, margin: float, cap: int):
-    z = np.clip(np.asarray(y0, dtype=np.float64) + margin, -1.0, 12.0)
-    return np.clip(np.ceil(np.exp2(z)), 1, cap).astype(np.int64)
+def policy_k(y1, margin: float, cap: int, floor_k: int = 1):
+    z = np.clip(np.asarray(y1, dtype=np.float64) + margin, -1.0, 12.0)
+    k = np.clip(np.ceil(np.exp2(z)), 1, 32)
+    return np.minimum(np.maximum(k, floor_k), cap).astype(np.int64)
 
 
 def labels_from_pixels(pix, rays, consumed):

@@ -116,6 +116,7 @@ class ServerStats(ctypes.Structure):
 
 
 SPR_POLICY_FEATURES = 12
+SPR_POLICY_FLOOR = 1
 SPR_POLICY_PARAMS = 5122
 
 
@@ -173,7 +174,7 @@ PROTOTYPES = {
     "spr_server_submit": ([_vp, _vp, _vp], _i32),
     "spr_server_poll": ([_vp, _vp, _i32, _vp], _i32),
     "spr_server_info": ([_vp, _vp], _i32),
-    "spr_set_policy": ([_vp, _vp, ctypes.c_float], _i32),
+    "spr_set_policy": ([_vp, _vp, ctypes.c_float, _i32], _i32),
     "spr_set_trace": ([_vp, _vp, _vp, _vp, _i64, ctypes.c_uint32], _i32),
     "spr_trace_labels": ([_vp, _vp, _vp, _vp], _i32),
     "spr_policy_forward": ([_vp, _vp, _i64, _vp, _vp], _i32),

@@ -364,11 +364,15 @@ def _params(params):
     return p
 
 
-def spr_set_policy(r: Renderer, params, margin: float = 0.0):
+SPR_POLICY_FLOOR = _lib.SPR_POLICY_FLOOR
+
+
+def spr_set_policy(r: Renderer, params, margin: float = 0.0, floor: bool = True):
     """params: SPR_POLICY_PARAMS floats (W1[64][12], b1, W2[64][64], b2,
-    W3[2][64], b3)."""
+    W3[2][64], b3); floor: counts never below the paper's uniform count."""
     p = _params(params)
-    check(load().spr_set_policy(r.handle, p.ctypes.data_as(ctypes.c_void_p), float(margin)))
+    check(load().spr_set_policy(r.handle, p.ctypes.data_as(ctypes.c_void_p), float(margin),
+                                SPR_POLICY_FLOOR if floor else 0))
 
 
 class Trace:

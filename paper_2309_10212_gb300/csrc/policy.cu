@@ -253,7 +253,7 @@ extern "C" int spr_policy_forward(const float *params, const float *features, in
         if (e == cudaSuccess) e = cudaMemsetAsync(err.p, 0, sizeof(unsigned int), s);
         if (e == cudaSuccess) {
             const int64_t tiles = (n + kRows - 1) / kRows;
-            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * device_sm_count()));
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 4 * device_sm_count()));
             forward_kernel<<<grid, kRows, 0, s>>>(w.as<float>(), features, n, out, err.as<unsigned int>());
             e = cudaGetLastError();
         }

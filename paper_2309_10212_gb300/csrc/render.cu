@@ -1612,18 +1612,23 @@ __device__ __noinline__ void ray_features(const Geo &P, const PassState *ps, uin
     f[11] = (float)ps->n_live / (float)max(ps->npix, 1u);
 }
 
-// Speculation count from the policy's first output, the predicted log2 of
-// the visible blocks the ray still needs: k = ceil(2^(y + margin)), clamped
-// to [1, cap].
-__device__ __forceinline__ uint32_t policy_k(float y, float margin, uint32_t cap)
+// Speculation count of a ray: the policy's upper-quantile estimate of the
+// log2 of the visible blocks it still needs, k = ceil(2^(y1 + margin)) in
+// [1, 32]; with SPR_POLICY_FLOOR never below the paper's uniform count for
+// the pass (min(k_max, floor(w*h / N_Act)), Sec. 4), so that no ray advances
+// less per pass than under the plain rule; capped at `cap`.
+constexpr uint32_t kLearnedMax = 32;
+__device__ __forceinline__ uint32_t policy_k(float y, float margin, uint32_t floor_k, uint32_t cap)
 {
     const float z = fminf(fmaxf(y + margin, -1.f), 12.f);
-    return min(cap, max(1u, (uint32_t)ceilf(exp2f(z))));
+    const uint32_t k = min(kLearnedMax, max(1u, (uint32_t)ceilf(exp2f(z))));
+    return min(cap, max(k, floor_k));
 }
 
 // SPR_SPEC_LEARNED: features of 128 live rays per tile, the policy MLP on
 // the tensor cores (mlp.cuh), each ray's count.  params holds the fp32
-// parameter vector followed by the margin.  Persistent CTAs over the tiles.
+// parameter vector, the margin and the floor flag.  Persistent CTAs over
+// the tiles.
 __global__ void __launch_bounds__(128) policy_kernel(Geo P, const uint32_t *__restrict__ live0,
                                                      const uint32_t *__restrict__ live1,
                                                      const PassState *__restrict__ ps,
@@ -1635,10 +1640,19 @@ __global__ void __launch_bounds__(128) policy_kernel(Geo P, const uint32_t *__re
     const uint32_t nproc = ps->nproc;
     const int64_t ntiles = ((int64_t)nproc + mlp::kRows - 1) / mlp::kRows;
     if ((int64_t)blockIdx.x >= ntiles) return;   // uniform per CTA: no TMEM taken
-    mlp::tile_setup(S, params);
     const float margin = params[mlp::kParams];
     const uint32_t cap = min(ps->kk, ps->k_max);
+    const uint32_t floor_k =
+        params[mlp::kParams + 1] != 0.f ? max(1u, min(ps->k_max, ps->npix / max(ps->n_live, 1u))) : 1u;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
+    if (floor_k >= kLearnedMax) {
+        // the floor is at least any count the policy can give: no inference
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nproc;
+             i += (int64_t)gridDim.x * blockDim.x)
+            kray[i] = min(cap, floor_k);
+        return;
+    }
+    mlp::tile_setup(S, params);
     uint32_t phase = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t i = tile * mlp::kRows + threadIdx.x;
@@ -1661,7 +1675,7 @@ __global__ void __launch_bounds__(128) policy_kernel(Geo P, const uint32_t *__re
             }
             break;
         }
-        if (i < nproc) kray[i] = policy_k(y[0], margin, cap);
+        if (i < nproc) kray[i] = policy_k(y[1], margin, floor_k, cap);
     }
     mlp::tile_teardown(S);
 }
@@ -2272,10 +2286,10 @@ inline cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing)
 // attempt.
 int launch_policy(spr_renderer *r, cudaStream_t s)
 {
-    // persistent CTAs: at most two per SM (TMEM columns and shared memory
-    // leave room for other work), never more than there are tiles
+    // persistent CTAs: at most four per SM (256 of the 512 TMEM columns,
+    // 134 KB of shared memory), never more than there are tiles
     const int64_t tiles = (r->npix_cap + mlp::kRows - 1) / mlp::kRows;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * device_sm_count()));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 4 * device_sm_count()));
     policy_kernel<<<grid, mlp::kRows, 0, s>>>(make_geo(r), r->live[0].as<uint32_t>(), r->live[1].as<uint32_t>(),
                                               r->ps.as<PassState>(), r->state_in.as<uint64_t>(),
                                               r->policy.as<float>(), r->kray.as<uint32_t>(), r->ctr.as<uint32_t>());
@@ -3209,7 +3223,7 @@ extern "C" int spr_renderer_memory_estimate(const spr_volume *vol, int width, in
     return SPR_OK;
 }
 
-extern "C" int spr_set_policy(spr_renderer *r, const float *params, float margin)
+extern "C" int spr_set_policy(spr_renderer *r, const float *params, float margin, int flags)
 {
     clear_error();
     if (!r || !params) return set_error(SPR_ERR_INVALID_ARG, "NULL argument");
@@ -3217,11 +3231,13 @@ extern "C" int spr_set_policy(spr_renderer *r, const float *params, float margin
     if (!std::isfinite(margin)) return set_error(SPR_ERR_INVALID_ARG, "margin must be finite");
     for (int i = 0; i < mlp::kParams; ++i)
         if (!std::isfinite(params[i])) return set_error(SPR_ERR_INVALID_ARG, "policy parameter %d is not finite", i);
-    if (!r->policy.p) SPR_TRY(buf_alloc(r->policy, sizeof(float) * (mlp::kParams + 1), nullptr));
+    if (flags & ~SPR_POLICY_FLOOR) return set_error(SPR_ERR_INVALID_ARG, "unknown policy flags 0x%x", flags);
+    if (!r->policy.p) SPR_TRY(buf_alloc(r->policy, sizeof(float) * (mlp::kParams + 2), nullptr));
     // ordered after every earlier render of this renderer (they may read it)
     SPR_CUDA_TRY(cudaDeviceSynchronize());
     SPR_CUDA_TRY(cudaMemcpy(r->policy.p, params, sizeof(float) * mlp::kParams, cudaMemcpyHostToDevice));
-    SPR_CUDA_TRY(cudaMemcpy(r->policy.as<float>() + mlp::kParams, &margin, sizeof(float), cudaMemcpyHostToDevice));
+    const float extra[2] = {margin, (flags & SPR_POLICY_FLOOR) ? 1.f : 0.f};
+    SPR_CUDA_TRY(cudaMemcpy(r->policy.as<float>() + mlp::kParams, extra, sizeof extra, cudaMemcpyHostToDevice));
     r->policy_set = true;
     r->need_raygen = true;
     return SPR_OK;

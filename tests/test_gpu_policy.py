@@ -71,15 +71,15 @@ def test_forward_of_scaled_weights_is_exact_on_bf16_grids(spr):
 def test_counts_follow_the_rule(spr):
     import torch
     p = OP.init_params(12).astype(np.float32)
-    p[OP.OFF_B3] = 2.0                      # counts around 4
+    p[OP.OFF_B3 + 1] = 2.0                  # counts around 4
     X = rand_features(4096, 5)
     y = spr.spr_policy_forward(p, torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
     want = OP.forward(p, X, bf16_round=True)
-    k_gpu = OP.policy_k(y[:, 0], 0.25, 32)
-    k_orc = OP.policy_k(want[:, 0], 0.25, 32)
+    k_gpu = OP.policy_k(y[:, 1], 0.25, 32)
+    k_orc = OP.policy_k(want[:, 1], 0.25, 32)
     # the count may differ only where 2^(y + margin) lies within the output
     # tolerance of an integer
-    z = np.exp2(want[:, 0] + 0.25)
+    z = np.exp2(want[:, 1] + 0.25)
     near = np.abs(z - np.round(z)) < 0.05 * z
     assert np.array_equal(k_gpu[~near], k_orc[~near])
 
@@ -110,7 +110,7 @@ def test_training_lowers_the_loss(spr):
     assert losses[-1] < losses[0]
 
 
-def render(spr, sc, mode, k_max=32, params=None, margin=0.0, trace=None, slots=None):
+def render(spr, sc, mode, k_max=32, params=None, margin=0.0, trace=None, slots=None, floor=True):
     import torch
     v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
     r = spr.spr_create_renderer(v, sc.W, sc.H)
@@ -119,7 +119,7 @@ def render(spr, sc, mode, k_max=32, params=None, margin=0.0, trace=None, slots=N
     nb = sc.ovol.fine.shape[0]
     spr.spr_set_cache_budget(r, 256 * (slots if slots else max(8, nb)))
     if params is not None:
-        spr.spr_set_policy(r, params, margin)
+        spr.spr_set_policy(r, params, margin, floor=floor)
     spr.spr_set_speculation(r, mode, k_max=k_max)
     if trace is not None:
         spr.spr_set_trace(r, trace, 1)
@@ -132,16 +132,19 @@ def render(spr, sc, mode, k_max=32, params=None, margin=0.0, trace=None, slots=N
     return fb, rs, passes
 
 
+@pytest.mark.parametrize("floor", [True, False])
 @pytest.mark.parametrize("bias", [-1.0, 1.5, 4.0])
-def test_learned_render_keeps_the_image(spr, orc, bias):
+def test_learned_render_keeps_the_image(spr, orc, bias, floor):
     sc = value_scene(orc, (48, 40, 36), 51, 96, 72)
-    want, rs0, _ = render(spr, sc, spr.SPR_SPEC_ADAPTIVE, k_max=64)
+    want, rs0, p0 = render(spr, sc, spr.SPR_SPEC_ADAPTIVE, k_max=32)
     p = OP.init_params(15).astype(np.float32)
-    p[OP.OFF_B3] = bias
-    got, rs1, passes = render(spr, sc, spr.SPR_SPEC_LEARNED, k_max=32, params=p)
+    p[OP.OFF_B3 + 1] = bias
+    got, rs1, passes = render(spr, sc, spr.SPR_SPEC_LEARNED, k_max=32, params=p, floor=floor)
     for key in FB_KEYS:
         assert np.array_equal(got[key], want[key]), key
     assert rs1["n_hits"] == rs0["n_hits"]
+    if floor:   # no ray advances less per pass than under the plain rule
+        assert rs1["passes"] <= rs0["passes"]
     compare(sc, got)
 
 
@@ -149,7 +152,7 @@ def test_learned_render_tight_cache(spr, orc):
     sc = value_scene(orc, (48, 44, 40), 52, 64, 64)
     want, _, _ = render(spr, sc, spr.SPR_SPEC_ADAPTIVE)
     p = OP.init_params(16).astype(np.float32)
-    p[OP.OFF_B3] = 5.0                      # counts at the cap: the cache overflows
+    p[OP.OFF_B3 + 1] = 5.0                  # counts at the cap: the cache overflows
     got, _, passes = render(spr, sc, spr.SPR_SPEC_LEARNED, k_max=32, params=p, slots=24)
     assert any(pp["retries"] for pp in passes)
     for key in FB_KEYS:

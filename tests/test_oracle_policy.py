@@ -75,8 +75,10 @@ def test_policy_k_rule():
     assert P.policy_k(2.5, 0.0, 32) == 6          # 2^2.5 = 5.66
     assert P.policy_k(2.5, -1.0, 32) == 3         # 2^1.5 = 2.83
     assert P.policy_k(-3.0, 0.0, 32) == 1         # clamped below at 1
-    assert P.policy_k(9.3, 0.0, 32) == 32         # capped
+    assert P.policy_k(9.3, 0.0, 64) == 32         # the learned count stops at 32
     assert P.policy_k(4.2, 0.3, 64) == 23         # 2^4.5 = 22.6
+    assert P.policy_k(2.5, 0.0, 64, floor_k=10) == 10   # never below the paper's uniform count
+    assert P.policy_k(2.5, 0.0, 8, floor_k=10) == 8     # the attempt's cap wins
 
 
 def test_labels_from_visible_lists():
