@@ -700,6 +700,8 @@ def main():
     ap.add_argument("--learn-epochs", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--warp-walk", type=int, default=-1,
+                    help="live-ray count below which a pass walks one ray per warp (-1: the library default)")
     ap.add_argument("--k-max", type=int, default=0,
                     help="override the workload's speculation limit (k sweeps; 0 keeps it)")
     args = ap.parse_args()
@@ -751,6 +753,8 @@ def main():
             spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=wl["k"])
         spr.spr_set_isovalue(r, wl["iso"])
         spr.spr_set_profiling(r, False)
+        if args.warp_walk >= 0:
+            spr.spr_set_warp_walk_threshold(r, args.warp_walk)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         torch.cuda.synchronize()
 
