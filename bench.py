@@ -653,10 +653,24 @@ def run_serve(args):
     k_best = min(tune_rows, key=lambda r_: r_["makespan_s"])["k_max"]
     out["autotune_k_max"] = {"table": [{k: r_[k] for k in ("k_max", "makespan_s")} for r_ in tune_rows],
                              "chosen": k_best}
-    # Poisson arrivals in real time; the pool is warmed by the same requests
-    # as a burst first (renderer creation and graph capture excluded)
-    srv, _ = run(trace, 4, 8, k_best, False)
+    # Poisson arrivals in real time on a pool reserved with one renderer per
+    # (volume, resolution) and warmed by one request of each (renderer
+    # creation and graph capture excluded)
+    srv = spr.spr_server_create(8 << 30, max_inflight=4, max_batch=8, k_max=k_best)
+    srv.ids = [spr.spr_server_add_volume(srv, v, c) for v, c in vols]
+    warm = []
+    for vi in range(len(vols)):
+        for W, H in SERVE_RES:
+            spr.spr_server_reserve(srv, srv.ids[vi], W, H, 1)
+            q = next(x for x in trace if x["vol"] == vi)
+            warm.append(dict(q, W=W, H=H, cam=dict(q["cam"]), t=0.0))
+    for q in warm:   # cameras are resolution-specific: rebuild for this size
+        q["cam"] = synth.cameras.random_pose(SERVE_VOLUMES[q["vol"]][1], seed=77, W=q["W"], H=q["H"])
+    run(warm, 4, 8, k_best, False, server=srv)
     _, out["poisson"] = run(trace, 4, 8, k_best, True, server=srv)
+    # the same requests queued at once on that pool: overlap and batching
+    # (a batch uses a pooled renderer's view capacity, or a new renderer
+    # when the budget has room)
     _, out["burst_batched"] = run(trace, 4, 8, k_best, False, server=srv)
     srv.close()
     srv, _ = run(trace, 1, 1, k_best, False)

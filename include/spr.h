@@ -393,6 +393,12 @@ int spr_server_destroy(spr_server *s);
  * a render of n views gets n times that. */
 int spr_server_add_volume(spr_server *s, spr_volume *vol, size_t cache_bytes_per_view,
                           int32_t *volume_id);
+/* Create an idle pooled renderer for requests of (volume, width x height)
+ * batched up to n_views (<= max_batch), so that the first such request does
+ * not wait for the allocation; SPR_ERR_OUT_OF_MEMORY when it does not fit
+ * the budget beside the renderers already pooled.  Its graphs are captured at
+ * its first render. */
+int spr_server_reserve(spr_server *s, int32_t volume, int32_t width, int32_t height, int32_t n_views);
 /* seconds since the server was created (a monotonic clock) */
 double spr_server_clock(const spr_server *s);
 /* Queue a request (copied); *id (may be NULL) numbers requests 0, 1, ... */

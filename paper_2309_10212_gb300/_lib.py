@@ -171,6 +171,7 @@ PROTOTYPES = {
     "spr_server_destroy": ([_vp], _i32),
     "spr_server_add_volume": ([_vp, _vp, _sz, _vp], _i32),
     "spr_server_clock": ([_vp], ctypes.c_double),
+    "spr_server_reserve": ([_vp, _i32, _i32, _i32, _i32], _i32),
     "spr_server_submit": ([_vp, _vp, _vp], _i32),
     "spr_server_poll": ([_vp, _vp, _i32, _vp], _i32),
     "spr_server_info": ([_vp, _vp], _i32),

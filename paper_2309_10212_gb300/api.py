@@ -487,6 +487,10 @@ def spr_server_add_volume(s: Server, vol: Volume, cache_bytes_per_view: int) -> 
     return i.value
 
 
+def spr_server_reserve(s: Server, volume: int, W: int, H: int, n_views: int = 1):
+    check(load().spr_server_reserve(s.handle, int(volume), int(W), int(H), int(n_views)))
+
+
 def spr_server_clock(s: Server) -> float:
     return load().spr_server_clock(s.handle)
 

@@ -446,6 +446,22 @@ extern "C" int spr_server_add_volume(spr_server *s, spr_volume *vol, size_t cach
     return SPR_OK;
 }
 
+extern "C" int spr_server_reserve(spr_server *s, int32_t volume, int32_t width, int32_t height, int32_t n_views)
+{
+    clear_error();
+    if (!s) return set_error(SPR_ERR_INVALID_ARG, "NULL server");
+    if (volume < 0 || volume >= (int)s->vols.size()) return set_error(SPR_ERR_INVALID_ARG, "unknown volume %d", volume);
+    if (width < 1 || height < 1 || n_views < 1 || n_views > s->d.max_batch)
+        return set_error(SPR_ERR_INVALID_ARG, "bad shape %dx%d x%d", width, height, n_views);
+    size_t need = 0;
+    SPR_TRY(estimate(s, volume, width, height, n_views, &need));
+    if (s->mem_used + need > s->d.memory_bytes)
+        return set_error(SPR_ERR_OUT_OF_MEMORY, "reserving %zu bytes would exceed the budget (%zu of %zu used)", need,
+                         s->mem_used, s->d.memory_bytes);
+    PoolEntry *pe = nullptr;
+    return create_entry(s, volume, width, height, n_views, need, &pe);
+}
+
 extern "C" double spr_server_clock(const spr_server *s)
 {
     return s ? now_s(s) : 0.0;

@@ -238,3 +238,28 @@ def test_staggered_arrivals_overlap(spr, orc):
         want = alone(spr, sc, 300)
         for k in FB_KEYS:
             assert np.array_equal(fbs[i][k], want[k]), (i, k)
+
+
+def test_reserve_pools_a_renderer_within_the_budget(spr, orc):
+    import torch
+    sc = value_scene(orc, (28, 24, 20), 24, 40, 32)
+    v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    one = spr.spr_renderer_memory_estimate(v, sc.W, sc.H, 1, 256 * 64)
+    srv = spr.spr_server_create(int(one * 1.5), max_inflight=2, max_batch=2)
+    vid = spr.spr_server_add_volume(srv, v, 256 * 64)
+    spr.spr_server_reserve(srv, vid, sc.W, sc.H, 1)
+    info = spr.spr_server_info(srv)
+    assert info["renderers"] == 1 and info["memory_used"] == one
+    with pytest.raises(spr.SprError):           # a second one does not fit
+        spr.spr_server_reserve(srv, vid, sc.W, sc.H, 1)
+    o = dict(depth=torch.zeros(sc.W * sc.H, device="cuda"))
+    spr.spr_server_submit(srv, vid, sc.cam, sc.iso, sc.W, sc.H, outputs=o)
+    res = []
+    while not res:
+        res = spr.spr_server_poll(srv)
+    assert res[0]["status"] == 0
+    assert spr.spr_server_info(srv)["renderers_created"] == 1   # the reserved one served it
+    want = alone(spr, sc, 64)
+    assert np.array_equal(o["depth"].cpu().numpy(), want["depth"])
+    srv.close()
+    v.close()
