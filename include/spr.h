@@ -438,9 +438,11 @@ int spr_server_info(const spr_server *s, spr_server_stats *out);
 #define SPR_POLICY_FEATURES 12
 #define SPR_POLICY_PARAMS 5122
 
-#define SPR_POLICY_FLOOR 1   /* counts never below the paper's uniform count */
+#define SPR_POLICY_FLOOR 1             /* counts never below the paper's uniform count */
+#define SPR_POLICY_FLOOR_AFTER_FIRST 2 /* the floor from the second pass on: the first
+                                        * pass takes the policy's counts alone */
 
-/* host parameters (copied), margin and flags (0 or SPR_POLICY_FLOOR);
+/* host parameters (copied), margin and flags (0 or one of the floors);
  * synchronises the device */
 int spr_set_policy(spr_renderer *r, const float *params, float margin, int flags);
 

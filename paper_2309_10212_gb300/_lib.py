@@ -117,6 +117,7 @@ class ServerStats(ctypes.Structure):
 
 SPR_POLICY_FEATURES = 12
 SPR_POLICY_FLOOR = 1
+SPR_POLICY_FLOOR_AFTER_FIRST = 2
 SPR_POLICY_PARAMS = 5122
 
 

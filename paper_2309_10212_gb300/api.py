@@ -365,14 +365,21 @@ def _params(params):
 
 
 SPR_POLICY_FLOOR = _lib.SPR_POLICY_FLOOR
+SPR_POLICY_FLOOR_AFTER_FIRST = _lib.SPR_POLICY_FLOOR_AFTER_FIRST
 
 
-def spr_set_policy(r: Renderer, params, margin: float = 0.0, floor: bool = True):
+def spr_set_policy(r: Renderer, params, margin: float = 0.0, floor="all"):
     """params: SPR_POLICY_PARAMS floats (W1[64][12], b1, W2[64][64], b2,
-    W3[2][64], b3); floor: counts never below the paper's uniform count."""
+    W3[2][64], b3); floor: "all" (counts never below the paper's uniform
+    count), "after_first" (from the second pass on) or None/False."""
     p = _params(params)
-    check(load().spr_set_policy(r.handle, p.ctypes.data_as(ctypes.c_void_p), float(margin),
-                                SPR_POLICY_FLOOR if floor else 0))
+    if floor is True or floor == "all":
+        flags = SPR_POLICY_FLOOR
+    elif floor == "after_first":
+        flags = SPR_POLICY_FLOOR_AFTER_FIRST
+    else:
+        flags = 0
+    check(load().spr_set_policy(r.handle, p.ctypes.data_as(ctypes.c_void_p), float(margin), flags))
 
 
 class Trace:

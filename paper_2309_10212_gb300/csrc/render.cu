@@ -1614,9 +1614,10 @@ __device__ __noinline__ void ray_features(const Geo &P, const PassState *ps, uin
 
 // Speculation count of a ray: the policy's upper-quantile estimate of the
 // log2 of the visible blocks it still needs, k = ceil(2^(y1 + margin)) in
-// [1, 32]; with SPR_POLICY_FLOOR never below the paper's uniform count for
-// the pass (min(k_max, floor(w*h / N_Act)), Sec. 4), so that no ray advances
-// less per pass than under the plain rule; capped at `cap`.
+// [1, 32]; in the passes the floor applies to (all with SPR_POLICY_FLOOR,
+// all but the first with SPR_POLICY_FLOOR_AFTER_FIRST) never below the
+// paper's uniform count for the pass (min(k_max, floor(w*h / N_Act)), Sec. 4);
+// capped at `cap`.
 constexpr uint32_t kLearnedMax = 32;
 __device__ __forceinline__ uint32_t policy_k(float y, float margin, uint32_t floor_k, uint32_t cap)
 {
@@ -1627,8 +1628,8 @@ __device__ __forceinline__ uint32_t policy_k(float y, float margin, uint32_t flo
 
 // SPR_SPEC_LEARNED: features of 128 live rays per tile, the policy MLP on
 // the tensor cores (mlp.cuh), each ray's count.  params holds the fp32
-// parameter vector, the margin and the floor flag.  Persistent CTAs over
-// the tiles.
+// parameter vector, the margin and the first floored pass.  Persistent CTAs
+// over the tiles.
 __global__ void __launch_bounds__(128) policy_kernel(Geo P, const uint32_t *__restrict__ live0,
                                                      const uint32_t *__restrict__ live1,
                                                      const PassState *__restrict__ ps,
@@ -1642,8 +1643,12 @@ __global__ void __launch_bounds__(128) policy_kernel(Geo P, const uint32_t *__re
     if ((int64_t)blockIdx.x >= ntiles) return;   // uniform per CTA: no TMEM taken
     const float margin = params[mlp::kParams];
     const uint32_t cap = min(ps->kk, ps->k_max);
-    const uint32_t floor_k =
-        params[mlp::kParams + 1] != 0.f ? max(1u, min(ps->k_max, ps->npix / max(ps->n_live, 1u))) : 1u;
+    // params[kParams + 1]: the first pass (0-based) whose counts are floored
+    // at the paper's uniform count; negative: never
+    const float floor_from = params[mlp::kParams + 1];
+    const uint32_t floor_k = (floor_from >= 0.f && (float)ps->pass >= floor_from)
+                                 ? max(1u, min(ps->k_max, ps->npix / max(ps->n_live, 1u)))
+                                 : 1u;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
     if (floor_k >= kLearnedMax) {
         // the floor is at least any count the policy can give: no inference
@@ -3231,12 +3236,13 @@ extern "C" int spr_set_policy(spr_renderer *r, const float *params, float margin
     if (!std::isfinite(margin)) return set_error(SPR_ERR_INVALID_ARG, "margin must be finite");
     for (int i = 0; i < mlp::kParams; ++i)
         if (!std::isfinite(params[i])) return set_error(SPR_ERR_INVALID_ARG, "policy parameter %d is not finite", i);
-    if (flags & ~SPR_POLICY_FLOOR) return set_error(SPR_ERR_INVALID_ARG, "unknown policy flags 0x%x", flags);
+    if (flags & ~(SPR_POLICY_FLOOR | SPR_POLICY_FLOOR_AFTER_FIRST))
+        return set_error(SPR_ERR_INVALID_ARG, "unknown policy flags 0x%x", flags);
     if (!r->policy.p) SPR_TRY(buf_alloc(r->policy, sizeof(float) * (mlp::kParams + 2), nullptr));
     // ordered after every earlier render of this renderer (they may read it)
     SPR_CUDA_TRY(cudaDeviceSynchronize());
     SPR_CUDA_TRY(cudaMemcpy(r->policy.p, params, sizeof(float) * mlp::kParams, cudaMemcpyHostToDevice));
-    const float extra[2] = {margin, (flags & SPR_POLICY_FLOOR) ? 1.f : 0.f};
+    const float extra[2] = {margin, (flags & SPR_POLICY_FLOOR) ? 0.f : ((flags & SPR_POLICY_FLOOR_AFTER_FIRST) ? 1.f : -1.f)};
     SPR_CUDA_TRY(cudaMemcpy(r->policy.as<float>() + mlp::kParams, extra, sizeof extra, cudaMemcpyHostToDevice));
     r->policy_set = true;
     r->need_raygen = true;

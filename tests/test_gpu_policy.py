@@ -132,7 +132,7 @@ def render(spr, sc, mode, k_max=32, params=None, margin=0.0, trace=None, slots=N
     return fb, rs, passes
 
 
-@pytest.mark.parametrize("floor", [True, False])
+@pytest.mark.parametrize("floor", [True, "after_first", False])
 @pytest.mark.parametrize("bias", [-1.0, 1.5, 4.0])
 def test_learned_render_keeps_the_image(spr, orc, bias, floor):
     sc = value_scene(orc, (48, 40, 36), 51, 96, 72)
@@ -143,7 +143,7 @@ def test_learned_render_keeps_the_image(spr, orc, bias, floor):
     for key in FB_KEYS:
         assert np.array_equal(got[key], want[key]), key
     assert rs1["n_hits"] == rs0["n_hits"]
-    if floor:   # no ray advances less per pass than under the plain rule
+    if floor is True:   # no ray advances less per pass than under the plain rule
         assert rs1["passes"] <= rs0["passes"]
     compare(sc, got)
 
@@ -225,3 +225,58 @@ def test_trace_features_and_labels(spr, orc):
     assert np.abs(feat[first] - of[idx]).max() < 2e-6
     # later passes consume exactly the counts taken before
     assert np.all(lab + np.minimum(cons, 10 ** 9) >= 1)
+
+
+def test_learned_mode_needs_a_policy_and_valid_flags(spr, orc):
+    import torch
+    sc = value_scene(orc, (16, 16, 16), 54, 16, 16)
+    v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    r = spr.spr_create_renderer(v, 16, 16)
+    with pytest.raises(spr.SprError):
+        spr.spr_set_speculation(r, spr.SPR_SPEC_LEARNED, k_max=8)
+    p = OP.init_params(1).astype(np.float32)
+    bad = p.copy()
+    bad[7] = np.nan
+    with pytest.raises(spr.SprError):
+        spr.spr_set_policy(r, bad, 0.0)
+    L = spr._lib.load()
+    assert L.spr_set_policy(r.handle, p.ctypes.data_as(spr.api.ctypes.c_void_p), 0.0, 4) == spr._lib.SPR_ERR_INVALID_ARG
+    spr.spr_set_policy(r, p, 0.0)
+    spr.spr_set_speculation(r, spr.SPR_SPEC_LEARNED, k_max=8)
+    r.close()
+    v.close()
+
+
+def test_trace_sampling_and_capacity(spr, orc):
+    """With sample_mod m only rays whose id hashes to 0 mod m are recorded;
+    a full buffer keeps its first samples and reports its capacity."""
+    import torch
+    sc = value_scene(orc, (40, 36, 32), 55, 80, 64)
+    full = spr.Trace(80 * 64 * 40)
+    render(spr, sc, spr.SPR_SPEC_ADAPTIVE, k_max=8, trace=full)
+    n_full = full.n
+    v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    r = spr.spr_create_renderer(v, sc.W, sc.H)
+    spr.spr_set_cache_budget(r, 256 * sc.ovol.fine.shape[0])
+    spr.spr_set_camera(r, sc.cam)
+    spr.spr_set_isovalue(r, sc.iso)
+    spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=8)
+    sub = spr.Trace(n_full)
+    spr.spr_set_trace(r, sub, 7)
+    spr.spr_render_to_convergence(r, 100000)
+    n_sub = spr.spr_trace_labels(r, sub)
+    assert 0 < n_sub < n_full / 3
+    rays_full = full.rays[:n_full].cpu().numpy()
+    rays_sub = sub.rays[:n_sub].cpu().numpy()
+    assert set(rays_sub.tolist()) <= set(rays_full.tolist())
+    small = spr.Trace(100)
+    spr.spr_set_trace(r, small, 1)
+    spr.spr_set_camera(r, sc.cam)
+    spr.spr_render_to_convergence(r, 100000)
+    assert spr.spr_trace_labels(r, small) == 100
+    # labels need a converged render
+    spr.spr_set_camera(r, sc.cam)
+    with pytest.raises(spr.SprError):
+        spr.spr_trace_labels(r, small)
+    r.close()
+    v.close()

@@ -263,3 +263,24 @@ def test_reserve_pools_a_renderer_within_the_budget(spr, orc):
     assert np.array_equal(o["depth"].cpu().numpy(), want["depth"])
     srv.close()
     v.close()
+
+
+def test_submit_rejects_bad_requests(spr, orc):
+    import torch
+    sc = value_scene(orc, (20, 20, 20), 25, 16, 16)
+    srv = spr.spr_server_create(1 << 26, max_inflight=1, max_batch=1)
+    v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    vid = spr.spr_server_add_volume(srv, v, 256 * 64)
+    with pytest.raises(spr.SprError):
+        spr.spr_server_submit(srv, vid + 1, sc.cam, sc.iso, 16, 16)      # unknown volume
+    cam = dict(sc.cam)
+    cam["eye"] = np.array(cam["eye"], np.float32) + np.float32(1e-3)   # off the 1/256 grid
+    with pytest.raises(spr.SprError):
+        spr.spr_server_submit(srv, vid, cam, sc.iso, 16, 16)
+    with pytest.raises(spr.SprError):
+        spr.spr_server_submit(srv, vid, sc.cam, float("nan"), 16, 16)
+    with pytest.raises(spr.SprError):
+        spr.spr_server_create(1 << 20, max_inflight=0)
+    assert spr.spr_server_info(srv)["pending"] == 0
+    srv.close()
+    v.close()
