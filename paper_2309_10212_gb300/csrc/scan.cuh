@@ -1,6 +1,7 @@
 // scan.cuh -- single-pass stream compaction / prefix sum with decoupled
 // look-back (Merrill and Garland), the primitive behind the compactions and
-// prefix sums of Sec. 3.6 and 4.2.
+// prefix sums of Sec. 3.6 and 4.2.  The look-back is warp-parallel: one warp
+// inspects 32 predecessors per round.
 //
 // One kernel computes, for elements i in [0, n), a count c(i) and calls
 // emit(i, prefix, c(i)) with the exclusive prefix sum of the counts.  Tiles
@@ -120,39 +121,63 @@ __global__ void __launch_bounds__(kScanThreads)
         __syncthreads();
         const uint32_t total_tile = s_total;
 
-        if (tid == 0) {
+        // Look-back by warp 0: lane j inspects tile - 1 - j - 32r in round
+        // r.  The nearest predecessor holding an inclusive prefix ends the
+        // walk; every tile between it and this one must have published its
+        // aggregate (else the warp waits and polls again).  One round covers
+        // 32 predecessors, so tiles that run together do not wait on each
+        // other's serial walks.
+        if (wid == 0) {
             uint32_t prefix = 0;
             const bool publish_ok = tile != ctl.withhold;
             if (tile == 0) {
-                if (publish_ok) publish(&ctl.status[0], kInc | tag | total_tile);
+                if (lane == 0 && publish_ok) publish(&ctl.status[0], kInc | tag | total_tile);
             } else {
-                if (publish_ok) publish(&ctl.status[tile], kAgg | tag | total_tile);
-                int64_t pred = tile - 1;
+                if (lane == 0 && publish_ok) publish(&ctl.status[tile], kAgg | tag | total_tile);
+                int64_t hi = tile - 1;   // nearest predecessor of this round's window
                 int64_t polls = 0;
                 unsigned ns = 32;
-                while (pred >= 0) {
-                    unsigned long long w = poll(&ctl.status[pred]);
-                    unsigned long long st = w & kStatusBits;
-                    if (st == 0 || (w & kEpochBits) != tag) {  // not yet published in this launch
+                bool gave_up = false;
+                for (;;) {
+                    const int64_t pred = hi - lane;
+                    unsigned long long w = pred >= 0 ? poll(&ctl.status[pred]) : 0ull;
+                    const unsigned long long st = w & kStatusBits;
+                    const bool valid = pred >= 0 && st != 0 && (w & kEpochBits) == tag;
+                    const unsigned inc = __ballot_sync(0xFFFFFFFFu, valid && st == kInc);
+                    const unsigned ok = __ballot_sync(0xFFFFFFFFu, valid);
+                    // lanes that must be valid: up to the nearest inclusive,
+                    // or every lane with a predecessor when none is inclusive
+                    const int first_inc = inc ? __ffs(inc) - 1 : 32;
+                    const int span = hi + 1 < 32 ? (int)(hi + 1) : 32;
+                    const int need_n = first_inc < 32 ? first_inc + 1 : span;
+                    const unsigned need = need_n >= 32 ? 0xFFFFFFFFu : ((1u << need_n) - 1u);
+                    if ((ok & need) != need) {
                         if (++polls > ctl.spin_limit) {
-                            atomicOr(ctl.flags, 1u);
-                            break;
+                            if (lane == 0) atomicOr(ctl.flags, 1u);
+                            gave_up = true;
+                        } else if ((polls & 63) == 0 && (*(volatile unsigned int *)ctl.flags & 1u)) {
+                            gave_up = true;
                         }
-                        if ((polls & 63) == 0 && (*(volatile unsigned int *)ctl.flags & 1u)) break;
+                        if (__any_sync(0xFFFFFFFFu, gave_up)) break;
                         __nanosleep(ns);
-                        if (ns < 1024) ns <<= 1;
+                        if (ns < 256) ns <<= 1;
                         continue;
                     }
-                    prefix += (uint32_t)(w & 0xFFFFFFFFull);
-                    if (st == kInc) break;
-                    --pred;
+                    uint32_t v = (lane < need_n) ? (uint32_t)(w & 0xFFFFFFFFull) : 0u;
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                    prefix += v;
+                    if (first_inc < 32 || hi < 32) break;
+                    hi -= 32;
                 }
-                if (publish_ok) publish(&ctl.status[tile], kInc | tag | (uint32_t)(prefix + total_tile));
+                if (lane == 0 && publish_ok) publish(&ctl.status[tile], kInc | tag | (uint32_t)(prefix + total_tile));
             }
-            s_prefix = prefix;
-            if (base + kScanTile >= n) {
-                if (total) *total = prefix + total_tile;
-                if (ctl.over) *ctl.over = (prefix + total_tile) > ctl.over_limit ? 1u : 0u;
+            if (lane == 0) {
+                s_prefix = prefix;
+                if (base + kScanTile >= n) {
+                    if (total) *total = prefix + total_tile;
+                    if (ctl.over) *ctl.over = (prefix + total_tile) > ctl.over_limit ? 1u : 0u;
+                }
             }
         }
         __syncthreads();
