@@ -144,16 +144,23 @@ __device__ __forceinline__ int64_t dec_id(const uint32_t *ids, int64_t i, int64_
     return i < n ? (ids ? (int64_t)ids[i] : i) : -1;
 }
 
-__global__ void __launch_bounds__(kDecThreads) decode_list_kernel(
+// One thread decodes one block into its own row of shared memory (64
+// coefficient words, padded to 68 so that the 128-bit accesses of a quarter
+// warp hit 32 distinct banks); the warp then writes its blocks out two per
+// instruction, 16 bytes per lane.  Rates <= 2 keep the whole stream in
+// registers (one 128-bit load, software-pipelined one block ahead).  Six
+// CTAs per SM (shared memory allows six; the register cap keeps it).
+__global__ void __launch_bounds__(kDecThreads, 6) decode_list_kernel(
     const uint8_t *__restrict__ comp, int64_t nblocks, int rate, const uint32_t *__restrict__ ids,
     const uint32_t *__restrict__ dst_ids, int64_t n_host, const uint32_t *n_dev,
     const uint32_t *skip, float *__restrict__ out, unsigned int *bad)
 {
-    __shared__ uint32_t col_s[64 * kColStride];
+    __shared__ __align__(16) uint32_t rows_s[kDecThreads * kRowStride];
     if (skip && *skip) return;
     const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t *col = col_s + threadIdx.x;
+    uint32_t *row = rows_s + threadIdx.x * kRowStride;
+    const uint32_t *wrows = rows_s + wid * 32 * kRowStride;
     const int64_t bytes = 8 * (int64_t)rate;
     const int64_t stride = (int64_t)gridDim.x * kDecThreads;
     const bool reg = rate <= 2;
@@ -162,6 +169,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_list_kernel(
     int64_t id_next = dec_id(ids, base + stride + lane, n);
     frc4::RegBits cur{0ull, 0ull};
     if (reg && id >= 0 && id < nblocks) cur = frc4::load_reg_bits(comp + id * bytes, rate);
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
     for (; base < n; base += stride) {
         const int64_t i = base + lane;
         // loads for the next items, consumed one and two iterations later
@@ -170,32 +178,39 @@ __global__ void __launch_bounds__(kDecThreads) decode_list_kernel(
         const int64_t id_after = dec_id(ids, base + 2 * stride + lane, n);
         const uint32_t my_slot = i < n ? (dst_ids ? dst_ids[i] : (uint32_t)i) : 0u;
         if (i < n) {
-            float v[64];
             int emax = 0;
             bool nz = false;
+            // the parse zeroes the row before it sets bits
             if (id < nblocks) {
-                nz = reg ? frc4::decode_coeffs(cur, rate, col, kColStride, &emax)
-                         : frc4::decode_block_coeffs(comp + id * bytes, rate, col, kColStride, &emax);
+                nz = reg ? frc4::decode_coeffs(cur, rate, row, 1, &emax)
+                         : frc4::decode_block_coeffs(comp + id * bytes, rate, row, 1, &emax);
             } else {
                 atomicOr(bad, 1u);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) reinterpret_cast<uint4 *>(row)[q] = zero4;
             }
             if (nz) {
-                frc4::reconstruct(col, kColStride, emax, v);
+                float v[64];
+                frc4::reconstruct_row(row, emax, v);
 #pragma unroll
-                for (int k = 0; k < 64; ++k) col[k * kColStride] = __float_as_uint(v[k]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 64; ++k) col[k * kColStride] = 0u;
+                for (int q = 0; q < 16; ++q)
+                    reinterpret_cast<uint4 *>(row)[q] =
+                        make_uint4(__float_as_uint(v[4 * q]), __float_as_uint(v[4 * q + 1]),
+                                   __float_as_uint(v[4 * q + 2]), __float_as_uint(v[4 * q + 3]));
             }
         }
         __syncwarp();
+        // blocks t and t + 1 of the warp per step: lanes 0-15 and 16-31 each
+        // move one 16-byte quarter-row
         const int m = n - base < 32 ? (int)(n - base) : 32;
-        for (int t = 0; t < m; ++t) {
-            const uint32_t slot = __shfl_sync(0xFFFFFFFFu, my_slot, t);
-            float *dst = out + (int64_t)slot * 64;
-            const uint32_t *src = col_s + wid * 32 + t;
-            dst[lane] = __uint_as_float(src[lane * kColStride]);
-            dst[lane + 32] = __uint_as_float(src[(lane + 32) * kColStride]);
+        const int half = lane >> 4, q = lane & 15;
+        for (int t = 0; t < m; t += 2) {
+            const int blk = t + half;
+            const uint32_t slot = __shfl_sync(0xFFFFFFFFu, my_slot, blk & 31);
+            if (blk < m) {
+                const uint4 w = reinterpret_cast<const uint4 *>(wrows + blk * kRowStride)[q];
+                reinterpret_cast<uint4 *>(out + (int64_t)slot * 64)[q] = w;
+            }
         }
         __syncwarp();
         cur = nxt;

@@ -75,13 +75,19 @@ __device__ __forceinline__ RegBits load_reg_bits(const uint8_t *blk, int rate)
 }
 
 // Parse one block.  col[k * stride] receives the negabinary value of the k-th
-// coefficient in sequency order.  Returns false for an all-zero block.
+// coefficient in sequency order (stride 1: col is 16-byte aligned).  Returns
+// false for an all-zero block.
 template <class Bits>
 __device__ __forceinline__ bool decode_coeffs(const Bits &bits_at, int rate, uint32_t *col, int stride,
                                               int *emax)
 {
+    if (stride == 1) {   // a row (16-byte aligned): vector stores
 #pragma unroll
-    for (int i = 0; i < 64; ++i) col[i * stride] = 0u;
+        for (int q = 0; q < 16; ++q) reinterpret_cast<uint4 *>(col)[q] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) col[i * stride] = 0u;
+    }
     uint32_t h = bits_at(0, 9);
     if (!(h & 1u)) return false;
     int e = (int)((h >> 1) & 0xFFu) - 127;
@@ -184,6 +190,40 @@ __device__ __forceinline__ void reconstruct(const uint32_t *col, int stride, int
     int32_t c[64];
 #pragma unroll
     for (int k = 0; k < 64; ++k) c[ord.v[k]] = from_negabinary(col[k * stride]);
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) inv_lift(c[x + 4 * y], c[x + 4 * y + 16], c[x + 4 * y + 32], c[x + 4 * y + 48]);
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) inv_lift(c[x + 16 * z], c[x + 16 * z + 4], c[x + 16 * z + 8], c[x + 16 * z + 12]);
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) inv_lift(c[4 * y + 16 * z], c[4 * y + 16 * z + 1], c[4 * y + 16 * z + 2], c[4 * y + 16 * z + 3]);
+    float scale = pow2f(emax - 24);
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __fmul_rn(__int2float_rn(c[i]), scale);
+}
+
+// reconstruct() for coefficients in row[0..63] (16-byte aligned), read with
+// 128-bit loads
+__device__ __forceinline__ void reconstruct_row(const uint32_t *row, int emax, float v[64])
+{
+    constexpr Order ord = make_order();
+    uint32_t u[64];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const uint4 w = reinterpret_cast<const uint4 *>(row)[q];
+        u[4 * q] = w.x;
+        u[4 * q + 1] = w.y;
+        u[4 * q + 2] = w.z;
+        u[4 * q + 3] = w.w;
+    }
+    int32_t c[64];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) c[ord.v[k]] = from_negabinary(u[k]);
 #pragma unroll
     for (int y = 0; y < 4; ++y)
 #pragma unroll

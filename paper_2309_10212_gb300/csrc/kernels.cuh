@@ -8,6 +8,7 @@ namespace spr {
 
 constexpr int kDecThreads = 128;             // decode: one thread per block
 constexpr int kColStride = kDecThreads + 1;  // padded shared-memory column stride
+constexpr int kRowStride = 68;               // decode_list_kernel: words per block row (64 + 4 pad)
 
 // grid for a grid-stride loop over n items, at most per_sm CTAs per SM
 int grid_for(int64_t n, int threads, int per_sm);
