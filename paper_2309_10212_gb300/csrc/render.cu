@@ -883,12 +883,13 @@ struct BitsCount {
 
 struct BitsEmit {
     const uint32_t *bits;
-    uint32_t *wpre;
+    uint32_t *wpre;  // optional: the prefix of each word that holds a set bit
     uint32_t *list;
     uint32_t *zero;  // optional: zero this array at each emitted position
     __device__ void operator()(int64_t w, uint32_t pre, uint32_t c) const
     {
-        wpre[w] = pre;
+        if (!c) return;   // empty words: no prefix is ever asked for them
+        if (wpre) wpre[w] = pre;
         uint32_t x = bits[w];
         while (x) {
             int k = __ffs(x) - 1;
@@ -1961,7 +1962,7 @@ struct spr_renderer {
     uint32_t tr_cap = 0, tr_mod = 1, tr_from = 0;
     DevBuf tr_count, tr_taken, tr_need;
     int64_t cap_entries = 0;
-    DevBuf vis_bits, act_bits, vis_wpre, act_wpre, ivis, iact, nbrays, obrays;
+    DevBuf vis_bits, act_bits, vis_wpre, ivis, iact, nbrays, obrays;
     DevBuf lbits;   // enter bits at ray generation, alive bits at resolve (one per live position)
     int64_t nwords = 0, cap_act = 0;
     DevBuf cache, blk_slot, slot_blk, lru[2], touched, miss, victim;
@@ -2025,7 +2026,7 @@ void free_all(spr_renderer *r)
     drop_graph(r);
     DevBuf *bufs[] = {&r->state_in, &r->state_out, &r->status, &r->live[0], &r->live[1], &r->keys,
                       &r->fb_depth, &r->fb_rgba, &r->fb_block, &r->fb_cell, &r->fb_final, &r->rbid,
-                      &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre, &r->act_wpre,
+                      &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre,
                       &r->ivis, &r->iact, &r->nbrays, &r->obrays, &r->cache, &r->blk_slot,
                       &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
                       &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
@@ -2380,7 +2381,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     // scan (cache branch) decides whether the pass overflows the cache.
     SPR_TRY(run_compact(r->scan_status[1], r->scan_ticket[1], flags, r->nwords, nullptr,
                         BitsCount{r->act_bits.as<uint32_t>(), nullptr},
-                        BitsEmit{r->act_bits.as<uint32_t>(), r->act_wpre.as<uint32_t>(), r->iact.as<uint32_t>(),
+                        BitsEmit{r->act_bits.as<uint32_t>(), nullptr, r->iact.as<uint32_t>(),
                                  nullptr},
                         ctr + C_NACT, sa, kDefaultSpinLimit, -1, ctr + C_OVERFLOW, (uint32_t)r->n_slots));
     SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, sa));
@@ -2740,7 +2741,6 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
     }
     if ((rc = buf_alloc(r->vis_bits, 4 * r->nwords, s)) ||
         (rc = buf_alloc(r->act_bits, 4 * r->nwords, s)) || (rc = buf_alloc(r->vis_wpre, 4 * r->nwords, s)) ||
-        (rc = buf_alloc(r->act_wpre, 4 * r->nwords, s)) ||
         (rc = buf_alloc(r->blk_slot, 4 * vol->g.nblocks, s)) || (rc = buf_alloc(r->scan_ticket[0], 64, s)) ||
         (rc = buf_alloc(r->scan_ticket[1], 64, s)) || (rc = buf_alloc(r->scan_ticket[2], 64, s)) ||
         (rc = buf_alloc(r->ctr, sizeof(uint32_t) * C_COUNT, s)) ||
@@ -3187,7 +3187,7 @@ extern "C" int spr_renderer_memory(const spr_renderer *r, size_t *device_bytes)
     if (!r || !device_bytes) return set_error(SPR_ERR_INVALID_ARG, "NULL argument");
     const DevBuf *bufs[] = {&r->state_in, &r->state_out, &r->status, &r->live[0], &r->live[1], &r->keys,
                             &r->fb_depth, &r->fb_rgba, &r->fb_block, &r->fb_cell, &r->fb_final, &r->rbid,
-                            &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre, &r->act_wpre,
+                            &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre,
                             &r->ivis, &r->iact, &r->nbrays, &r->obrays, &r->cache, &r->blk_slot,
                             &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
                             &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
@@ -3216,7 +3216,7 @@ extern "C" int spr_renderer_memory_estimate(const spr_volume *vol, int width, in
     for (int a = 0; a < 3; ++a) ns *= (g.nc[a] + 3) / 4;
     const int64_t scan_items = std::max({tiled_ray_count(width, height) * n_views, slots, nwords, cap, act,
                                          (int64_t)1});
-    int64_t n = 16 * nwords + 4 * g.nblocks                        // block bitmaps, block -> slot
+    int64_t n = 12 * nwords + 4 * g.nblocks                        // block bitmaps, block -> slot
                 + 57 * np + 4 * (tiled_ray_count(width, height) * n_views / 32 + 1)   // per ray, bitmap
                 + 8 * (g.ncoarse + ns) * n_views                   // brick masks
                 + 269 * slots                                       // cache slots and their tables
