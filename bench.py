@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -124,7 +125,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples go to $SPR_CLOCKS_CSV (default: the temp directory)
+        self.path = os.environ.get("SPR_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                     "spr_clocks_bench.csv")
 
     def __enter__(self):
         try:
