@@ -63,6 +63,24 @@ WORKLOADS = {
 }
 
 
+def replica_pose_index(rank: int, i: int) -> int:
+    """Pose index of the i-th render of replica `rank`: every rank renders
+    its own sequence (the path shards by image with no exchange), offset by
+    1000 per rank so that no two ranks render the same pose."""
+    return rank * 1000 + i
+
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest value over the ranks of the process group (the job's time
+    is its slowest replica's); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -784,7 +802,7 @@ def main():
 
         def step(i):
             spr.spr_reset_cache(r)
-            spr.spr_set_camera(r, pose(wl, rank * 1000 + i))
+            spr.spr_set_camera(r, pose(wl, replica_pose_index(rank, i)))
             return spr.spr_render_to_convergence(r, 100000, stream=stream)
 
         # The timed loop calls the C ABI directly with camera arrays prepared
@@ -797,7 +815,7 @@ def main():
 
         class Timed:
             def __init__(self, n):
-                self.cams = [cam_args(pose(wl, rank * 1000 + args.warmup + i)) for i in range(n)]
+                self.cams = [cam_args(pose(wl, replica_pose_index(rank, args.warmup + i))) for i in range(n)]
                 self.rs = [_lib.RenderStats() for _ in range(n)]
                 self.per = [(_lib.PassStats * 64)() for _ in range(n)]
 
@@ -834,10 +852,7 @@ def main():
             dist.barrier()
         step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
         ms_image = statistics.mean(step_ms)
-        if dist:
-            t = torch.tensor([ms_image], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_image = float(t.item())
+        ms_image = max_over_ranks(ms_image, dist, device="cuda")
 
         # Per-stage device times: the same steps again with the library's
         # CUDA events between stages (host-driven passes, so the stage events
