@@ -875,6 +875,8 @@ def main():
             n_pass += rs["passes"]
             blocks += rs["blocks_decoded"]
             launches += rs["kernel_launches"]
+        per_index = {}          # pass index -> stage-sum ms of each instrumented render
+        isect_entries, isect_ms = 0, 0.0
         for rs, passes in prof_stats:
             for p in passes:
                 for k, n in enumerate(stage_names):
@@ -882,7 +884,13 @@ def main():
                 if p["n_decoded"]:
                     decode_launch_ms.append(p["ms_stage"][3])
                     decode_bytes.append(p["n_decoded"] * (8 * wl["rate"] + 256))
+                per_index.setdefault(p["pass"], []).append(p["ms"])
+                isect_entries += p["n_entries"]
+                isect_ms += p["ms_stage"][4]
         total_stage = sum(stage.values()) or 1.0
+        # ray-block tests per second: entries tested by the intersection,
+        # over its stage time and over the whole render
+        entries_per_image = sum(rs["entries"] for rs, _ in stats) / max(1, len(stats))
         pk = peaks()
         # the kernel-level stages with one kernel each: traverse, decode, intersect
         one_kernel = {"traverse": "traverse_kernel", "decode": "decode_list_kernel",
@@ -1043,6 +1051,13 @@ def main():
             "decoded_gbs": round(dec_gbs, 1),
             "images_per_s": round(1e3 / ms_image * world, 2),
             "stage_ms_per_image": {k: round(v / max(1, len(prof_stats)), 4) for k, v in stage.items()},
+            "ms_per_pass_index": {str(k): round(statistics.mean(v), 4) for k, v in sorted(per_index.items())},
+            "ray_block_tests_per_s": {
+                "intersect_stage": round(isect_entries / (isect_ms / 1e3), 1) if isect_ms > 0 else None,
+                "whole_render": round(entries_per_image / (ms_image / 1e3), 1),
+                "entries_per_image": round(entries_per_image, 1),
+                "timing": "entries of the instrumented renders over their intersection stage time; "
+                          "entries of the timed renders over their ms to the final image"},
             "roofline": roofline,
             "decode_all": {"kernel": "decode_list_kernel", "blocks": nb_all,
                            "ms": round(dec_all_ms, 4), "achieved": round(dec_all_gbs, 1),
