@@ -2502,6 +2502,7 @@ int read_state(spr_renderer *r, cudaStream_t s)
     if (h.error & 1u) return set_error(SPR_ERR_DEVICE_TIMEOUT, "a decoupled look-back wait timed out");
     if (h.error & 2u) return set_error(SPR_ERR_DEVICE_ERROR, "a kernel flagged an out-of-range block id");
     if (h.error & 4u) return set_error(SPR_ERR_DEVICE_ERROR, "a traversal exceeded its step bound");
+    if (h.error & 16u) return set_error(SPR_ERR_DEVICE_TIMEOUT, "a tensor-core wait of the speculation policy timed out");
     return SPR_OK;
 }
 

@@ -123,6 +123,13 @@ int same_shape_count(const spr_server *s, const PoolEntry *e)
 // wants, then (`any`) the rest.
 bool make_room(spr_server *s, size_t need, bool any)
 {
+    // release nothing unless releasing every eligible idle renderer would
+    // make room (otherwise warm caches would be lost for no admission)
+    size_t idle = 0;
+    for (PoolEntry *pe : s->pool)
+        if (!pe->busy && (any || same_shape_count(s, pe) >= 2 || !has_pending(s, pe->vol, pe->W, pe->H)))
+            idle += pe->bytes;
+    if (s->mem_used - std::min(s->mem_used, idle) + need > s->d.memory_bytes) return false;
     for (int round = 0; round < (any ? 3 : 2); ++round)
         while (s->mem_used + need > s->d.memory_bytes) {
             PoolEntry *lru = nullptr;
