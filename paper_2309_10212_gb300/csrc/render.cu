@@ -554,6 +554,7 @@ struct EnterEmit {
 // with spr_set_warp_walk_threshold) walk one ray per warp
 // (traverse_coop_kernel); larger passes one ray per thread (traverse_kernel).
 constexpr uint32_t kCoopBelowDefault = 16384;
+constexpr uint32_t kHalfWarpFrom = 4096;   // warp walks: a half warp per ray from this many rays
 
 __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__restrict__ live0,
                                                        const uint32_t *__restrict__ live1,
@@ -654,7 +655,8 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
     }
 }
 
-// One ray per warp, for passes whose few rays make the walk latency-bound.
+// One ray per warp or half warp, for passes whose few rays make the walk
+// latency-bound.
 // The walk is the same as traverse_kernel's; inside an occupied coarse cell
 // the blocks are found in one step instead of one by one.  Lane 4a + k - 1
 // (a < 3, k = 1..4) takes the k-th block-plane crossing of the ray along
@@ -667,6 +669,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
 // visible blocks of the cell are then taken in rank order, and the walk moves
 // to the block after T_exit.  Empty coarse and super cells are skipped with
 // skip_level, computed identically by all lanes.
+template <int LPR>
 __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_t *__restrict__ live0,
                                                             const uint32_t *__restrict__ live1,
                                                             const PassState *__restrict__ ps,
@@ -676,22 +679,33 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
                                                             uint32_t *vis_bits, uint32_t *act_bits,
                                                             uint32_t *ctr, Spec S)
 {
+    static_assert(LPR == 16 || LPR == 32, "16 or 32 lanes per ray");
     const VolGeom &g = P.g;
     const uint32_t nproc = ps->nproc;
     if (nproc >= ps->coop_below) return;
+    // a half warp per ray when there are enough rays to fill the GPU (the
+    // walk is then bound by instruction throughput), a whole warp per ray
+    // for the last few (bound by each walk's latency)
+    if ((LPR == 16) != (nproc >= kHalfWarpFrom)) return;
     const int kk = (int)ps->kk;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
     const int max_steps = 2 * (g.tb[0] + g.tb[1] + g.tb[2]) + 8;
     const uint32_t nb0 = g.nb[0], nb1 = g.nb[1], nc0 = g.nc[0], nc1 = g.nc[1];
     const uint32_t ns0 = P.occ.ns[0], ns1 = P.occ.ns[1];
+    // LPR lanes walk one ray: lanes 0-11 of the group take the crossings,
+    // lane LPR - 1 the current block; masks, ballots and shuffles stay within
+    // the group, so the two rays of a warp (LPR = 16) proceed independently
+    constexpr int kShift = LPR == 16 ? 4 : 5;
     const int lane = threadIdx.x & 31;
-    const bool elane = lane < 12;
-    const int ea = elane ? lane >> 2 : 0;   // axis of this lane's crossing
-    const int ek = (lane & 3) + 1;          // its number along that axis
-    const unsigned full = 0xFFFFFFFFu;
+    const int gl = lane & (LPR - 1);                   // lane within the group
+    const int gshift = LPR == 16 ? (lane & 16) : 0;    // the group's first lane
+    const unsigned full = LPR == 16 ? (0xFFFFu << gshift) : 0xFFFFFFFFu;
+    const bool elane = gl < 12;
+    const int ea = elane ? gl >> 2 : 0;     // axis of this lane's crossing
+    const int ek = (gl & 3) + 1;            // its number along that axis
     uint32_t tot_steps = 0, max_seen = 0;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nproc;
-         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> kShift; i < nproc;
+         i += ((int64_t)gridDim.x * blockDim.x) >> kShift) {
         const uint32_t ray = live[i];
         Walk w;
         int view, px, py;
@@ -717,9 +731,9 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
         }
         flags &= ~kStep;
         int steps = 0;
-        while (alive) {   // uniform across the warp: every lane holds the same walk
+        while (alive) {   // uniform across the group: every lane holds the same walk
             if (++steps > max_steps) {
-                if (lane == 0) atomicOr(&ctr[C_BAD], 2u);
+                if (gl == 0) atomicOr(&ctr[C_BAD], 2u);
                 alive = false;
                 break;
             }
@@ -800,8 +814,7 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
                     }
                 }
             }
-            const unsigned repm = __ballot_sync(full, valid && rep);
-            const unsigned repi = __ballot_sync(full, interior && rep);
+            const unsigned repm = __ballot_sync(full, valid && rep) >> gshift;
             const unsigned ltm = ((1u << clt[0]) - 1u) | (((1u << clt[1]) - 1u) << 4) | (((1u << clt[2]) - 1u) << 8);
             const int rank = __popc(repm & ltm);
             int nbk[3];
@@ -811,7 +824,7 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
             // block after an interior crossing
             bool vis = false;
             int pos = 0, bb[3] = {b[0], b[1], b[2]};
-            if (lane == 31) {
+            if (gl == LPR - 1) {
                 vis = (fmask >> ((b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) & 1ull;
             } else if (interior && rep) {
                 pos = rank + 1;
@@ -838,18 +851,18 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
             }
             cnt += take;
             if (take == need) {   // k blocks taken: stop on the last one
-                const int src = __ffs(__ballot_sync(full, idx == take - 1)) - 1;
+                const int src = __ffs(__ballot_sync(full, idx == take - 1) >> gshift) - 1;
 #pragma unroll
-                for (int a2 = 0; a2 < 3; ++a2) w.b[a2] = __shfl_sync(full, bb[a2], src);
+                for (int a2 = 0; a2 < 3; ++a2) w.b[a2] = __shfl_sync(full, bb[a2], src, LPR);
                 flags |= kStep;
                 break;
             }
             // on to the block after T_exit (the lowest axis crossing then)
-            const int src = __ffs(__ballot_sync(full, valid && rep && !interior)) - 1;
+            const int src = __ffs(__ballot_sync(full, valid && rep && !interior) >> gshift) - 1;
             bool inside = true;
 #pragma unroll
             for (int a2 = 0; a2 < 3; ++a2) {
-                w.b[a2] = __shfl_sync(full, nbk[a2], src);
+                w.b[a2] = __shfl_sync(full, nbk[a2], src, LPR);
                 if (w.b[a2] < 0 || w.b[a2] >= g.tb[a2]) inside = false;
             }
             if (!inside) {
@@ -860,14 +873,14 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
             for (int a2 = 0; a2 < 3; ++a2) set_axis(w, g, a2);
         }
         if (!alive) flags |= kDone;
-        for (int j = cnt + lane; j < ki; j += 32) out[j] = kNone;
-        if (lane == 0) {
+        for (int j = cnt + gl; j < ki; j += LPR) out[j] = kNone;
+        if (gl == 0) {
             state_out[ray] = pack_state(w.b, flags);
             tot_steps += (uint32_t)steps;
             max_seen = max(max_seen, (uint32_t)steps);
         }
     }
-    if (lane == 0) {
+    if (gl == 0) {
         if (tot_steps) atomicAdd(&ctr[C_STEPS], tot_steps);
         if (max_seen) atomicMax(&ctr[C_MAXSTEPS], max_seen);
     }
@@ -2366,7 +2379,11 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
         make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
         r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
     count_launch();
-    traverse_coop_kernel<<<device_sm_count() * 16, 128, 0, s>>>(
+    traverse_coop_kernel<32><<<device_sm_count() * 16, 128, 0, s>>>(
+        make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
+        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
+    count_launch();
+    traverse_coop_kernel<16><<<device_sm_count() * 16, 128, 0, s>>>(
         make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
         r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
     count_launch();
