@@ -156,8 +156,15 @@ int spr_count_active_blocks(const spr_volume *vol, float iso, int64_t *n_active,
 /* Per-ray speculation: every live ray takes its own count k_i in [1, k_max]
  * each pass (the paper's future work, Sec. 6: a per-ray speculation count).
  * The image does not depend on the counts; only the passes and the blocks
- * decoded do. */
-#define SPR_SPEC_HASHED   2   /* k_i = 1 + hash(ray, pass) mod k_max: a model-free per-ray count */
+ * decoded do.  Every attempt of a pass caps k_i by kk, which starts at k_max
+ * and halves when the pass overflows the cache, as k does in the rules above.
+ *
+ * SPR_SPEC_HASHED, a model-free per-ray count: in pass P (1-based), the ray
+ * with id q (view * w*h + y*w + x) takes k_i = min(kk, 1 + (h mod k_max)),
+ * where, in unsigned 32-bit arithmetic,
+ *     h  = (q * 0x9E3779B1) ^ (P * 0x85EBCA77);
+ *     h ^= h >> 15;  h *= 0x2C1B3C6D;  h ^= h >> 12; */
+#define SPR_SPEC_HASHED   2   /* k_i from the hash of (ray, pass) above                  */
 #define SPR_SPEC_LEARNED  3   /* k_i from the renderer's policy MLP (spr_set_policy)              */
 #define SPR_K_LIMIT       4096
 #define SPR_K_PER_RAY_LIMIT 64

@@ -69,7 +69,7 @@ STATS_DTYPE = np.dtype([("pass", "<i4"), ("n_active", "<i8"), ("k", "<i4"), ("k_
 
 AMB_FACE, AMB_VALUE, AMB_TANGENT, AMB_SHALLOW = 1, 2, 4, 8
 AMB_INTERNAL = 0x10000
-SPEC_FIXED, SPEC_ADAPTIVE = 0, 1
+SPEC_FIXED, SPEC_ADAPTIVE, SPEC_PER_RAY = 0, 1, 2
 
 
 class _Camera(ctypes.Structure):
@@ -112,7 +112,7 @@ def lib():
                 ("orc_entry_block", [vp, vp, i32, i32, i32, i32], ctypes.c_uint32),
                 ("orc_march", [vp, vp, i32, i32, ctypes.c_float, vp, i64, vp, i32], i32),
                 ("orc_simulate", [i32, i32, vp, vp, vp, vp, vp, vp, i32, i32, i32, i64, i32,
-                                  vp, vp], i32),
+                                  vp, vp, vp], i32),
                 ("orc_spec_count", [i64, i64, i32], i32),
                 ("orc_sizeof_pixel", [], i32),
                 ("orc_sizeof_pass_stats", [], i32),
@@ -372,11 +372,18 @@ def spec_count(slots: int, n_active: int, k_max: int = 64) -> int:
 
 
 def simulate(W, H, dims, pix, vis_off, vis, spec_mode=SPEC_ADAPTIVE, k=1, k_max=64,
-             n_slots=None, max_passes=10000):
+             n_slots=None, max_passes=10000, kray=None):
     """Progressive pass simulation from a cold cache.  `pix`, `vis_off`, `vis`
-    come from render(..., lists=True) over all pixels in order.  Returns
-    (stats array, final_pass per pixel)."""
+    come from render(..., lists=True) over all pixels in order.  With
+    spec_mode SPEC_PER_RAY, kray[P-1, p] is pixel p's own count in pass P
+    (capped by k_max, which halves on cache overflow), and at most
+    kray.shape[0] passes run.  Returns (stats array, final_pass per pixel)."""
     assert pix.size == W * H
+    kr = None
+    if spec_mode == SPEC_PER_RAY:
+        kr = np.ascontiguousarray(kray, dtype=np.int32)
+        assert kr.ndim == 2 and kr.shape[1] == W * H
+        max_passes = min(max_passes, kr.shape[0])
     if n_slots is None:
         nb = nblocks(dims)
         n_slots = max(8, nb[0] * nb[1] * nb[2])
@@ -390,7 +397,8 @@ def simulate(W, H, dims, pix, vis_off, vis, spec_mode=SPEC_ADAPTIVE, k=1, k_max=
     final = np.zeros(W * H, dtype=np.int32)
     n = lib().orc_simulate(W, H, _ptr(_dims(dims)), _ptr(enters), _ptr(hit_index), _ptr(off),
                            _ptr(n_vis), _ptr(v), spec_mode, k, k_max, int(n_slots),
-                           max_passes, _ptr(stats), _ptr(final))
+                           max_passes, _ptr(kr) if kr is not None else None, _ptr(stats),
+                           _ptr(final))
     if n < 0:
         raise ValueError("orc_simulate failed: %d" % n)
     return stats[:n].copy(), final

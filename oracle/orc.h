@@ -206,6 +206,7 @@ int orc_march(const orc_volume *vol, const orc_camera *cam, int W, int H, float 
 /* ------------------------------------------------------------------ */
 #define ORC_SPEC_FIXED    0
 #define ORC_SPEC_ADAPTIVE 1
+#define ORC_SPEC_PER_RAY  2   /* each ray's own count per pass, from a table */
 
 typedef struct {
     int32_t  pass;
@@ -230,6 +231,7 @@ int orc_simulate(int W, int H, const int32_t dims[3],
                  const int32_t *enters, const int32_t *hit_index,
                  const int64_t *vis_off, const int32_t *n_vis, const uint32_t *vis,
                  int spec_mode, int k, int k_max, int64_t n_slots, int max_passes,
+                 const int32_t *kray /* ORC_SPEC_PER_RAY: [max_passes][W*H] counts, else NULL */,
                  orc_pass_stats *stats /* max_passes */, int32_t *final_pass /* W*H or NULL */);
 
 /* speculation count of Sec. 4: min(k_max, floor(slots / n_active)), at least 1 */

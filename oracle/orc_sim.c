@@ -15,7 +15,11 @@
  *       without one (Sec. 4.4);
  *   (f) the remaining rays form the next pass's live list, in the order of
  *       the first live list.
- * k is the fixed count, or floor(w*h / N_Act) capped at k_max (Sec. 4).
+ * k is the fixed count, or floor(w*h / N_Act) capped at k_max (Sec. 4), or,
+ * for the per-ray count of Sec. 6's future work, ray p's own count in pass P
+ * taken from a given table, capped by the pass's k_max (halved on overflow
+ * like k); a ray that gets fewer blocks than its own count has left the
+ * volume.
  *
  * Choices where the paper is silent (the cache of Sec. 3.5 grows instead):
  *   - LRU victims are the slots not used in this pass, ordered by the pass
@@ -58,6 +62,15 @@ static int cmp_lru(const void *a, const void *b)
     return (x->slot > y->slot) - (x->slot < y->slot);
 }
 
+/* ray p's count this attempt: the pass's k, or its own count (at least 1)
+ * capped by it */
+static int64_t ray_count(const int32_t *kp, int64_t p, int64_t kk)
+{
+    if (!kp) return kk;
+    int64_t c = kp[p] < 1 ? 1 : kp[p];
+    return c < kk ? c : kk;
+}
+
 /* sort and drop duplicates */
 static int64_t uniq(uint32_t *v, int64_t n)
 {
@@ -72,10 +85,11 @@ static int64_t uniq(uint32_t *v, int64_t n)
 int orc_simulate(int W, int H, const int32_t dims[3], const int32_t *enters,
                  const int32_t *hit_index, const int64_t *vis_off, const int32_t *n_vis,
                  const uint32_t *vis, int spec_mode, int k_fixed, int k_max, int64_t n_slots,
-                 int max_passes, orc_pass_stats *stats, int32_t *final_pass)
+                 int max_passes, const int32_t *kray, orc_pass_stats *stats, int32_t *final_pass)
 {
     int64_t npix = (int64_t)W * H;
     if (n_slots < 8 || k_fixed < 1 || k_max < 1) return -1;
+    if (spec_mode == ORC_SPEC_PER_RAY && !kray) return -1;
     int64_t nb[3] = { (dims[0] + 3) / 4, (dims[1] + 3) / 4, (dims[2] + 3) / 4 };
     int64_t nblocks = nb[0] * nb[1] * nb[2];
     /* a cache with at least one slot per block never evicts; more slots than
@@ -111,7 +125,10 @@ int orc_simulate(int W, int H, const int32_t dims[3], const int32_t *enters,
         memset(&st, 0, sizeof st);
         st.pass = pass;
         st.n_active = n_live;
-        int k = spec_mode == ORC_SPEC_FIXED ? k_fixed : orc_spec_count(npix, n_live, k_max);
+        int k = spec_mode == ORC_SPEC_FIXED      ? k_fixed
+                : spec_mode == ORC_SPEC_PER_RAY ? k_max
+                                                : orc_spec_count(npix, n_live, k_max);
+        const int32_t *kp = spec_mode == ORC_SPEC_PER_RAY ? kray + (int64_t)(pass - 1) * npix : NULL;
         st.k = k;
         int kk = k;
         int64_t nproc = n_live, nvis = 0, nact = 0;
@@ -120,8 +137,8 @@ int orc_simulate(int W, int H, const int32_t dims[3], const int32_t *enters,
             /* (a)+(b): entries, visible and active sets */
             int64_t cap = 0;
             for (int64_t i = 0; i < nproc; i++) {
-                int64_t p = live[i], avail = n_vis[p] - pos[p];
-                cap += avail < kk ? avail : kk;
+                int64_t p = live[i], avail = n_vis[p] - pos[p], kr = ray_count(kp, p, kk);
+                cap += avail < kr ? avail : kr;
             }
             free(vis_set);
             free(act_set);
@@ -129,8 +146,8 @@ int orc_simulate(int W, int H, const int32_t dims[3], const int32_t *enters,
             act_set = malloc(sizeof(uint32_t) * (8 * cap + 1));
             nvis = 0;
             for (int64_t i = 0; i < nproc; i++) {
-                int64_t p = live[i], avail = n_vis[p] - pos[p];
-                int64_t take = avail < kk ? avail : kk;
+                int64_t p = live[i], avail = n_vis[p] - pos[p], kr = ray_count(kp, p, kk);
+                int64_t take = avail < kr ? avail : kr;
                 for (int64_t j = 0; j < take; j++) vis_set[nvis++] = vis[vis_off[p] + pos[p] + j];
             }
             st.n_entries = nvis;
@@ -195,12 +212,12 @@ int orc_simulate(int W, int H, const int32_t dims[3], const int32_t *enters,
                 next[n_next++] = p;
                 continue;
             }
-            int64_t avail = n_vis[p] - pos[p];
-            int64_t take = avail < kk ? avail : kk;
+            int64_t avail = n_vis[p] - pos[p], kr = ray_count(kp, p, kk);
+            int64_t take = avail < kr ? avail : kr;
             if (hit_index[p] >= 0 && hit_index[p] < pos[p] + take) {
                 st.n_term_hit++;
                 if (final_pass) final_pass[p] = pass;
-            } else if (take < kk) {
+            } else if (take < kr) {
                 st.n_term_miss++;
                 if (final_pass) final_pass[p] = pass;
             } else {

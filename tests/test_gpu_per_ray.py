@@ -9,7 +9,7 @@ import pytest
 
 import synth
 from test_gpu_batch import render_batch, views_of
-from test_gpu_render import compare, value_scene
+from test_gpu_render import check_counters, compare, value_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -69,6 +69,45 @@ def test_hashed_counts_both_walks(spr, orc, warp_walk):
         assert np.array_equal(a[key], b[key]), key
     keys = ("n_active", "n_entries", "n_visible", "n_requested", "n_decoded", "n_term_hit", "n_term_miss")
     assert [[p[k] for k in keys] for p in pa] == [[p[k] for k in keys] for p in pb]
+
+
+def hashed_counts(npix, passes, k_max):
+    """The counts SPR_SPEC_HASHED draws, written from the definition in
+    spr.h (unsigned 32-bit arithmetic): row P-1 holds pass P's count of every
+    ray, before the overflow cap."""
+    m = np.uint64(0xFFFFFFFF)
+    q = np.arange(npix, dtype=np.uint64)
+    rows = []
+    for P in range(1, passes + 1):
+        h = ((q * np.uint64(0x9E3779B1)) & m) ^ np.uint64((P * 0x85EBCA77) & 0xFFFFFFFF)
+        h ^= h >> np.uint64(15)
+        h = (h * np.uint64(0x2C1B3C6D)) & m
+        h ^= h >> np.uint64(12)
+        rows.append(1 + (h % np.uint64(k_max)).astype(np.int64))
+    return np.stack(rows).astype(np.int32)
+
+
+@pytest.mark.parametrize("k_max,slots", [(9, None), (64, None), (24, 60), (48, 120)])
+def test_hashed_counters_match_pass_simulator(spr, orc, k_max, slots):
+    """Every per-pass counter, each pixel's final pass and the blocks decoded
+    equal the oracle's pass simulator fed the same per-ray counts, with a
+    cache that holds every block and with caches that overflow (the cap
+    halves, then the ray window does)."""
+    sc = value_scene(orc, (48, 40, 44), 21, 80, 64, rate=4, q=0.62, lists=True)
+    assert np.all(sc.pix["amb"] == 0), "counters are compared on a clear scene"
+    fb, rs, passes = render(spr, sc, spr.SPR_SPEC_HASHED, k_max=k_max, slots=slots)
+    compare(sc, fb)
+    sim = dict(spec_mode=orc.SPEC_PER_RAY, k_max=k_max,
+               kray=hashed_counts(sc.W * sc.H, 1000, k_max))
+    if slots:
+        sim["n_slots"] = slots
+    st, final = orc.simulate(sc.W, sc.H, sc.dims, sc.pix, sc.off, sc.vis, **sim)
+    assert len(st) < 1000
+    check_counters(st, passes)
+    assert np.array_equal(fb["final_pass"], final)
+    assert rs["blocks_decoded"] == int(st["n_decoded"].sum())
+    if slots:
+        assert st["retries"].sum() > 0
 
 
 def test_per_ray_k1_equals_fixed_k1(spr, orc):

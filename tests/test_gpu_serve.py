@@ -138,13 +138,16 @@ def run_service(spr, reqs, memory_bytes, cache_slots, max_inflight, max_batch, s
                 results[res["id"]] = res
         rid = spr.spr_server_submit(srv, vols[vi][1], sc.cam, sc.iso, sc.W, sc.H, outputs=o)
         assert rid == i
+    inflight_peak = 0
     while len(results) < len(reqs):
         for res in spr.spr_server_poll(srv):
             results[res["id"]] = res
         info = spr.spr_server_info(srv)
         peak = max(peak, info["memory_used"])
+        inflight_peak = max(inflight_peak, info["in_flight"])
         assert info["in_flight"] <= max_inflight
     info = spr.spr_server_info(srv)
+    info["inflight_peak"] = inflight_peak
     torch.cuda.synchronize()
     srv.close()
     for v, _ in vols.values():
@@ -166,6 +169,13 @@ def test_service_results_equal_alone(spr, orc, max_inflight, max_batch):
         assert max(batches) == 1
     else:
         assert max(batches) > 1      # queued requests of one volume and size were merged
+    if max_inflight > 1:
+        # renders overlapped: several were on the device at once, and a
+        # request was admitted while an earlier one was still running
+        assert info["inflight_peak"] >= 2
+        assert any(results[j]["t_admit"] < results[i]["t_done"]
+                   for i in range(len(reqs)) for j in range(len(reqs))
+                   if results[j]["t_admit"] > results[i]["t_admit"])
     for i, (vi, sc) in enumerate(reqs):
         res = results[i]
         assert res["status"] == 0

@@ -113,3 +113,75 @@ def test_tight_cache_splits_passes(orc):
     assert tight["n_term_hit"].sum() == full["n_term_hit"].sum()
     assert tight["n_decoded"].sum() >= full["n_decoded"].sum()
     assert tight["n_evicted"].sum() > 0
+
+
+def test_per_ray_counts_worked_example(orc):
+    """Per-ray counts (Sec. 6's per-ray speculation count) on the Fig. 3 rays,
+    worked by hand: rays 2 and 3 take one block and hit; ray 4 takes three
+    and hits in its third; ray 5 takes one per pass and hits in its third
+    block in pass 3."""
+    W, H = 6, 1
+    lists = {2: [5], 3: [6], 4: [10, 11, 12], 5: [20, 21, 22, 23]}
+    hits = {2: 0, 3: 0, 4: 2, 5: 2}
+    pix, off, vis = make_lists(W, H, lists, hits)
+    kray = np.ones((8, W), np.int32)
+    kray[:, 4] = 3
+    st, final = orc.simulate(W, H, (16, 16, 16), pix, off, vis, spec_mode=orc.SPEC_PER_RAY,
+                             k_max=4, kray=kray)
+    assert list(final) == [0, 0, 1, 1, 1, 3]
+    assert list(st["n_entries"]) == [6, 1, 1]
+    assert list(st["n_active"]) == [4, 1, 1]
+    assert list(st["k"]) == [4, 4, 4]
+    # unique visible blocks: {5, 6, 10, 11, 12, 20}, then {21}, then {22}
+    assert list(st["n_visible"]) == [6, 1, 1]
+    # the count is capped by k_max: with k_max = 1 ray 4 needs three passes
+    st1, final1 = orc.simulate(W, H, (16, 16, 16), pix, off, vis, spec_mode=orc.SPEC_PER_RAY,
+                               k_max=1, kray=kray)
+    assert list(final1) == [0, 0, 1, 1, 3, 3]
+
+
+def test_per_ray_uniform_counts_equal_fixed(orc):
+    """Every ray taking the same count c is the fixed rule with k = c."""
+    dims = (32, 28, 30)
+    W = H = 32
+    pix, off, vis = _scene(orc, dims, 32, W, H)
+    for c in (1, 3, 8):
+        fixed, ff = orc.simulate(W, H, dims, pix, off, vis, spec_mode=orc.SPEC_FIXED, k=c)
+        kray = np.full((len(fixed) + 1, W * H), c, np.int32)
+        per, fp = orc.simulate(W, H, dims, pix, off, vis, spec_mode=orc.SPEC_PER_RAY,
+                               k_max=c, kray=kray)
+        assert np.array_equal(fixed, per) and np.array_equal(ff, fp)
+
+
+def test_per_ray_counts_closed_form(orc):
+    """With a cache that never overflows, each ray is on its own: with
+    cumulative counts C_P = k_1 + ... + k_P it finishes in the first pass
+    where C_P > its hit index (a hit) or where its remaining list is shorter
+    than its count (it left the volume), and takes min(count, remaining)
+    entries in every pass until then."""
+    dims = (32, 28, 30)
+    W = H = 32
+    pix, off, vis = _scene(orc, dims, 33, W, H)
+    rng = np.random.default_rng(5)
+    P = 200
+    kray = rng.integers(1, 10, size=(P, W * H)).astype(np.int32)
+    st, final = orc.simulate(W, H, dims, pix, off, vis, spec_mode=orc.SPEC_PER_RAY,
+                             k_max=9, kray=kray)
+    entries = np.zeros(P, np.int64)
+    want = np.zeros(W * H, np.int32)
+    for p in np.nonzero(pix["enters"])[0]:
+        nv = int(pix["n_visible"][p])
+        hi = int(pix["hit_index"][p]) if pix["hit"][p] else -1
+        pos = 0
+        for q in range(P):
+            c = int(kray[q, p])
+            take = min(c, nv - pos)
+            entries[q] += take
+            if (hi >= 0 and hi < pos + take) or take < c:
+                want[p] = q + 1
+                break
+            pos += take
+    assert np.array_equal(final, want)
+    assert np.array_equal(st["n_entries"], entries[:len(st)])
+    assert entries[len(st):].sum() == 0
+    assert st["retries"].sum() == 0 and st["n_evicted"].sum() == 0
