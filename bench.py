@@ -716,6 +716,47 @@ def run_serve(args):
     return 0
 
 
+def run_decode_slab(args):
+    """Decode rate of the blocks the paper-scale render decodes: a slab of the
+    2048x2048x1920 mixing layer at its interface (z = 928..959, 2 bits/value,
+    2,097,152 blocks), every block decoded in one spr_decode_blocks call,
+    timed with CUDA events (median of --steps calls, L2 written between
+    them).  Prints one JSON line."""
+    import torch
+
+    from paper_2309_10212_gb300 import build
+    build.build()
+    import paper_2309_10212_gb300 as spr
+    import synth
+    dims, z0, z1, rate = (2048, 2048, 1920), 928, 960, 2
+    u8 = synth.volumes.mixing_layer_slab(dims, z0, z1, synth.volumes.mixing_layer_params(3, scale=1.0),
+                                         z_mid=960.0, device="cuda")
+    comp = spr.spr_encode_u8(u8, rate)
+    del u8
+    nb = comp.numel() // (8 * rate)
+    out = torch.empty((nb, 64), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ts = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(i & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        spr.spr_decode_blocks(comp, nb, rate, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    pk = peaks()
+    gbs = nb * (8 * rate + 256) / (ms / 1e3) / 1e9
+    print(json.dumps({"decode_slab": "mixing layer 2048x2048x1920, z %d..%d, %d bits/value" % (z0, z1 - 1, rate),
+                      "kernel": "decode_list_kernel", "blocks": nb, "ms": round(ms, 4),
+                      "gblocks_per_s": round(nb / ms / 1e6, 3), "achieved_gbs": round(gbs, 1),
+                      "peak_gbs": pk["hbm_gbs"], "frac": round(gbs / pk["hbm_gbs"], 4),
+                      "timing": "median of %d CUDA-event timed calls, L2 written before each" % len(ts)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -740,6 +781,9 @@ def main():
     ap.add_argument("--learn-mod", type=int, default=16)
     ap.add_argument("--learn-samples", type=int, default=24 << 20)
     ap.add_argument("--learn-epochs", type=int, default=8)
+    ap.add_argument("--decode-slab", action="store_true",
+                    help="instead of the bench line: the decode rate of the paper-scale field's "
+                         "interface blocks (one JSON line)")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--warp-walk", type=int, default=-1,
@@ -759,6 +803,8 @@ def main():
         return run_serve(args)
     if args.learned:
         return run_learned(args, wl)
+    if args.decode_slab:
+        return run_decode_slab(args)
     if args.warmup < 3:
         args.warmup = 3
 

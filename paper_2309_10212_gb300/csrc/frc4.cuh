@@ -74,6 +74,11 @@ __device__ __forceinline__ RegBits load_reg_bits(const uint8_t *blk, int rate)
     return b;
 }
 
+// Set bit p of a coefficient word in shared memory with an atomic OR: the
+// thread issues it and moves on, where a load-or-store sequence would wait
+// for the load of every set bit (no other thread touches the word).
+__device__ __forceinline__ void set_bit_of(uint32_t *w, int p) { atomicOr(w, 1u << p); }
+
 // Parse one block.  col[k * stride] receives the negabinary value of the k-th
 // coefficient in sequency order (stride 1: col is 16-byte aligned).  Returns
 // false for an all-zero block.
@@ -102,7 +107,7 @@ __device__ __forceinline__ bool decode_coeffs(const Bits &bits_at, int rate, uin
             while (bits) {
                 int i = __ffs(bits) - 1;
                 bits &= bits - 1;
-                col[(base + i) * stride] |= 1u << p;
+                set_bit_of(col + (base + i) * stride, p);
             }
         }
         pos += m;
@@ -129,7 +134,7 @@ __device__ __forceinline__ bool decode_coeffs(const Bits &bits_at, int rate, uin
             pos += used;
             budget -= used;
             n += used;
-            if (found) col[(n - 1) * stride] |= 1u << p;
+            if (found) set_bit_of(col + (n - 1) * stride, p);
         }
     }
     return true;
