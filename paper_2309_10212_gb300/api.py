@@ -201,6 +201,13 @@ class Renderer:
         self.handle = handle
         self.vol = vol
         self.W, self.H = W, H
+        self._recs = None   # per-pass record buffer, reused across renders
+
+    def records(self, n: int):
+        """A ctypes array of at least n pass records (kept between calls)."""
+        if self._recs is None or len(self._recs) < n:
+            self._recs = (_lib.PassStats * n)()
+        return self._recs
 
     def close(self):
         if self.handle:
@@ -276,7 +283,7 @@ def spr_render_to_convergence(r: Renderer, max_passes: int = 10000, stream=None,
                               allow_partial: bool = False):
     """Returns (render stats, [pass stats])."""
     rs = _lib.RenderStats()
-    per = (_lib.PassStats * min(max_passes, 4096))()
+    per = r.records(min(max_passes, 4096))
     status = load().spr_render_to_convergence(r.handle, _stream(stream), int(max_passes),
                                               ctypes.byref(rs), per)
     if not (allow_partial and status == _lib.SPR_ERR_NOT_CONVERGED):
@@ -332,7 +339,7 @@ def spr_render_query(r: Renderer):
 def spr_render_collect(r: Renderer, allow_partial: bool = False):
     """Wait for the submitted render; returns (render stats, [pass stats])."""
     rs = _lib.RenderStats()
-    per = (_lib.PassStats * 4096)()
+    per = r.records(4096)
     status = load().spr_render_collect(r.handle, ctypes.byref(rs), per)
     if not (allow_partial and status == _lib.SPR_ERR_NOT_CONVERGED):
         check(status)

@@ -74,10 +74,16 @@ __device__ __forceinline__ RegBits load_reg_bits(const uint8_t *blk, int rate)
     return b;
 }
 
-// Set bit p of a coefficient word in shared memory with an atomic OR: the
-// thread issues it and moves on, where a load-or-store sequence would wait
-// for the load of every set bit (no other thread touches the word).
-__device__ __forceinline__ void set_bit_of(uint32_t *w, int p) { atomicOr(w, 1u << p); }
+// Set bit p of a coefficient word in shared memory.  In a row (stride 1,
+// decode_list_kernel) with an atomic OR: the thread issues it and moves on,
+// where a load-or-store sequence would wait for the load of every set bit
+// (no other thread touches the word).  In the strided columns of the range
+// pass the atomics measured 5.6x slower than the load-or-store.
+__device__ __forceinline__ void set_bit_of(uint32_t *w, int p, int stride)
+{
+    if (stride == 1) atomicOr(w, 1u << p);
+    else *w |= 1u << p;
+}
 
 // Parse one block.  col[k * stride] receives the negabinary value of the k-th
 // coefficient in sequency order (stride 1: col is 16-byte aligned).  Returns
@@ -107,7 +113,7 @@ __device__ __forceinline__ bool decode_coeffs(const Bits &bits_at, int rate, uin
             while (bits) {
                 int i = __ffs(bits) - 1;
                 bits &= bits - 1;
-                set_bit_of(col + (base + i) * stride, p);
+                set_bit_of(col + (base + i) * stride, p, stride);
             }
         }
         pos += m;
@@ -134,7 +140,7 @@ __device__ __forceinline__ bool decode_coeffs(const Bits &bits_at, int rate, uin
             pos += used;
             budget -= used;
             n += used;
-            if (found) set_bit_of(col + (n - 1) * stride, p);
+            if (found) set_bit_of(col + (n - 1) * stride, p, stride);
         }
     }
     return true;

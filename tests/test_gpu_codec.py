@@ -109,6 +109,26 @@ def test_decode_medium_workload_volume(spr, orc):
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
 
 
+def test_decode_mixing_layer_interface_blocks(spr, orc):
+    """The blocks a paper-scale render decodes most: the interface of the
+    2048x2048x1920 mixing layer (z = 956..963, full-scale generator, 2
+    bits/value, 524,288 blocks), whose parses are the longest; encoder and
+    decoder against the oracle, bit for bit."""
+    dims = (2048, 2048, 1920)
+    u8 = synth.volumes.mixing_layer_slab(dims, 956, 964, synth.volumes.mixing_layer_params(3),
+                                         z_mid=960.0, device="cuda")
+    sdims = (2048, 2048, 8)
+    comp = orc.encode_volume(u8.cpu().numpy(), sdims, 2)
+    gpu_comp = spr.spr_encode_u8(u8, 2).cpu().numpy()
+    assert np.array_equal(gpu_comp, comp)
+    got = _decode_as_volume(spr, comp, sdims, 2)
+    want = orc.decode_volume(comp, sdims, 2)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    # the slab holds the interface: a third of its blocks are not constant
+    b = u8.cpu().numpy().reshape(2, 4, 512, 4, 512, 4).transpose(0, 2, 4, 1, 3, 5).reshape(-1, 64)
+    assert np.mean(b.max(axis=1) != b.min(axis=1)) > 0.2
+
+
 @pytest.mark.parametrize("dims", [(16, 16, 16), (21, 13, 9), (65, 33, 18), (64, 64, 64)])
 def test_range_grids_match_oracle(spr, orc, dims):
     vol = synth.volumes.value_noise(dims, seed=9, ref=max(dims))
