@@ -1,0 +1,45 @@
+"""The JSON contract of bench.py's reference arm, on CPU: the oracle timed on
+the host cores for the small workload prints one line with the metric, the
+value, its CPU-baseline record and the e2e record; the paper-scale workload,
+which the oracle cannot hold decoded, prints an `unavailable` line; a rank
+other than 0 prints nothing."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def run(args, env_extra=None):
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    return [json.loads(line) for line in p.stdout.splitlines() if line.startswith("{")]
+
+
+def test_reference_arm_line():
+    lines = run(["--impl", "reference", "--workload", "small", "--steps", "2", "--warmup", "1"])
+    assert len(lines) == 1
+    d = lines[0]
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "ms"
+    assert d["higher_is_better"] is False and d["steps"] == 2 and d["warmup"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] == d["value"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == bench.WORKLOADS["small"]["name"]
+
+
+def test_reference_arm_paper_scale_unavailable():
+    lines = run(["--impl", "reference", "--workload", "paper", "--steps", "1", "--warmup", "0"])
+    assert len(lines) == 1 and lines[0]["impl"] == "reference" and lines[0]["unavailable"]
+
+
+def test_reference_arm_other_ranks_are_silent():
+    lines = run(["--impl", "reference", "--workload", "small", "--steps", "1", "--warmup", "0"],
+                {"RANK": "1", "WORLD_SIZE": "2"})
+    assert lines == []
