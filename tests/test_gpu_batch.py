@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from test_gpu_render import Scene, compare
+from test_gpu_render import Scene, check_counters, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -25,14 +25,27 @@ def spr():
     return m
 
 
-def views_of(orc, dims, seed, n, W, H, isos):
+def views_of(orc, dims, seed, n, W, H, isos, lists=False):
     vol = synth.volumes.value_noise(dims, seed=seed, ref=max(dims))
     scenes = []
     for v in range(n):
         iso = float(np.float32(np.quantile(vol, isos[v % len(isos)])))
         cam = synth.cameras.random_pose(dims, seed=seed + 10 * v + 1, W=W, H=H, distance_factor=1.6)
-        scenes.append(Scene(orc, dims, vol, 8, iso, cam, W, H))
+        scenes.append(Scene(orc, dims, vol, 8, iso, cam, W, H, lists=lists))
     return scenes
+
+
+def stacked(scenes):
+    """The views as one image of W x (H * views) pixels for the oracle's pass
+    simulator: pixel p of view v is ray v * W * H + p, as in the renderer,
+    and with H a multiple of 4 the screen tiles come in the renderer's order
+    (view by view)."""
+    pix = np.concatenate([s.pix for s in scenes])
+    offs, base = [], 0
+    for s in scenes:
+        offs.append(s.off + base)
+        base += s.vis.size
+    return pix, np.concatenate(offs), np.concatenate([s.vis for s in scenes])
 
 
 def render_batch(spr, scenes, slots=None, **spec):
@@ -158,3 +171,26 @@ def test_view_count_within_capacity(spr, orc):
         assert spr.spr_renderer_memory(r) == mem
     r.close()
     v.close()
+
+
+@pytest.mark.parametrize("spec,sim,slots", [(dict(mode="fixed", k=3), dict(spec_mode=0, k=3), None),
+                                            (dict(k_max=64), dict(spec_mode=1, k_max=64), None),
+                                            (dict(k_max=64), dict(spec_mode=1, k_max=64), 40)])
+def test_batch_counters_match_pass_simulator(spr, orc, spec, sim, slots):
+    """Three views with two isovalues in one wavefront: every per-pass counter
+    and every pixel's final pass equal the oracle's pass simulator run on the
+    views stacked into one image (one live list, one speculation budget of
+    views x W x H, one cache)."""
+    scenes = views_of(orc, (40, 36, 32), 7, 3, 64, 48, (0.4, 0.6), lists=True)
+    assert all(np.all(s.pix["amb"] == 0) for s in scenes), "counters are compared on clear scenes"
+    batch, rs, passes = render_batch(spr, scenes, slots=slots, **spec)
+    pix, off, vis = stacked(scenes)
+    W, H = scenes[0].W, scenes[0].H
+    if slots:
+        sim = dict(sim, n_slots=slots)
+    st, final = orc.simulate(W, H * len(scenes), scenes[0].dims, pix, off, vis, **sim)
+    check_counters(st, passes)
+    assert np.array_equal(np.concatenate([fb["final_pass"] for fb in batch]), final)
+    assert rs["blocks_decoded"] == int(st["n_decoded"].sum())
+    if slots:
+        assert st["retries"].sum() > 0
