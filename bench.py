@@ -8,11 +8,13 @@ ray is live -- of one camera pose from a cold block cache, on a volume that is
 already resident in device memory.  Poses cycle through the workload's orbit.
 
 Workloads (synthetic stand-ins for the paper's data sets, see synth/):
-  medium (default)  512^3 u8 Gaussian blobs + 10% noise, 2 bits/value, iso 0.3,
-                    1280x720, 16-pose orbit, cache 10% of the decoded size,
-                    adaptive speculation capped at 16
-  paper             2048x2048x1920 u8 mixing layer, 2 bits/value, iso 0.5,
+  paper (default)   2048x2048x1920 u8 mixing layer, 2 bits/value, iso 0.5,
                     1280x720, one pose, 4 GB cache, adaptive speculation (cap 64)
+                    -- the configuration of the paper's R-M figure (Sec. 5.1)
+  medium            512^3 u8 Gaussian blobs + 10% noise, 2 bits/value, iso 0.3,
+                    1280x720, 16-pose orbit, cache 10% of the decoded size,
+                    adaptive speculation capped at 16 (also reported as a
+                    sub-object of the paper line unless --no-medium)
   small             64^3 float value noise, 8 bits/value, iso 0.5, 256x256,
                     cache 25% of the blocks, fixed k = 4
 
@@ -35,28 +37,36 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms to final image & per pass at 1280×720; decoded GB/s vs HBM peak; blocks decoded"
 
-# The traversal is bound by dependent integer/float instruction chains, not by
-# memory: its roofline is the SM issue rate (4 warp instructions per clock per
-# SM, 32 lanes each).  Thread instructions per walk step and DRAM bytes per
-# launch come from one ncu capture of traverse_kernel on the medium workload
-# (smsp__thread_inst_executed.sum and dram__bytes_read/write.sum over the four
-# passes of one render: 1.1463e9 thread instructions for the 5,289,370 steps
-# of the two passes it walks; 4.42 MB over 4 launches); the live run supplies
-# the steps and the time.
-TRAV_THREAD_INST_PER_STEP = 216.7
-TRAV_DRAM_BYTES_PER_LAUNCH = 1104896
-TRAV_COOP_BELOW = 16384   # passes with fewer live rays walk one ray per warp
+# Algorithmic bytes of the hot-path kernels per unit of work (the units come
+# from the render's own per-pass counters):
+#   traversal: per live ray, its ray (16 B) and iterator state (32 B) read and
+#     the state written back (32 B), 4 B per speculated R_BID slot, and 8 B per
+#     range-grid entry the walk visits (one per walk step);
+#   decode: 8*rate bytes of bit stream read and 256 bytes of values written
+#     per decoded block;
+#   intersection: per visible block its 5^3 dual grid (125 x 4 B), per entry
+#     the ray (16 B) and the 8-byte atomic on the pixel's key.
+TRAV_BYTES_PER_RAY = 16 + 32 + 32
+TRAV_BYTES_PER_SLOT = 4
+TRAV_BYTES_PER_STEP = 8
+ISECT_BYTES_PER_VISIBLE = 125 * 4
+ISECT_BYTES_PER_ENTRY = 16 + 8
+
+
+def decode_bytes_per_block(rate):
+    return 8 * rate + 256
+
 
 WORKLOADS = {
-    "medium": dict(dims=(512, 512, 512), rate=2, iso=0.3, W=1280, H=720, poses=16,
+    "medium": dict(field="blobs", dims=(512, 512, 512), rate=2, iso=0.3, W=1280, H=720, poses=16,
                    cache_bytes=int(0.10 * 512 ** 3 * 4), spec="adaptive", k=16,
                    name="medium: 512^3 u8 Gaussian blobs + 10% noise, 2 bits/value, iso 0.3, "
                         "1280x720, 16-pose orbit, cache 10% of decoded size, adaptive k<=16"),
-    "paper": dict(dims=(2048, 2048, 1920), rate=2, iso=0.5, W=1280, H=720, poses=1,
+    "paper": dict(field="mixing", dims=(2048, 2048, 1920), rate=2, iso=0.5, W=1280, H=720, poses=1,
                   cache_bytes=4 << 30, spec="adaptive", k=64,
                   name="paper-scale: 2048x2048x1920 u8 mixing layer, 2 bits/value, iso 0.5, "
                        "1280x720, cache 4 GB, adaptive k<=64"),
-    "small": dict(dims=(64, 64, 64), rate=8, iso=0.5, W=256, H=256, poses=1,
+    "small": dict(field="noise", dims=(64, 64, 64), rate=8, iso=0.5, W=256, H=256, poses=1,
                   cache_bytes=1024 * 256, spec="fixed", k=4,
                   name="small: 64^3 value noise, 8 bits/value, iso 0.5, 256x256, "
                        "cache 25% of blocks, k=4"),
@@ -91,47 +101,82 @@ def peaks():
 
 def pose(wl, i):
     import synth
-    if wl["dims"] == (64, 64, 64):
+    if wl["field"] == "noise":
         return synth.cameras.small_pose(wl["dims"], wl["W"], wl["H"])
-    if wl["poses"] == 1 and wl["dims"][0] == 2048:
+    if wl["field"] == "mixing":
         return synth.cameras.paper_pose(wl["dims"], wl["W"], wl["H"])
     return synth.cameras.medium_pose(i % wl["poses"], wl["dims"], wl["W"], wl["H"])
 
 
 def make_volume_u8_or_f32(wl, device):
-    """The raw (uncompressed) volume as a torch tensor on `device`."""
+    """The raw (uncompressed) volume as a torch tensor on `device` (small and
+    medium workloads; the mixing layer is generated slab by slab)."""
     import synth
     dims = wl["dims"]
-    if dims == (64, 64, 64):
+    if wl["field"] == "noise":
         return synth.volumes.value_noise(dims, seed=1, device=device)
-    if dims[0] == 2048:
-        return None  # generated slab by slab
     return synth.volumes.gaussian_blobs(dims, seed=2, device=device)
+
+
+def is_mixing_layer(wl):
+    return wl["field"] == "mixing"
+
+
+def raw_slabs(wl, device):
+    """The workload's raw volume as (z0, z1, tensor (z1-z0, Dy, Dx)) slabs,
+    generated by synth (the seeded input generator both sides use) on
+    `device`: 64-voxel slabs of the mixing layer, the other volumes whole."""
+    import synth
+    dims = wl["dims"]
+    if is_mixing_layer(wl):
+        Dz = dims[2]
+        params = synth.volumes.mixing_layer_params(3, scale=Dz / 1920.0)
+        for z0 in range(0, Dz, 64):
+            z1 = min(Dz, z0 + 64)
+            yield z0, z1, synth.volumes.mixing_layer_slab(dims, z0, z1, params, z_mid=Dz / 2.0,
+                                                          device=device)
+    else:
+        yield 0, dims[2], make_volume_u8_or_f32(wl, device)
+
+
+def compress_volume(wl, spr=None, torch=None, library=True, oracle_side=False):
+    """Compress the workload's volume slab by slab (slabs of 4k voxels in z,
+    so the per-slab streams concatenate to the whole volume's): with the
+    library's encoder into a device stream (`library`) and/or with the
+    oracle's own encoder into a host stream (`oracle_side`).  The raw slabs
+    come from synth on the GPU when there is one.  Returns (device stream or
+    None, host stream or None)."""
+    import numpy as np
+    if torch is None:
+        import torch
+    dims, rate = wl["dims"], wl["rate"]
+    nb = [(d + 3) // 4 for d in dims]
+    total = nb[0] * nb[1] * nb[2] * 8 * rate
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    out_dev = torch.empty(total, dtype=torch.uint8, device="cuda") if library else None
+    out_host = np.empty(total, dtype=np.uint8) if oracle_side else None
+    if oracle_side:
+        import oracle
+        oracle.build()
+    for z0, z1, raw in raw_slabs(wl, dev):
+        lo = nb[0] * nb[1] * (z0 // 4) * 8 * rate
+        n = nb[0] * nb[1] * ((z1 - z0 + 3) // 4) * 8 * rate
+        if library:
+            if raw.dtype == torch.uint8:
+                spr.spr_encode_u8(raw, rate, out=out_dev[lo:lo + n])
+            else:
+                spr.spr_encode_f32(raw, rate, out=out_dev[lo:lo + n])
+        if oracle_side:
+            host = raw.cpu().numpy()
+            out_host[lo:lo + n] = oracle.encode_volume(host, (dims[0], dims[1], z1 - z0), rate)
+        del raw
+    return out_dev, out_host
 
 
 def compressed_on_device(wl, spr, torch):
     """Generate the workload's volume on the GPU and compress it with the
     library's encoder; returns the block stream (device)."""
-    import synth
-    dims, rate = wl["dims"], wl["rate"]
-    if dims[0] == 2048:
-        Dx, Dy, Dz = dims
-        nb = ((Dx + 3) // 4, (Dy + 3) // 4, (Dz + 3) // 4)
-        out = torch.empty(nb[0] * nb[1] * nb[2] * 8 * rate, dtype=torch.uint8, device="cuda")
-        params = synth.volumes.mixing_layer_params(3, scale=Dz / 1920.0)
-        slab = 64
-        per_slab = nb[0] * nb[1] * (slab // 4) * 8 * rate
-        for i, z0 in enumerate(range(0, Dz, slab)):
-            z1 = min(Dz, z0 + slab)
-            u8 = synth.volumes.mixing_layer_slab(dims, z0, z1, params, z_mid=Dz / 2.0,
-                                                 device="cuda")
-            n = nb[0] * nb[1] * ((z1 - z0 + 3) // 4) * 8 * rate
-            spr.spr_encode_u8(u8, rate, out=out[i * per_slab:i * per_slab + n])
-        return out
-    vol = make_volume_u8_or_f32(wl, "cuda")
-    if vol.dtype == torch.uint8:
-        return spr.spr_encode_u8(vol, rate)
-    return spr.spr_encode_f32(vol, rate)
+    return compress_volume(wl, spr, torch)[0]
 
 
 class ClockSampler:
@@ -191,73 +236,95 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(wl, pose_index, rows_every, nthreads, comp_host=None):
-    """Time the CPU oracle on every `rows_every`-th pixel row of one pose:
-    decode the whole volume once, then ray cast the sample.  Returns
-    (extrapolated ms per image, details)."""
+def sample_rows(H, bands, rows):
+    """`bands` bands of `rows` consecutive pixel rows, spread evenly over an
+    image of H rows: the oracle's timed sample (consecutive rows share
+    blocks, as they do in a whole image)."""
+    out = []
+    for b in range(bands):
+        c = int(round((b + 0.5) * H / bands)) - rows // 2
+        c = max(0, min(H - rows, c))
+        out.extend(range(c, c + rows))
+    return sorted(set(out))
+
+
+# Oracle samples (bands x rows): all host cores, and one core.  Sized for
+# about 10-30 s of CPU work at paper scale on a 16-core host.
+ORACLE_SAMPLE = {"all": (8, 4), "one": (2, 1)}
+
+
+def oracle_time(wl, comp_host, cam, rows, nthreads):
+    """Render the pixel rows `rows` of one pose with the CPU oracle, blocks
+    decoded on demand (Sec. 3.5) and memoised within the call, so the decode
+    of every block the rays reach is counted.  Returns (ms per image
+    extrapolated from the sample, details)."""
     import numpy as np
 
     import oracle
-    dims, rate = wl["dims"], wl["rate"]
-    if comp_host is None:
-        import synth
-        dev = "cpu"
-        vol = make_volume_u8_or_f32(wl, dev)
-        vol = vol.numpy() if hasattr(vol, "numpy") else vol
-        comp_host = oracle.encode_volume(vol, dims, rate)
+    dims, rate, W, H = wl["dims"], wl["rate"], wl["W"], wl["H"]
+    ov = oracle.Volume.on_demand(comp_host, dims, rate)
+    r = np.asarray(rows, dtype=np.int64)
+    pixels = (r[:, None] * W + np.arange(W)[None, :]).reshape(-1)
     t0 = time.perf_counter()
-    dec = oracle.decode_volume(comp_host, dims, rate)
-    _, fine, _ = oracle.ranges(dec, dims)
-    t_dec = time.perf_counter() - t0
-    ov = oracle.Volume(dec, dims, fine)
-    W, H = wl["W"], wl["H"]
-    rows = np.arange(0, H, rows_every)
-    pixels = (rows[:, None] * W + np.arange(W)[None, :]).reshape(-1)
-    cam = pose(wl, pose_index)
-    t0 = time.perf_counter()
-    oracle.render(ov, cam, W, H, wl["iso"], pixels=pixels, nthreads=nthreads)
-    t_ray = time.perf_counter() - t0
-    ms = 1e3 * (t_dec + t_ray * (W * H) / pixels.size)
-    return ms, dict(decode_s=t_dec, raycast_s=t_ray, pixels=int(pixels.size))
+    pix = oracle.render(ov, cam, W, H, wl["iso"], pixels=pixels, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    ms = 1e3 * dt * (W * H) / pixels.size
+    return ms, dict(seconds=dt, pixels=int(pixels.size), rows=len(rows),
+                    blocks_decoded=ov.last_decodes, hits=int(pix["hit"].sum()), threads=nthreads)
+
+
+def cpu_baseline(wl, comp_host, cam, which=("all", "one")):
+    """The oracle as it stands on the host cores: all cores (OpenMP over
+    pixels) and one core, each on its bounded sample of pixel rows of the
+    pose, extrapolated to the whole image."""
+    ncores = os.cpu_count() or 1
+    res = {}
+    for key in which:
+        bands, rows = ORACLE_SAMPLE[key]
+        nt = ncores if key == "all" else 1
+        ms, det = oracle_time(wl, comp_host, cam, sample_rows(wl["H"], bands, rows), nt)
+        res[key] = dict(ms=ms, **det)
+    return res
+
+
+def describe_sample(d, W, H):
+    return ("C oracle (FP64, %d thread%s, blocks decoded on demand and memoised per render, "
+            "%d decoded): %d pixel rows (%d pixels, bands of consecutive rows spread over the "
+            "image) of the %dx%d image in %.2f s, extrapolated to the whole image" %
+            (d["threads"], "" if d["threads"] == 1 else "s", d["blocks_decoded"], d["rows"],
+             d["pixels"], W, H, d["seconds"]))
 
 
 def run_reference(args, wl):
+    """The reference arm: the CPU oracle (the plain definition the GPU path is
+    checked against) timed on the host cores on the workload's pose, each
+    step a bounded sample of pixel rows.  Its input is the oracle's own
+    encoding of the synth volume."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import numpy as np
-
     import oracle
     oracle.build()
     nthreads = os.cpu_count() or 1
-    dims = wl["dims"]
-    if dims[0] == 2048:
-        print(json.dumps({"impl": "reference", "unavailable":
-                          "the CPU oracle holds the decoded volume in host memory; the "
-                          "2048x2048x1920 volume (30 GB of floats) is measured on the medium "
-                          "workload instead"}))
-        return 0
-    vol = make_volume_u8_or_f32(wl, "cpu")
-    vol = vol.numpy() if hasattr(vol, "numpy") else vol
-    comp = oracle.encode_volume(vol, dims, wl["rate"])
-    rows_every = 4 if wl["W"] >= 1280 else 2
-    times = []
+    _, comp = compress_volume(wl, library=False, oracle_side=True)
+    cam = pose(wl, 0)
+    bands, rows = ORACLE_SAMPLE["all"]
+    sample = sample_rows(wl["H"], bands, rows)
+    times, det = [], None
     for step in range(args.warmup + args.steps):
-        ms, det = oracle_sample(wl, step, rows_every, nthreads, comp)
+        ms, det = oracle_time(wl, comp, cam, sample, nthreads)
         if step >= args.warmup:
             times.append(ms)
-    value = statistics.mean(times)
-    sample = ("oracle (C, FP64, %d threads): full decode + ray casting of every %dth pixel row "
-              "(%d pixels), extrapolated to the whole %dx%d image" %
-              (nthreads, rows_every, det["pixels"], wl["W"], wl["H"]))
+    value = statistics.mean(times) if times else float("nan")
     print(json.dumps({
         "metric": METRIC, "value": round(value, 3), "unit": "ms", "impl": "reference",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(value, 3), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["name"]},
+        "config": {"workload": wl["name"], "dims": list(wl["dims"]), "rate": wl["rate"],
+                   "image": [wl["W"], wl["H"]], "iso": wl["iso"]},
         "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": nthreads,
-                         "kind": "oracle", "sample": sample},
+                         "kind": "oracle", "sample": describe_sample(det, wl["W"], wl["H"])},
         "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }))
@@ -757,14 +824,269 @@ def run_decode_slab(args):
     return 0
 
 
+def stage_rooflines(prof_stats, stage, rate, pk):
+    """Algorithmic GB/s of the traversal, decode and intersection stages over
+    the instrumented renders (per-pass counters x bytes per unit, over each
+    stage's CUDA-event time), against the measured HBM copy peak."""
+    per_pass = [p for _, ps in prof_stats for p in ps]
+    trav = sum(p["n_processed"] * TRAV_BYTES_PER_RAY + p["n_entries_cap"] * TRAV_BYTES_PER_SLOT +
+               p["n_steps"] * TRAV_BYTES_PER_STEP for p in per_pass)
+    dec = sum(p["n_decoded"] * decode_bytes_per_block(rate) for p in per_pass)
+    isect = sum(p["n_visible"] * ISECT_BYTES_PER_VISIBLE + p["n_entries"] * ISECT_BYTES_PER_ENTRY
+                for p in per_pass)
+    out = {}
+    for name, kernel, nbytes, units in (
+            ("traverse", "traverse_kernel / traverse_coop_kernel", trav,
+             "live rays x %d B + speculated slots x %d B + walk steps x %d B" %
+             (TRAV_BYTES_PER_RAY, TRAV_BYTES_PER_SLOT, TRAV_BYTES_PER_STEP)),
+            ("decode", "decode_list_kernel", dec, "decoded blocks x %d B" % decode_bytes_per_block(rate)),
+            ("intersect", "intersect_kernel", isect,
+             "visible blocks x %d B + entries x %d B" % (ISECT_BYTES_PER_VISIBLE, ISECT_BYTES_PER_ENTRY))):
+        ms = stage[name]
+        gbs = (nbytes / 1e9) / (ms / 1e3) if ms > 0 else 0.0
+        out[name] = {"kernel": kernel, "bytes": int(nbytes), "ms": ms, "achieved": round(gbs, 1),
+                     "frac": round(gbs / pk["hbm_gbs"], 4), "units": units}
+    return out
+
+
+def pass_slots(p):
+    """Speculated R_BID slots of a pass under a uniform rule: k_used per ray
+    taken."""
+    return p["n_processed"] * p["k_used"]
+
+
+def measure_workload(wl, args, spr, _lib, torch, stream, rank, world, dist, local, comp,
+                     headline=True):
+    """Time `args.steps` renders of the workload (after warm-up) and the
+    instrumented renders behind the stage breakdown; returns a dict."""
+    import ctypes
+    pk = peaks()
+    vol = spr.spr_create_volume(wl["dims"], wl["rate"], comp, stream=stream)
+    r = spr.spr_create_renderer(vol, wl["W"], wl["H"])
+    spr.spr_set_cache_budget(r, wl["cache_bytes"])
+    if wl["spec"] == "fixed":
+        spr.spr_set_speculation(r, spr.SPR_SPEC_FIXED, k=wl["k"])
+    else:
+        spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=wl["k"])
+    spr.spr_set_isovalue(r, wl["iso"])
+    spr.spr_set_profiling(r, False)
+    if args.warp_walk >= 0:
+        spr.spr_set_warp_walk_threshold(r, args.warp_walk)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    L = _lib.load()
+    f3 = ctypes.c_float * 3
+
+    def cam_args(c):
+        return tuple(f3(*[float(v) for v in c[k]]) for k in ("eye", "p00", "du", "dv"))
+
+    def step(i):
+        spr.spr_reset_cache(r)
+        spr.spr_set_camera(r, pose(wl, replica_pose_index(rank, i)))
+        return spr.spr_render_to_convergence(r, 100000, stream=stream)
+
+    # The timed loop calls the C ABI directly with camera arrays prepared
+    # beforehand; the per-pass records are converted after the end event.
+    class Timed:
+        def __init__(self, n, first):
+            self.cams = [cam_args(pose(wl, replica_pose_index(rank, first + i))) for i in range(n)]
+            self.rs = [_lib.RenderStats() for _ in range(n)]
+            self.per = [(_lib.PassStats * 64)() for _ in range(n)]
+
+        def run(self, i):
+            _lib.check(L.spr_reset_cache(r.handle))
+            _lib.check(L.spr_set_camera(r.handle, *self.cams[i]))
+            _lib.check(L.spr_render_to_convergence(r.handle, ctypes.c_void_p(stream.cuda_stream), 64,
+                                                   ctypes.byref(self.rs[i]), self.per[i]))
+
+        def stats(self, i):
+            rs = self.rs[i].as_dict()
+            return rs, [self.per[i][k].as_dict() for k in range(rs["passes"])]
+
+    res = {}
+    with ClockSampler(local) as clk:
+        # warm-up: at least `warmup` renders and at least `warm_s` seconds of
+        # them, so that the clock record covers the load the timed renders run in
+        t_end = time.perf_counter() + (args.warm_s if headline else 0.0)
+        i = 0
+        while i < args.warmup or time.perf_counter() < t_end:
+            flush.fill_(i & 255)
+            step(i)
+            torch.cuda.synchronize()
+            i += 1
+        res["warmup_renders"] = i
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        timed = Timed(args.steps, args.warmup)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_((i + 7) & 255)          # L2 flush, outside the timed region
+            ev0[i].record(stream)
+            timed.run(i)
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    res["clocks"] = clk.summary()
+    stats = [timed.stats(i) for i in range(args.steps)]
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    ms_image = max_over_ranks(statistics.mean(step_ms), dist, device="cuda")
+    res["ms_image"] = ms_image
+    res["ms_image_median"] = statistics.median(step_ms)
+    res["stats"] = stats
+
+    # Per-stage device times: the same poses again, each pass attempt as a
+    # captured graph with events between its stages.
+    n_prof = min(args.steps, 16)
+    prof_stats = []
+    spr.spr_set_profiling(r, True)
+    for i in range(n_prof):
+        flush.fill_((i + 7) & 255)
+        prof_stats.append(step(args.warmup + i))
+    spr.spr_set_profiling(r, False)
+    torch.cuda.synchronize()
+    stage_names = ["traverse", "group", "cache", "decode", "intersect", "resolve"]
+    stage = {n: 0.0 for n in stage_names}
+    per_index = {}
+    isect_entries, isect_ms = 0, 0.0
+    for rs, passes in prof_stats:
+        for p in passes:
+            p["n_entries_cap"] = pass_slots(p)
+            for k, n in enumerate(stage_names):
+                stage[n] += p["ms_stage"][k]
+            per_index.setdefault(p["pass"], []).append(p["ms"])
+            isect_entries += p["n_entries"]
+            isect_ms += p["ms_stage"][4]
+    n_prof_r = max(1, len(prof_stats))
+    rl = stage_rooflines(prof_stats, stage, wl["rate"], pk)
+    dom = max(rl, key=lambda n: stage[n])
+    total_stage = sum(stage.values()) or 1.0
+    d = rl[dom]
+    res["roofline"] = {
+        "kernel": d["kernel"], "stage": dom, "bound": "hbm", "achieved": d["achieved"],
+        "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": d["frac"],
+        "traffic": None, "peak_source": pk["src"] + " HBM copy peak (MEASURED_PEAKS.json hbm_gbs)",
+        "work": d["units"] + " (per-pass counters of the instrumented renders)",
+        "share": round(stage[dom] / total_stage, 3),
+        "timing": "CUDA-event time of the kernel's stage, %d instrumented renders of the same poses" % n_prof_r}
+    res["stage_roofline"] = {k: {kk: v[kk] for kk in ("kernel", "achieved", "frac", "units")} | {
+        "ms_per_image": round(v["ms"] / n_prof_r, 4)} for k, v in rl.items()}
+    res["stage_ms_per_image"] = {k: round(v / n_prof_r, 4) for k, v in stage.items()}
+    res["ms_per_pass_index"] = {str(k): round(statistics.mean(v), 4) for k, v in sorted(per_index.items())}
+    res["isect"] = (isect_entries, isect_ms)
+    dec_ms = stage["decode"]
+    dec_bytes = rl["decode"]["bytes"]
+    res["decoded_gbs"] = (dec_bytes / 1e9) / (dec_ms / 1e3) if dec_ms > 0 else 0.0
+    res["prof_stats"] = prof_stats
+    if not headline:
+        r.close()
+        vol.close()
+        return res
+
+    # end to end through the C ABI with host buffers: camera in, image out
+    n = wl["W"] * wl["H"]
+    host = {k: torch.empty(n * sz, dtype=torch.uint8, pin_memory=True)
+            for k, sz in (("depth", 4), ("rgba", 4), ("block", 4), ("cell", 8),
+                          ("final", 4), ("status", 1))}
+    e2e, pass_reads = [], []
+    h2d = 4 * 12 + 4
+    d2h = sum(t.numel() for t in host.values())
+    e2e_cams = [pose(wl, i) for i in range(args.e2e_steps)]
+    for i in range(args.e2e_steps):
+        flush.fill_(i & 255)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        spr.spr_reset_cache(r)
+        spr.spr_set_camera(r, e2e_cams[i])
+        spr.spr_set_isovalue(r, wl["iso"])
+        rs, _ = spr.spr_render_to_convergence(r, 100000, stream=stream)
+        _lib.check(L.spr_read_framebuffer(r.handle, ctypes.c_void_p(stream.cuda_stream),
+                                          *[ctypes.c_void_p(host[k].data_ptr()) for k in
+                                            ("depth", "rgba", "block", "cell", "final", "status")]))
+        e2e.append(1e3 * (time.perf_counter() - t0))
+        pass_reads.append(rs["passes"] + 1)
+    res["e2e"] = {"value": round(statistics.mean(e2e), 4), "unit": "ms", "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": int(d2h + 64 * statistics.mean(pass_reads))}
+
+    # Decode of a contiguous run of blocks (up to 16M blocks, 4 GB out)
+    # through spr_decode_blocks: the decoder alone against the HBM copy
+    # peak.  The library's 4-byte error flag comes from torch's caching
+    # allocator, so no cudaMalloc sits between the events.
+    import numpy as np
+    nb_vol = int(np.prod([(x + 3) // 4 for x in wl["dims"]]))
+    nb_all = min(nb_vol, 16 << 20)
+    first = (nb_vol - nb_all) // 2      # centred on the middle z layer (the mixing layer)
+    dec_ids = torch.arange(first, first + nb_all, dtype=torch.int64, device="cuda").to(torch.int32)
+    dec_out = torch.empty((nb_all, 64), dtype=torch.float32, device="cuda")
+    spr.use_torch_allocator()
+    try:
+        for _ in range(2):
+            spr.spr_decode_blocks(comp, nb_vol, wl["rate"], ids=dec_ids, n=nb_all, out=dec_out, stream=stream)
+        dec_times = []
+        for i in range(5):
+            flush.fill_(i & 255)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            spr.spr_decode_blocks(comp, nb_vol, wl["rate"], ids=dec_ids, n=nb_all, out=dec_out, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            dec_times.append(a.elapsed_time(b))
+    finally:
+        spr.spr_set_allocator()
+    del dec_out, dec_ids
+    ms_ = statistics.median(dec_times)
+    gbs = nb_all * (decode_bytes_per_block(wl["rate"]) + 4) / 1e9 / (ms_ / 1e3)
+    res["decode_all"] = {"kernel": "decode_list_kernel", "blocks": nb_all, "ms": round(ms_, 4),
+                         "achieved": round(gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(gbs / pk["hbm_gbs"], 4), "first_block": first,
+                         "bytes_per_block": decode_bytes_per_block(wl["rate"]) + 4,
+                         "timing": "median of 5 CUDA-event timed calls, L2 flushed before each"}
+    r.close()
+    vol.close()
+    return res
+
+
+def summarise(wl, res, world):
+    stats = res["stats"]
+    n_pass = sum(rs["passes"] for rs, _ in stats)
+    blocks = sum(rs["blocks_decoded"] for rs, _ in stats)
+    entries = sum(rs["entries"] for rs, _ in stats) / max(1, len(stats))
+    ie, ims = res["isect"]
+    return {
+        "ms_per_pass": round(res["ms_image"] * len(stats) / max(1, n_pass), 4),
+        "passes_per_image": round(n_pass / len(stats), 2),
+        "blocks_decoded_per_image": round(blocks / len(stats), 1),
+        "decoded_gbs": round(res["decoded_gbs"], 1),
+        "images_per_s": round(1e3 / res["ms_image"] * world, 2),
+        "stage_ms_per_image": res["stage_ms_per_image"],
+        "ms_per_pass_index": res["ms_per_pass_index"],
+        "ray_block_tests_per_s": {
+            "intersect_stage": round(ie / (ims / 1e3), 1) if ims > 0 else None,
+            "whole_render": round(entries / (res["ms_image"] / 1e3), 1),
+            "entries_per_image": round(entries, 1),
+            "timing": "entries of the instrumented renders over their intersection stage time; "
+                      "entries of the timed renders over their ms to the final image"},
+        "gpu_launches": int(sum(rs["kernel_launches"] for rs, _ in stats)),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=128)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warm-s", type=float, default=2.0,
+                    help="minimum seconds of warm-up renders (clock record under load)")
     ap.add_argument("--impl", default="spr", choices=["spr", "reference"])
-    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="paper", choices=sorted(WORKLOADS))
+    ap.add_argument("--dims", type=int, nargs=3, default=None,
+                    help="override the workload's volume size (quick runs; the line names it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-medium", action="store_true",
+                    help="skip the medium workload's sub-object in the paper-scale line")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--dump", default="", help="write per-pass details to this JSON file")
     ap.add_argument("--study", default="",
@@ -792,6 +1114,10 @@ def main():
                     help="override the workload's speculation limit (k sweeps; 0 keeps it)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
+    if args.dims:
+        wl["dims"] = tuple(args.dims)
+        wl["name"] = wl["name"].replace("2048x2048x1920", "x".join(map(str, args.dims))).replace(
+            "512^3", "x".join(map(str, args.dims)))
     if args.k_max > 0:
         wl["k"] = args.k_max
         wl["name"] = wl["name"].rsplit("k<=", 1)[0] + f"k<={args.k_max}" if "k<=" in wl["name"] else wl["name"]
@@ -808,9 +1134,6 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
 
-    import ctypes
-
-    import numpy as np
     import torch
 
     rank = int(os.environ.get("RANK", "0"))
@@ -829,259 +1152,49 @@ def main():
     import paper_2309_10212_gb300 as spr
     from paper_2309_10212_gb300 import _lib
 
+    want_cpu = rank == 0 and not args.no_cpu_baseline
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        comp = compressed_on_device(wl, spr, torch)
-        vol = spr.spr_create_volume(wl["dims"], wl["rate"], comp, stream=stream)
-        r = spr.spr_create_renderer(vol, wl["W"], wl["H"])
-        spr.spr_set_cache_budget(r, wl["cache_bytes"])
-        if wl["spec"] == "fixed":
-            spr.spr_set_speculation(r, spr.SPR_SPEC_FIXED, k=wl["k"])
-        else:
-            spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=wl["k"])
-        spr.spr_set_isovalue(r, wl["iso"])
-        spr.spr_set_profiling(r, False)
-        if args.warp_walk >= 0:
-            spr.spr_set_warp_walk_threshold(r, args.warp_walk)
-        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        torch.cuda.synchronize()
-
-        def step(i):
-            spr.spr_reset_cache(r)
-            spr.spr_set_camera(r, pose(wl, replica_pose_index(rank, i)))
-            return spr.spr_render_to_convergence(r, 100000, stream=stream)
-
-        # The timed loop calls the C ABI directly with camera arrays prepared
-        # beforehand; the per-pass records are converted after the end event.
-        L = _lib.load()
-        f3 = ctypes.c_float * 3
-
-        def cam_args(c):
-            return tuple(f3(*[float(v) for v in c[k]]) for k in ("eye", "p00", "du", "dv"))
-
-        class Timed:
-            def __init__(self, n):
-                self.cams = [cam_args(pose(wl, replica_pose_index(rank, args.warmup + i))) for i in range(n)]
-                self.rs = [_lib.RenderStats() for _ in range(n)]
-                self.per = [(_lib.PassStats * 64)() for _ in range(n)]
-
-            def run(self, i):
-                _lib.check(L.spr_reset_cache(r.handle))
-                _lib.check(L.spr_set_camera(r.handle, *self.cams[i]))
-                _lib.check(L.spr_render_to_convergence(r.handle, ctypes.c_void_p(stream.cuda_stream), 64,
-                                                       ctypes.byref(self.rs[i]), self.per[i]))
-
-            def stats(self, i):
-                rs = self.rs[i].as_dict()
-                return rs, [self.per[i][k].as_dict() for k in range(rs["passes"])]
-
-        for i in range(args.warmup):
-            flush.fill_(i & 255)
-            step(i)
-        torch.cuda.synchronize()
-        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        stats = []
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        timed = Timed(args.steps)
-        with ClockSampler(local) as clk:
-            for i in range(args.steps):
-                flush.fill_((i + 7) & 255)          # L2 flush, outside the timed region
-                ev0[i].record(stream)
-                timed.run(i)
-                ev1[i].record(stream)
-            torch.cuda.synchronize()
-        stats = [timed.stats(i) for i in range(args.steps)]
-        if dist:
-            dist.barrier()
-        step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-        ms_image = statistics.mean(step_ms)
-        ms_image = max_over_ranks(ms_image, dist, device="cuda")
-
-        # Per-stage device times: the same steps again with the library's
-        # CUDA events between stages (host-driven passes, so the stage events
-        # bracket each kernel group); the headline above ran the graph path.
-        n_prof = min(args.steps, 16)
-        prof_stats = []
-        spr.spr_set_profiling(r, True)
-        for i in range(n_prof):
-            flush.fill_((i + 7) & 255)
-            prof_stats.append(step(args.warmup + i))
-        spr.spr_set_profiling(r, False)
-        torch.cuda.synchronize()
-        stage_names = ["traverse", "group", "cache", "decode", "intersect", "resolve"]
-        stage = {n: 0.0 for n in stage_names}
-        n_pass = 0
-        blocks = 0
-        launches = 0
-        decode_launch_ms, decode_bytes = [], []
-        for rs, passes in stats:
-            n_pass += rs["passes"]
-            blocks += rs["blocks_decoded"]
-            launches += rs["kernel_launches"]
-        per_index = {}          # pass index -> stage-sum ms of each instrumented render
-        isect_entries, isect_ms = 0, 0.0
-        for rs, passes in prof_stats:
-            for p in passes:
-                for k, n in enumerate(stage_names):
-                    stage[n] += p["ms_stage"][k]
-                if p["n_decoded"]:
-                    decode_launch_ms.append(p["ms_stage"][3])
-                    decode_bytes.append(p["n_decoded"] * (8 * wl["rate"] + 256))
-                per_index.setdefault(p["pass"], []).append(p["ms"])
-                isect_entries += p["n_entries"]
-                isect_ms += p["ms_stage"][4]
-        total_stage = sum(stage.values()) or 1.0
-        # ray-block tests per second: entries tested by the intersection,
-        # over its stage time and over the whole render
-        entries_per_image = sum(rs["entries"] for rs, _ in stats) / max(1, len(stats))
-        pk = peaks()
-        # the kernel-level stages with one kernel each: traverse, decode, intersect
-        one_kernel = {"traverse": "traverse_kernel", "decode": "decode_list_kernel",
-                      "intersect": "intersect_kernel"}
-        dom = max(one_kernel, key=lambda n: stage[n])
-        dec_ms = sum(decode_launch_ms)
-        dec_gbs = (sum(decode_bytes) / 1e9) / (dec_ms / 1e3) if dec_ms > 0 else 0.0
-        roofline = None
-        if dom == "decode" and dec_ms > 0:
-            roofline = {"kernel": one_kernel[dom], "bound": "hbm",
-                        "achieved": round(dec_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                        "frac": round(dec_gbs / pk["hbm_gbs"], 4), "traffic": None,
-                        "peak_source": pk["src"]}
-        elif dom == "traverse":
-            # passes walked one ray per thread (the kernel the per-step
-            # instruction count describes); fewer rays go one per warp
-            per_pass = [p for _, ps in prof_stats for p in ps if p["n_processed"] >= TRAV_COOP_BELOW]
-            steps_ = sum(p["n_steps"] for p in per_pass)
-            ms_ = sum(p["ms_stage"][0] for p in per_pass)
-            sms = torch.cuda.get_device_properties(local).multi_processor_count
-            f_mhz = (clk.summary() or {}).get("sm_max_mhz") or 2070.0
-            peak_ti = sms * 4 * 32 * f_mhz * 1e6 / 1e12
-            ach = steps_ * TRAV_THREAD_INST_PER_STEP / (ms_ / 1e3) / 1e12 if ms_ > 0 else 0.0
-            roofline = {"kernel": one_kernel[dom], "bound": "alu", "achieved": round(ach, 3),
-                        "peak": round(peak_ti, 2), "unit": "Tinst/s", "frac": round(ach / peak_ti, 4),
-                        "traffic": TRAV_DRAM_BYTES_PER_LAUNCH,
-                        "peak_source": "%d SMs x 4 issue slots x 32 lanes x %.0f MHz" % (sms, f_mhz),
-                        "work": "walk steps x %.1f thread instructions per step (ncu), passes "
-                                "with >= %d live rays" % (TRAV_THREAD_INST_PER_STEP, TRAV_COOP_BELOW),
-                        "hbm_frac": None}
-        else:
-            # the intersection is latency/ALU bound; report its algorithmic
-            # HBM bytes against the copy peak
-            per_pass = [p for _, ps in prof_stats for p in ps]
-            if dom == "traverse":
-                bytes_ = sum(p["n_processed"] * (4 + 8 + 8) + p["n_processed"] * p["k_used"] * 4
-                             for p in per_pass)
-            else:
-                bytes_ = sum(p["n_entries"] * (4 + 4 + 4 + 8 + 32 + 256) for p in per_pass)
-            ms_ = stage[dom]
-            ach = (bytes_ / 1e9) / (ms_ / 1e3) if ms_ > 0 else 0.0
-            roofline = {"kernel": one_kernel[dom], "bound": "hbm", "achieved": round(ach, 1),
-                        "peak": pk["hbm_gbs"], "unit": "GB/s",
-                        "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None,
-                        "peak_source": pk["src"]}
-        roofline["share"] = round(stage[dom] / total_stage, 3)
-        roofline["timing"] = ("mean CUDA-event time of the kernel's stage in %d instrumented "
-                              "renders of the same poses" % n_prof)
-
-        # end to end through the C ABI with host buffers: camera in, image out
-        n = wl["W"] * wl["H"]
-        host = {k: torch.empty(n * s, dtype=torch.uint8, pin_memory=True)
-                for k, s in (("depth", 4), ("rgba", 4), ("block", 4), ("cell", 8),
-                             ("final", 4), ("status", 1))}
-        L = _lib.load()
-        e2e = []
-        h2d = 4 * 12 + 4
-        d2h = sum(t.numel() for t in host.values())
-        pass_reads = []
-        spr.spr_set_profiling(r, False)
-        # the cameras are the steps' host inputs, made before the timed region
-        # (as in the device-timed loop); each step hands its camera to the
-        # library (host -> device) and reads the whole framebuffer back
-        e2e_cams = [pose(wl, i) for i in range(args.e2e_steps)]
-        for i in range(args.e2e_steps):
-            flush.fill_(i & 255)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            spr.spr_reset_cache(r)
-            cam = e2e_cams[i]
-            spr.spr_set_camera(r, cam)
-            spr.spr_set_isovalue(r, wl["iso"])
-            rs, _ = spr.spr_render_to_convergence(r, 100000, stream=stream)
-            _lib.check(L.spr_read_framebuffer(r.handle, ctypes.c_void_p(stream.cuda_stream),
-                                              *[ctypes.c_void_p(host[k].data_ptr()) for k in
-                                                ("depth", "rgba", "block", "cell", "final",
-                                                 "status")]))
-            e2e.append(1e3 * (time.perf_counter() - t0))
-            pass_reads.append(rs["passes"] + 1)
-        e2e_ms = statistics.mean(e2e)
-        d2h_total = d2h + 64 * statistics.mean(pass_reads)
-
-        # Decode of every block once (up to 16M blocks, 4 GB out) through
-        # spr_decode_blocks: the decoder's HBM roofline figure, 8*rate bytes
-        # read and 256 bytes written per block.  The library allocates its
-        # 4-byte error flag from torch's caching allocator here, so no
-        # cudaMalloc sits between the events.
-        nb_vol = int(np.prod([(d + 3) // 4 for d in wl["dims"]]))
-        nb_all = min(nb_vol, 16 << 20)
-        # a contiguous run of block ids centred on the middle z layer (the
-        # mixing layer of the paper-scale field), not the empty bottom slabs
-        first = (nb_vol - nb_all) // 2
-        dec_ids = torch.arange(first, first + nb_all, dtype=torch.int64, device="cuda").to(torch.int32)
-        dec_out = torch.empty((nb_all, 64), dtype=torch.float32, device="cuda")
-        spr.use_torch_allocator()
-        try:
-            for _ in range(2):
-                spr.spr_decode_blocks(comp, nb_vol, wl["rate"], ids=dec_ids, n=nb_all, out=dec_out,
-                                      stream=stream)
-            dec_times = []
-            for i in range(5):
-                flush.fill_(i & 255)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                spr.spr_decode_blocks(comp, nb_vol, wl["rate"], ids=dec_ids, n=nb_all, out=dec_out,
-                                      stream=stream)
-                b.record(stream)
-                b.synchronize()
-                dec_times.append(a.elapsed_time(b))
-        finally:
-            spr.spr_set_allocator()
-        del dec_out, dec_ids
-        dec_all_ms = statistics.median(dec_times)
-        dec_all_gbs = nb_all * (256 + 8 * wl["rate"] + 4) / 1e9 / (dec_all_ms / 1e3)
+        # one generation of the raw volume feeds both encoders: the library's
+        # (the GPU path's input) and, for the CPU baseline, the oracle's own
+        comp, comp_host = compress_volume(wl, spr, torch, library=True, oracle_side=want_cpu)
+        res = measure_workload(wl, args, spr, _lib, torch, stream, rank, world, dist, local, comp)
+        del comp
+        torch.cuda.empty_cache()
+        med = None
+        if wl["field"] == "mixing" and not args.no_medium and not args.dims:
+            mwl = dict(WORKLOADS["medium"])
+            mcomp = compress_volume(mwl, spr, torch)[0]
+            margs = argparse.Namespace(**vars(args))
+            margs.steps = max(16, min(args.steps, 64))
+            med = measure_workload(mwl, margs, spr, _lib, torch, stream, rank, world, dist, local, mcomp,
+                                   headline=False)
+            del mcomp
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and wl["dims"][0] != 2048:
-        try:
-            import oracle
-            oracle.build()
-            comp_host = comp.cpu().numpy()
-            nthreads = os.cpu_count() or 1
-            ms_cpu, det = oracle_sample(wl, 0, 1, nthreads, comp_host)
-            cpu = {"value": round(ms_cpu, 1), "unit": "ms", "cores": nthreads, "kind": "oracle",
-                   "sample": "C oracle (FP64, OpenMP %d threads): decode of all blocks (%.2f s) + "
-                             "ray casting of all %d pixels (%.2f s) of pose 0" %
-                             (nthreads, det["decode_s"], det["pixels"], det["raycast_s"])}
-        except Exception as exc:  # noqa: BLE001
-            cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": "failed: %s" % exc}
+    if want_cpu:
+        cb = cpu_baseline(wl, comp_host, pose(wl, 0))
+        a, o = cb["all"], cb["one"]
+        cpu = {"value": round(a["ms"], 1), "unit": "ms", "cores": a["threads"], "kind": "oracle",
+               "sample": describe_sample(a, wl["W"], wl["H"]) + "; pose 0",
+               "one_core": {"value": round(o["ms"], 1), "unit": "ms", "cores": 1,
+                            "sample": describe_sample(o, wl["W"], wl["H"])},
+               "input": "the oracle's own FRC4 encoding of the synth volume"}
+        del comp_host
     elif rank == 0:
         cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "not run: the oracle holds the 30 GB decoded volume in host memory"}
+               "sample": "not run (--no-cpu-baseline)"}
 
     if rank == 0:
-        clocks = clk.summary()
+        sm = summarise(wl, res, world)
         line = {
             "metric": METRIC,
-            "value": round(ms_image, 4),
+            "value": round(res["ms_image"], 4),
             "unit": "ms",
             "n_gpus": world,
             "steps": args.steps,
             "warmup": args.warmup,
-            "ms_per_step": round(ms_image, 4),
+            "ms_per_step": round(res["ms_image"], 4),
             "higher_is_better": False,
             "scaling": "weak",
             "vs_baseline": None,
@@ -1095,39 +1208,35 @@ def main():
                        "cold_cache_per_step": True,
                        "l2": "256 MB buffer written between timed steps",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "ms_per_pass": round(ms_image * len(stats) / max(1, n_pass), 4),
-            "passes_per_image": round(n_pass / len(stats), 2),
-            "blocks_decoded_per_image": round(blocks / len(stats), 1),
-            "decoded_gbs": round(dec_gbs, 1),
-            "images_per_s": round(1e3 / ms_image * world, 2),
-            "stage_ms_per_image": {k: round(v / max(1, len(prof_stats)), 4) for k, v in stage.items()},
-            "ms_per_pass_index": {str(k): round(statistics.mean(v), 4) for k, v in sorted(per_index.items())},
-            "ray_block_tests_per_s": {
-                "intersect_stage": round(isect_entries / (isect_ms / 1e3), 1) if isect_ms > 0 else None,
-                "whole_render": round(entries_per_image / (ms_image / 1e3), 1),
-                "entries_per_image": round(entries_per_image, 1),
-                "timing": "entries of the instrumented renders over their intersection stage time; "
-                          "entries of the timed renders over their ms to the final image"},
-            "roofline": roofline,
-            "decode_all": {"kernel": "decode_list_kernel", "blocks": nb_all,
-                           "ms": round(dec_all_ms, 4), "achieved": round(dec_all_gbs, 1),
-                           "peak": pk["hbm_gbs"], "unit": "GB/s",
-                           "frac": round(dec_all_gbs / pk["hbm_gbs"], 4),
-                           "first_block": first, "bytes_per_block": 256 + 8 * wl["rate"] + 4,
-                           "timing": "median of 5 CUDA-event timed calls, L2 flushed before each"},
-            "cpu_baseline": cpu,
-            "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": int(d2h_total)},
-            "gpu_launches": int(launches),
-            "clocks": clocks,
+            "ms_median": round(res["ms_image_median"], 4),
         }
+        line.update({k: v for k, v in sm.items() if k != "gpu_launches"})
+        line["roofline"] = res["roofline"]
+        line["stage_roofline"] = res["stage_roofline"]
+        line["decode_all"] = res["decode_all"]
+        line["cpu_baseline"] = cpu
+        line["e2e"] = res["e2e"]
+        line["gpu_launches"] = sm["gpu_launches"]
+        clocks = res["clocks"]
+        if clocks:
+            clocks["window"] = ("nvidia-smi every 50 ms from the first warm-up render (%d renders, "
+                                ">= %.1f s) to the end of the timed renders" % (res["warmup_renders"], args.warm_s))
+        line["clocks"] = clocks
+        if med is not None:
+            msm = summarise(WORKLOADS["medium"], med, world)
+            line["medium"] = {"workload": WORKLOADS["medium"]["name"], "ms": round(med["ms_image"], 4),
+                              "steps": len(med["stats"]),
+                              "passes_per_image": msm["passes_per_image"], "ms_per_pass": msm["ms_per_pass"],
+                              "blocks_decoded_per_image": msm["blocks_decoded_per_image"],
+                              "decoded_gbs": msm["decoded_gbs"], "stage_ms_per_image": msm["stage_ms_per_image"],
+                              "ms_per_pass_index": msm["ms_per_pass_index"],
+                              "roofline": med["roofline"], "stage_roofline": med["stage_roofline"],
+                              "gpu_launches": msm["gpu_launches"]}
         print(json.dumps(line))
         if args.dump:
-            json.dump({"line": line, "steps": [{"render": rs, "passes": ps} for rs, ps in stats],
-                       "profiled": [{"render": rs, "passes": ps} for rs, ps in prof_stats]},
+            json.dump({"line": line, "steps": [{"render": rs, "passes": ps} for rs, ps in res["stats"]],
+                       "profiled": [{"render": rs, "passes": ps} for rs, ps in res["prof_stats"]]},
                       open(args.dump, "w"), indent=1)
-    r.close()
-    vol.close()
     if dist:
         dist.destroy_process_group()
     return 0

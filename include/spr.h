@@ -515,12 +515,16 @@ int spr_debug_scan_withhold(const uint32_t *in, uint32_t *out, int64_t n,
  * let cudaMalloc/cudaFree synchronise the device.  Its look-back scratch is
  * a static device array (256 KiB + 256 B per device), so n is limited to
  * 2^26 elements; a longer n returns SPR_ERR_INVALID_ARG before any device
- * work.  Each call clears the scratch it uses on `stream` before its launch
- * and synchronises `stream` afterwards.  The first call on a device, made
- * with that device current, resolves the scratch address
- * (cudaGetSymbolAddress); make that first call before any stream capture on
- * the device.  Calls that overlap on one device (different streams or
- * unordered host threads) share the scratch and race: order them. */
+ * work.  Each call clears the scratch it uses on `stream` before its launch,
+ * then copies the timeout flag to the host and synchronises `stream`: every
+ * call blocks the host, and none may be made on a capturing stream.  The
+ * first call on a device, made with that device current, resolves the
+ * scratch address (cudaGetSymbolAddress) and loads the scan kernel; under
+ * CUDA's lazy module loading that first call is when the runtime places the
+ * library module (its code and this array) in device memory, so make it
+ * early -- before memory can run out -- and later calls allocate nothing.
+ * Calls that overlap on one device (different streams or unordered host
+ * threads) share the scratch and race: order them. */
 int spr_exclusive_scan_u32_noalloc(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
                                    spr_stream stream);
 

@@ -79,7 +79,8 @@ class _Camera(ctypes.Structure):
 
 class _Volume(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("vals", ctypes.c_void_p),
-                ("fine", ctypes.c_void_p)]
+                ("fine", ctypes.c_void_p), ("comp", ctypes.c_void_p), ("rate", ctypes.c_int32),
+                ("lazy_fine", ctypes.c_int32), ("decodes", ctypes.c_void_p)]
 
 
 def lib():
@@ -116,12 +117,14 @@ def lib():
                 ("orc_spec_count", [i64, i64, i32], i32),
                 ("orc_sizeof_pixel", [], i32),
                 ("orc_sizeof_pass_stats", [], i32),
+                ("orc_sizeof_volume", [], i32),
             ]:
                 f = getattr(L, name)
                 f.argtypes = args
                 f.restype = res
             assert L.orc_sizeof_pixel() == PIXEL_DTYPE.itemsize, "orc_pixel layout"
             assert L.orc_sizeof_pass_stats() == STATS_DTYPE.itemsize, "orc_pass_stats layout"
+            assert L.orc_sizeof_volume() == ctypes.sizeof(_Volume), "orc_volume layout"
     return _lib
 
 
@@ -280,23 +283,54 @@ def ray_dirs(cam, W: int, H: int) -> np.ndarray:
 
 
 class Volume:
-    """A decoded volume plus its fine ranges, as the oracle renderer wants it."""
+    """A decoded volume plus its fine ranges, as the oracle renderer wants it;
+    or, from `on_demand`, the compressed blocks alone, each decoded the first
+    time a ray reaches it (Sec. 3.5) and kept in a bounded per-thread memo
+    for the duration of one render call.  Both forms give identical results."""
 
     def __init__(self, decoded: np.ndarray, dims, fine=None):
-        self.decoded = np.ascontiguousarray(decoded, dtype=np.float32)
-        assert self.decoded.shape == (dims[2], dims[1], dims[0])
         self.dims = tuple(int(d) for d in dims)
         self.fine = None if fine is None else np.ascontiguousarray(fine, dtype=np.float32)
+        self.comp = None
+        self.rate = 0
+        self.last_decodes = 0
+        self._decodes = np.zeros(1, dtype=np.int64)
         self._s = _Volume()
         self._s.dims[:] = list(self.dims)
-        self._s.vals = self.decoded.ctypes.data
+        if decoded is None:
+            self.decoded = None
+            self._s.vals = None
+        else:
+            self.decoded = np.ascontiguousarray(decoded, dtype=np.float32)
+            assert self.decoded.shape == (dims[2], dims[1], dims[0])
+            self._s.vals = self.decoded.ctypes.data
         self._s.fine = None if self.fine is None else self.fine.ctypes.data
+        self._s.decodes = self._decodes.ctypes.data
 
     @classmethod
     def from_compressed(cls, comp, dims, rate):
         dec = decode_volume(comp, dims, rate)
         _, fine, _ = ranges(dec, dims)
         return cls(dec, dims, fine)
+
+    @classmethod
+    def on_demand(cls, comp, dims, rate: int, lazy_fine: bool = False):
+        """Blocks decoded on demand from `comp` (the volume's FRC4 stream at
+        `rate` bits/value).  With lazy_fine, fine ranges are formed on demand
+        too, so that render(..., lists=True) works without a decoded grid."""
+        v = cls(None, dims)
+        nb = nblocks(dims)
+        c = np.ascontiguousarray(comp, dtype=np.uint8)
+        assert c.size >= nb[0] * nb[1] * nb[2] * 8 * rate
+        v.comp = c
+        v.rate = int(rate)
+        v._s.comp = c.ctypes.data
+        v._s.rate = int(rate)
+        v._s.lazy_fine = 1 if lazy_fine else 0
+        return v
+
+    def _done(self):
+        self.last_decodes = int(self._decodes[0])
 
 
 def render(vol: Volume, cam, W: int, H: int, iso: float, pixels=None, full_lists=False,
@@ -314,6 +348,7 @@ def render(vol: Volume, cam, W: int, H: int, iso: float, pixels=None, full_lists
     L = lib()
     rc = L.orc_render(ctypes.byref(vol._s), ctypes.byref(c), W, H, float(iso), pix_p, n,
                       1 if (full_lists or lists) else 0, _ptr(out), None, None, nt)
+    vol._done()
     if rc:
         raise ValueError("orc_render failed: %d" % rc)
     if not lists:
@@ -325,6 +360,7 @@ def render(vol: Volume, cam, W: int, H: int, iso: float, pixels=None, full_lists
     out2 = np.zeros(n, dtype=PIXEL_DTYPE)
     rc = L.orc_render(ctypes.byref(vol._s), ctypes.byref(c), W, H, float(iso), pix_p, n, 1,
                       _ptr(out2), _ptr(off), _ptr(vis), nt)
+    vol._done()
     if rc:
         raise ValueError("orc_render failed: %d" % rc)
     return out2, off, vis
@@ -341,6 +377,7 @@ def march(vol: Volume, cam, W: int, H: int, iso: float, pixels=None, nthreads=No
     out = np.zeros(n, dtype=PIXEL_DTYPE)
     rc = lib().orc_march(ctypes.byref(vol._s), ctypes.byref(c), W, H, float(iso), pix_p, n,
                          _ptr(out), nt)
+    vol._done()
     if rc:
         raise ValueError("orc_march failed: %d" % rc)
     return out

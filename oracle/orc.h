@@ -144,9 +144,25 @@ int orc_ranges(const float *decoded, const int32_t dims[3],
  */
 typedef struct {
     int32_t dims[3];
-    const float *vals;   /* dense decoded volume (x fastest) */
+    const float *vals;   /* dense decoded volume (x fastest), or NULL (below) */
     const float *fine;   /* fine ranges (nb*2), needed for visible-block lists */
+    /* On-demand form, used when vals is NULL (Sec. 3.5: the renderer
+     * decompresses the blocks its rays reach, not the whole volume).  A
+     * voxel's value is read from its block, decoded from comp (FRC4 at
+     * `rate`) the first time it is needed and kept in a bounded memo
+     * (ORC_MEMO_LINES blocks per thread, one memo per render call).
+     * Decoding is a pure function of the block's bits, so the results are
+     * identical to the dense form's.  With lazy_fine and fine == NULL, the
+     * fine range of a block is formed on demand from the raw ranges of its
+     * +x/+y/+z neighbours (the definition of orc_ranges), so that visible
+     * lists need no precomputed grid either. */
+    const uint8_t *comp;
+    int32_t rate;
+    int32_t lazy_fine;
+    int64_t *decodes;    /* if non-NULL, receives the blocks decoded by the call */
 } orc_volume;
+
+#define ORC_MEMO_LINES (1 << 16)
 
 typedef struct {
     float eye[3], p00[3], du[3], dv[3];
@@ -239,6 +255,7 @@ int orc_spec_count(int64_t slots, int64_t n_active, int k_max);
 
 int orc_sizeof_pixel(void);
 int orc_sizeof_pass_stats(void);
+int orc_sizeof_volume(void);
 
 #ifdef __cplusplus
 }

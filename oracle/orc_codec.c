@@ -259,6 +259,11 @@ static int encode_volume(const float *vf, const uint8_t *vu, const int32_t dims[
     int64_t nb[3];
     for (int a = 0; a < 3; a++) nb[a] = (dims[a] + 3) / 4;
     int64_t bytes = 8 * (int64_t)rate;
+    int bad = 0;
+    /* blocks are independent: the rows of blocks are encoded in parallel */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) collapse(2) reduction(| : bad)
+#endif
     for (int64_t bz = 0; bz < nb[2]; bz++)
         for (int64_t by = 0; by < nb[1]; by++)
             for (int64_t bx = 0; bx < nb[0]; bx++) {
@@ -274,10 +279,9 @@ static int encode_volume(const float *vf, const uint8_t *vu, const int32_t dims[
                             blk[x + 4 * y + 16 * z] = vf ? vf[g] : (float)vu[g] / 255.0f;
                         }
                 int64_t b = bx + nb[0] * (by + nb[1] * bz);
-                int rc = orc_encode_block(blk, rate, out + b * bytes);
-                if (rc) return rc;
+                if (orc_encode_block(blk, rate, out + b * bytes)) bad = 1;
             }
-    return 0;
+    return bad ? -1 : 0;
 }
 
 int orc_encode_volume_f32(const float *vol, const int32_t dims[3], int rate, uint8_t *out)

@@ -299,21 +299,150 @@ static int cell_first_root(const cell_fn *f, double L, double *s_hit, uint32_t *
     return 0;
 }
 
-static double voxel(const orc_volume *vol, int64_t x, int64_t y, int64_t z)
+/* ---------------- voxel access: dense, or blocks decoded on demand ---------- */
+/* One reader per thread and render call.  In the on-demand form a memo line
+ * holds one decoded block (64 values, x fastest) and the min/max of its
+ * in-domain voxels; line = hash(block id), replaced when another block
+ * maps there. */
+typedef struct {
+    const orc_volume *vol;
+    int64_t nb[3];
+    int64_t *tag;    /* block held by each line, -1 when empty */
+    float *val;      /* 64 values per line */
+    float *raw;      /* min, max per line */
+    int64_t decodes;
+    int ok;
+} orc_reader;
+
+static int reader_init(orc_reader *rd, const orc_volume *vol)
 {
-    return vol->vals[x + (int64_t)vol->dims[0] * (y + (int64_t)vol->dims[1] * z)];
+    memset(rd, 0, sizeof *rd);
+    rd->vol = vol;
+    rd->ok = 1;
+    for (int a = 0; a < 3; a++) rd->nb[a] = (vol->dims[a] + 3) / 4;
+    if (vol->vals) return 0;
+    if (!vol->comp || vol->rate < 1 || vol->rate > 32) return -1;
+    rd->tag = (int64_t *)malloc(sizeof(int64_t) * ORC_MEMO_LINES);
+    rd->val = (float *)malloc(sizeof(float) * 64 * ORC_MEMO_LINES);
+    rd->raw = (float *)malloc(sizeof(float) * 2 * ORC_MEMO_LINES);
+    if (!rd->tag || !rd->val || !rd->raw) return -2;
+    for (int64_t i = 0; i < ORC_MEMO_LINES; i++) rd->tag[i] = -1;
+    return 0;
 }
 
-static void cell_corners(const orc_volume *vol, const int64_t c[3], double v[8])
+static void reader_free(orc_reader *rd)
+{
+    free(rd->tag);
+    free(rd->val);
+    free(rd->raw);
+    rd->tag = NULL;
+    rd->val = rd->raw = NULL;
+}
+
+/* the memo line holding decoded block b (decoding it if it is not there) */
+static int64_t reader_line(orc_reader *rd, int64_t b)
+{
+    uint64_t h = (uint64_t)b * 0x9E3779B97F4A7C15ull;
+    int64_t line = (int64_t)(h >> 48) & (ORC_MEMO_LINES - 1);
+    if (rd->tag[line] == b) return line;
+    const orc_volume *vol = rd->vol;
+    float *v = rd->val + 64 * line;
+    if (orc_decode_block(vol->comp + b * 8 * (int64_t)vol->rate, vol->rate, v)) rd->ok = 0;
+    rd->decodes++;
+    /* min/max of the block's in-domain voxels (raw(b) of orc_ranges) */
+    int64_t bx = b % rd->nb[0], by = (b / rd->nb[0]) % rd->nb[1], bz = b / (rd->nb[0] * rd->nb[1]);
+    float mn = INFINITY, mx = -INFINITY;
+    for (int z = 0; z < 4 && 4 * bz + z < vol->dims[2]; z++)
+        for (int y = 0; y < 4 && 4 * by + y < vol->dims[1]; y++)
+            for (int x = 0; x < 4 && 4 * bx + x < vol->dims[0]; x++) {
+                float q = v[x + 4 * y + 16 * z];
+                if (q < mn) mn = q;
+                if (q > mx) mx = q;
+            }
+    rd->raw[2 * line] = mn;
+    rd->raw[2 * line + 1] = mx;
+    rd->tag[line] = b;
+    return line;
+}
+
+static double voxel(orc_reader *rd, int64_t x, int64_t y, int64_t z)
+{
+    const orc_volume *vol = rd->vol;
+    if (vol->vals) return vol->vals[x + (int64_t)vol->dims[0] * (y + (int64_t)vol->dims[1] * z)];
+    int64_t b = (x >> 2) + rd->nb[0] * ((y >> 2) + rd->nb[1] * (z >> 2));
+    int64_t line = reader_line(rd, b);
+    return rd->val[64 * line + (x & 3) + 4 * (y & 3) + 16 * (z & 3)];
+}
+
+/* 1 when iso lies in the fine range of block b, 0 when not, -1 when the
+ * volume has no fine ranges (no visible lists) */
+static int block_visible(orc_reader *rd, int64_t b, float iso)
+{
+    const orc_volume *vol = rd->vol;
+    if (vol->fine) return vol->fine[2 * b] <= iso && iso <= vol->fine[2 * b + 1];
+    if (vol->vals || !vol->lazy_fine) return -1;
+    /* fine(b) = union of raw(b + o), o in {0,1}^3, over neighbours that exist */
+    int64_t bx = b % rd->nb[0], by = (b / rd->nb[0]) % rd->nb[1], bz = b / (rd->nb[0] * rd->nb[1]);
+    float mn = INFINITY, mx = -INFINITY;
+    for (int o = 0; o < 8; o++) {
+        int64_t x = bx + (o & 1), y = by + ((o >> 1) & 1), z = bz + (o >> 2);
+        if (x >= rd->nb[0] || y >= rd->nb[1] || z >= rd->nb[2]) continue;
+        int64_t line = reader_line(rd, x + rd->nb[0] * (y + rd->nb[1] * z));
+        if (rd->raw[2 * line] < mn) mn = rd->raw[2 * line];
+        if (rd->raw[2 * line + 1] > mx) mx = rd->raw[2 * line + 1];
+    }
+    return mn <= iso && iso <= mx;
+}
+
+static void cell_corners(orc_reader *rd, const int64_t c[3], double v[8])
 {
     for (int k = 0; k < 8; k++)
-        v[k] = voxel(vol, c[0] + (k & 1), c[1] + ((k >> 1) & 1), c[2] + (k >> 2));
+        v[k] = voxel(rd, c[0] + (k & 1), c[1] + ((k >> 1) & 1), c[2] + (k >> 2));
+}
+
+/* readers for up to n threads; returns NULL on failure */
+static orc_reader *readers_new(const orc_volume *vol, int n)
+{
+    orc_reader *rd = (orc_reader *)calloc((size_t)n, sizeof(orc_reader));
+    if (!rd) return NULL;
+    for (int i = 0; i < n; i++)
+        if (reader_init(&rd[i], vol)) {
+            for (int j = 0; j <= i; j++) reader_free(&rd[j]);
+            free(rd);
+            return NULL;
+        }
+    return rd;
+}
+
+/* frees the readers; returns -1 if a block failed to decode */
+static int readers_done(const orc_volume *vol, orc_reader *rd, int n)
+{
+    int64_t dec = 0;
+    int ok = 1;
+    for (int i = 0; i < n; i++) {
+        dec += rd[i].decodes;
+        ok &= rd[i].ok;
+        reader_free(&rd[i]);
+    }
+    free(rd);
+    if (vol->decodes) *vol->decodes = dec;
+    return ok ? 0 : -1;
+}
+
+static int thread_index(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
 }
 
 /* ---------------- one pixel ---------------------------------------------- */
-static void render_pixel(const orc_volume *vol, const ray_t *r, float iso, int full_list,
+static void render_pixel(orc_reader *rd, const ray_t *r, float iso, int full_list,
                          orc_pixel *out, uint32_t *vis_out)
 {
+    const orc_volume *vol = rd->vol;
     memset(out, 0, sizeof *out);
     out->t = INFINITY;
     out->depth = INFINITY;
@@ -353,7 +482,7 @@ static void render_pixel(const orc_volume *vol, const ray_t *r, float iso, int f
         int64_t bid = (c[0] >> 2) + nb[0] * ((c[1] >> 2) + nb[1] * (c[2] >> 2));
         if (bid != prev_block) {
             prev_block = bid;
-            if (vol->fine && vol->fine[2 * bid] <= iso && iso <= vol->fine[2 * bid + 1]) {
+            if (block_visible(rd, bid, iso) == 1) {
                 if (vis_out) vis_out[out->n_visible] = (uint32_t)bid;
                 out->n_visible++;
             }
@@ -361,7 +490,7 @@ static void render_pixel(const orc_volume *vol, const ray_t *r, float iso, int f
 
         if (!out->hit) {
             cell_fn f;
-            cell_corners(vol, c, f.v);
+            cell_corners(rd, c, f.v);
             int below = 0, above = 0;
             for (int k = 0; k < 8; k++) {
                 below += f.v[k] < iso;
@@ -383,8 +512,7 @@ static void render_pixel(const orc_volume *vol, const ray_t *r, float iso, int f
                     for (int a = 0; a < 3; a++) out->cell[a] = (int32_t)c[a];
                     out->block = (uint32_t)bid;
                     out->hit_index = out->n_visible - 1;
-                    if (vol->fine && !(vol->fine[2 * bid] <= iso && iso <= vol->fine[2 * bid + 1]))
-                        out->amb |= ORC_INTERNAL_HIT_NOT_VISIBLE;
+                    if (block_visible(rd, bid, iso) == 0) out->amb |= ORC_INTERNAL_HIT_NOT_VISIBLE;
                     for (int a = 0; a < 3; a++) {
                         double p = r->e[a] + out->t * r->d[a];
                         if (fabs(p - rint(p)) < EPS_FACE) out->amb |= ORC_AMB_FACE;
@@ -422,20 +550,23 @@ int orc_render(const orc_volume *vol, const orc_camera *cam, int W, int H, float
     if (orc_check_camera(cam, vol->dims)) return -1;
     if (W < 1 || H < 1) return -1;
     if (!pixels) npix = (int64_t)W * H;
-#ifdef _OPENMP
     if (nthreads < 1) nthreads = 1;
+#ifndef _OPENMP
+    nthreads = 1;
+#endif
+    orc_reader *rd = readers_new(vol, nthreads);
+    if (!rd) return -2;
+#ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
-#else
-    (void)nthreads;
 #endif
     for (int64_t k = 0; k < npix; k++) {
         int64_t p = pixels ? pixels[k] : k;
         ray_t r;
         make_ray(&r, cam, vol->dims, W, H, (int)(p % W), (int)(p / W));
-        render_pixel(vol, &r, iso, full_lists, &out[k],
+        render_pixel(&rd[thread_index()], &r, iso, full_lists, &out[k],
                      (vis_off && vis_out) ? vis_out + vis_off[k] : NULL);
     }
-    return 0;
+    return readers_done(vol, rd, nthreads) ? -3 : 0;
 }
 
 int64_t orc_trace_cells(const int32_t dims[3], const orc_camera *cam, int W, int H, int px,
@@ -495,8 +626,9 @@ uint32_t orc_entry_block(const int32_t dims[3], const orc_camera *cam, int W, in
 }
 
 /* ---------------- independent dense march --------------------------------- */
-static double field_at(const orc_volume *vol, const double p[3], double iso)
+static double field_at(orc_reader *rd, const double p[3], double iso)
 {
+    const orc_volume *vol = rd->vol;
     int64_t c[3];
     double u[3], v[8];
     for (int a = 0; a < 3; a++) {
@@ -506,7 +638,7 @@ static double field_at(const orc_volume *vol, const double p[3], double iso)
         c[a] = (int64_t)f;
         u[a] = p[a] - f;
     }
-    cell_corners(vol, c, v);
+    cell_corners(rd, c, v);
     return tri_eval(v, u) - iso;
 }
 
@@ -515,13 +647,17 @@ int orc_march(const orc_volume *vol, const orc_camera *cam, int W, int H, float 
 {
     if (orc_check_camera(cam, vol->dims)) return -1;
     if (!pixels) npix = (int64_t)W * H;
-#ifdef _OPENMP
     if (nthreads < 1) nthreads = 1;
+#ifndef _OPENMP
+    nthreads = 1;
+#endif
+    orc_reader *rds = readers_new(vol, nthreads);
+    if (!rds) return -2;
+#ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
-#else
-    (void)nthreads;
 #endif
     for (int64_t k = 0; k < npix; k++) {
+        orc_reader *rd = &rds[thread_index()];
         int64_t pix = pixels ? pixels[k] : k;
         ray_t r;
         make_ray(&r, cam, vol->dims, W, H, (int)(pix % W), (int)(pix / W));
@@ -540,7 +676,7 @@ int orc_march(const orc_volume *vol, const orc_camera *cam, int W, int H, float 
         double dt = 1e-3 / dn;
         double p[3];
         for (int a = 0; a < 3; a++) p[a] = r.e[a] + t0 * r.d[a];
-        double tp = t0, fp = field_at(vol, p, iso);
+        double tp = t0, fp = field_at(rd, p, iso);
         if (fp == 0.0) {
             o->hit = 1;
             o->t = t0;
@@ -549,14 +685,14 @@ int orc_march(const orc_volume *vol, const orc_camera *cam, int W, int H, float 
                 double t = t0 + (double)i * dt;
                 if (t > t1) t = t1;
                 for (int a = 0; a < 3; a++) p[a] = r.e[a] + t * r.d[a];
-                double f = field_at(vol, p, iso);
+                double f = field_at(rd, p, iso);
                 if (f == 0.0 || (f < 0.0) != (fp < 0.0)) {
                     double lo = tp, hi = t, flo = fp;
                     if (f != 0.0) {
                         for (int it = 0; it < 200 && hi - lo > 1e-14 * (1.0 + fabs(hi)); it++) {
                             double mid = 0.5 * (lo + hi), q[3];
                             for (int a = 0; a < 3; a++) q[a] = r.e[a] + mid * r.d[a];
-                            double fm = field_at(vol, q, iso);
+                            double fm = field_at(rd, q, iso);
                             if (fm == 0.0) {
                                 lo = hi = mid;
                                 break;
@@ -582,5 +718,5 @@ int orc_march(const orc_volume *vol, const orc_camera *cam, int W, int H, float 
         }
         if (o->hit) o->depth = o->t * dn;
     }
-    return 0;
+    return readers_done(vol, rds, nthreads) ? -3 : 0;
 }

@@ -246,3 +246,4 @@ int orc_simulate(int W, int H, const int32_t dims[3], const int32_t *enters,
 /* struct sizes, so that bindings can check their layouts */
 int orc_sizeof_pixel(void) { return (int)sizeof(orc_pixel); }
 int orc_sizeof_pass_stats(void) { return (int)sizeof(orc_pass_stats); }
+int orc_sizeof_volume(void) { return (int)sizeof(orc_volume); }

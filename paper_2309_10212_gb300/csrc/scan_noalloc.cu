@@ -56,7 +56,12 @@ struct NoAllocEmit {
 };
 
 // Per-device set-up: the scratch address (cudaGetSymbolAddress with the
-// device current) and the SM count that sizes the persistent grid.
+// device current), the SM count that sizes the persistent grid, and the
+// kernel itself.  Under CUDA's lazy module loading the module holding the
+// array and the kernel's code are placed in device memory the first time
+// they are used; resolving the symbol and querying the kernel's attributes
+// here makes both happen in this first call, not in a later one (which may
+// then run when device memory is exhausted).
 constexpr int kMaxDevices = 64;
 struct DeviceSetup {
     unsigned long long *scratch = nullptr;
@@ -83,6 +88,10 @@ int setup_for_current_device(DeviceSetup &out)
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess)
             return set_error(SPR_ERR_CUDA, "cudaDeviceGetAttribute failed: %s", cudaGetErrorString(e));
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, compact_kernel<NoAllocCount, NoAllocEmit>);
+        if (e != cudaSuccess)
+            return set_error(SPR_ERR_CUDA, "loading the scan kernel failed: %s", cudaGetErrorString(e));
         d.sms = sms > 0 ? sms : 1;
         d.scratch = static_cast<unsigned long long *>(p);
     }
