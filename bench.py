@@ -249,8 +249,9 @@ def sample_rows(H, bands, rows):
 
 
 # Oracle samples (bands x rows): all host cores, and one core.  Sized for
-# about 10-30 s of CPU work at paper scale on a 16-core host.
-ORACLE_SAMPLE = {"all": (8, 4), "one": (2, 1)}
+# about 10-30 s of CPU work at paper scale on a 16-core host (about 1.5 s and
+# 4 s of wall time).
+ORACLE_SAMPLE = {"all": (16, 8), "one": (6, 3)}
 
 
 def oracle_time(wl, comp_host, cam, rows, nthreads):
@@ -664,6 +665,104 @@ def serve_trace(n, rate_hz, seed=11):
     return out
 
 
+def serve_volumes(spr, torch):
+    """The serving mix's three resident volumes at 2 bits/value, with their
+    per-view cache budgets: [(volume, cache bytes per view)]."""
+    import synth
+    vols = []
+    for name, dims, gen, cache in SERVE_VOLUMES:
+        if gen == "paper":
+            comp = compressed_on_device(WORKLOADS["paper"], spr, torch)
+        else:
+            n = 100 if dims[0] == 256 else 800
+            u8 = synth.volumes.gaussian_blobs(dims, seed=6 if dims[0] == 256 else 7, n=n, device="cuda")
+            comp = spr.spr_encode_u8(u8, 2)
+            del u8
+        vols.append((spr.spr_create_volume(dims, 2, comp), cache))
+        del comp
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return vols
+
+
+def run_batched(args):
+    """Renders of several volumes in one graph launch (spr_batch_render)
+    against the plain loop of one render at a time, on the serving mix:
+    three resident volumes (256^3 and 1024^3 Gaussian blobs, the
+    2048x2048x1920 mixing layer; 2 bits/value), resolutions 640x360 /
+    1280x720 / 1920x1080, random cameras and isovalues in [0.2, 0.8], an
+    8 GB cache budget.  A burst of requests is split in two: the first half
+    tunes the batch's knobs (views per renderer, the cache split among the
+    renderers, k_max) and the plain loop's k_max; the second half is timed
+    in both forms (device time, cold caches), every image compared."""
+    import torch
+
+    from paper_2309_10212_gb300 import build
+    build.build()
+    import paper_2309_10212_gb300 as spr
+    from paper_2309_10212_gb300 import tune
+    t0 = time.perf_counter()
+    vols = serve_volumes(spr, torch)
+    setup_s = time.perf_counter() - t0
+    trace = serve_trace(args.batch_requests, args.serve_rate)
+    half = len(trace) // 2
+    tune_set, eval_set = trace[:half], trace[half:]
+    per_view = {i: c for i, (_, c) in enumerate(vols)}
+    handles = [v for v, _ in vols]
+    total = 8 << 30
+    stream = torch.cuda.Stream()
+    out = {"config": "serving mix: volumes " + ", ".join(v[0] for v in SERVE_VOLUMES) +
+                     "; resolutions 640x360/1280x720/1920x1080; iso U[0.2,0.8]; 8 GB cache budget; "
+                     "%d requests (%d tune, %d timed); cold caches" % (len(trace), half, len(eval_set)),
+           "setup_s": round(setup_s, 1)}
+    with torch.cuda.stream(stream):
+        runner = tune.BatchRunner(handles, stream)
+        best = tune.autotune_batch(runner, tune_set, total, per_view, views=(1, 2, 4, 8),
+                                   splits=("per_view", "equal", "pixels"), k_max=(16, 64))
+        out["autotune"] = {"chosen": {k: best[k] for k in ("views", "split", "k_max")},
+                           "table": best["table"]}
+        plain_tune = []
+        for k in (16, 64):
+            pool = {}
+            tune.run_requests_plain(handles, tune_set, per_view, k, stream, pool)
+            plain_tune.append(dict(k_max=k, **tune.run_requests_plain(handles, tune_set, per_view, k, stream, pool)))
+            for r in pool.values():
+                r.close()
+        kp = min(plain_tune, key=lambda x: x["ms"])["k_max"]
+        out["plain_autotune"] = {"chosen_k_max": kp, "table": plain_tune}
+        # the timed half: plain loop (images kept), then the batched form
+        imgs = {}
+
+        def keep_plain(i, fb):
+            imgs[i] = {k: fb[k].clone() for k in ("depth", "block", "status", "rgba")}
+        pool = {}
+        tune.run_requests_plain(handles, eval_set, per_view, kp, stream, pool)
+        out["plain"] = tune.run_requests_plain(handles, eval_set, per_view, kp, stream, pool, keep=keep_plain)
+        for r in pool.values():
+            r.close()
+        same = {"n": 0}
+
+        def keep_batched(i, fb):
+            same["n"] += all(torch.equal(fb[k], imgs[i][k]) for k in imgs[i])
+        V, split, k = best["views"], best["split"], best["k_max"]
+        runner.run(eval_set, V, split, total, per_view, k)
+        out["batched"] = runner.run(eval_set, V, split, total, per_view, k)
+        runner.run(eval_set, V, split, total, per_view, k, keep=keep_batched)
+        out["batched"].update(views=V, split=split, k_max=k)
+        runner.close()
+        out["identical_images"] = "%d/%d" % (same["n"], len(eval_set))
+        out["speedup_device"] = round(out["plain"]["ms"] / out["batched"]["ms"], 3)
+        out["speedup_wall"] = round(out["plain"]["wall_ms"] / out["batched"]["wall_ms"], 3)
+    for v, _ in vols:
+        v.close()
+    with open(args.batched, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps({"batched": args.batched, "plain": out["plain"], "batched_form": out["batched"],
+                      "identical_images": out["identical_images"], "speedup_device": out["speedup_device"],
+                      "speedup_wall": out["speedup_wall"]}))
+    return 0
+
+
 def run_serve(args):
     """The render service (config: 256 requests arriving as a Poisson process
     at 20/s over three resident volumes, resolutions 640x360 / 1280x720 /
@@ -681,19 +780,7 @@ def run_serve(args):
     out = {"config": "256 requests, Poisson 20/s, volumes " + ", ".join(v[0] for v in SERVE_VOLUMES) +
                      ", resolutions 640x360/1280x720/1920x1080, iso U[0.2,0.8], 8 GB memory budget"}
     t0 = time.perf_counter()
-    vols = []
-    for name, dims, gen, cache in SERVE_VOLUMES:
-        if gen == "paper":
-            comp = compressed_on_device(WORKLOADS["paper"], spr, torch)
-        else:
-            n = 100 if dims[0] == 256 else 800
-            u8 = synth.volumes.gaussian_blobs(dims, seed=6 if dims[0] == 256 else 7, n=n, device="cuda")
-            comp = spr.spr_encode_u8(u8, 2)
-            del u8
-        vols.append((spr.spr_create_volume(dims, 2, comp), cache))
-        del comp
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
+    vols = serve_volumes(spr, torch)
     out["setup_s"] = round(time.perf_counter() - t0, 1)
     trace = serve_trace(args.serve_requests, args.serve_rate)
 
@@ -872,6 +959,8 @@ def measure_workload(wl, args, spr, _lib, torch, stream, rank, world, dist, loca
     spr.spr_set_profiling(r, False)
     if args.warp_walk >= 0:
         spr.spr_set_warp_walk_threshold(r, args.warp_walk)
+    if args.seg_lanes >= 0:
+        spr.spr_set_segment_walk(r, args.seg_lanes)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     L = _lib.load()
@@ -1106,10 +1195,16 @@ def main():
     ap.add_argument("--decode-slab", action="store_true",
                     help="instead of the bench line: the decode rate of the paper-scale field's "
                          "interface blocks (one JSON line)")
+    ap.add_argument("--batched", default="",
+                    help="instead of the bench line: several volumes rendered by one graph launch against "
+                         "the plain one-at-a-time loop on the serving mix (JSON to this file)")
+    ap.add_argument("--batch-requests", type=int, default=96)
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--warp-walk", type=int, default=-1,
                     help="live-ray count below which a pass walks one ray per warp (-1: the library default)")
+    ap.add_argument("--seg-lanes", type=int, default=-1,
+                    help="lane budget of the segmented walk (-1: the library default, 0: off)")
     ap.add_argument("--k-max", type=int, default=0,
                     help="override the workload's speculation limit (k sweeps; 0 keeps it)")
     args = ap.parse_args()
@@ -1131,6 +1226,8 @@ def main():
         return run_learned(args, wl)
     if args.decode_slab:
         return run_decode_slab(args)
+    if args.batched:
+        return run_batched(args)
     if args.warmup < 3:
         args.warmup = 3
 

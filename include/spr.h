@@ -266,6 +266,22 @@ int spr_set_speculation(spr_renderer *r, int mode, int k, int k_max);
  * the same blocks in the same order (Sec. 3.3).  Takes effect at the next
  * render or pass. */
 int spr_set_warp_walk_threshold(spr_renderer *r, int64_t n_rays);
+/* Segmented walk (no counterpart in the paper, results unchanged): a pass of
+ * n live rays with lanes / n >= 2 gives each ray a group of G lanes (G the
+ * largest power of two <= min(lanes / n, 32)).  The ray's remaining path is
+ * cut at block planes of the axis along which its direction is largest into
+ * G parts of equal block count; each lane walks one part (the first resumes
+ * the saved walk, the others start at the exact crossing time of their first
+ * plane) and the group keeps the first k visible blocks in walk order -- the
+ * same blocks, in the same order, as the one-lane walk (Sec. 3.3).  Passes
+ * with lanes / n < 2 use the walks above.  Default 262144 lanes; 0 turns
+ * it off.  Takes effect at the next render or pass. */
+int spr_set_segment_walk(spr_renderer *r, int64_t lanes);
+/* Intersection variant (results unchanged): on = stage each visible block's
+ * 5^3 dual grid in shared memory and intersect its entries from there, as
+ * Sec. 3.7's work groups do; off (the default) = read each cell's corners
+ * from the cache slots.  Takes effect at the next render or pass. */
+int spr_set_intersect_staging(spr_renderer *r, int on);
 /* empty the block cache (the next pass decodes from scratch) */
 int spr_reset_cache(spr_renderer *r);
 /* per-pass CUDA-event timing of the stages (adds host synchronisation) */
@@ -315,6 +331,29 @@ int spr_render_query(spr_renderer *r, int32_t *passes_done, int32_t *done);
 /* Wait for the submitted render and report it as spr_render_to_convergence
  * does (same statuses, e.g. SPR_ERR_NOT_CONVERGED). */
 int spr_render_collect(spr_renderer *r, spr_render_stats *out, spr_pass_stats *per_pass);
+/* Batched renders of several volumes (no counterpart in the paper, which
+ * renders one view of one volume; Sec. 4's shared speculation budget and
+ * cache already generalise to the views of one renderer).  A batch lists n
+ * renderers -- of the same or different volumes, image sizes, view counts
+ * and cache budgets -- and spr_batch_render renders all of them with ONE
+ * graph launch on `stream`: per renderer, the start of its render (ray
+ * generation) as a child graph, then its pass loop as a conditional while
+ * node; the branches are independent, so the renders run concurrently.
+ * Each renderer keeps its own block cache, brick masks and wavefront, and
+ * its images equal those of its own spr_render_to_convergence.  Every
+ * renderer must have a camera and start a fresh render (a set_camera,
+ * set_view or set_isovalue since its last render), else SPR_ERR_INVALID_ARG.
+ * stats (n entries, may be NULL) receives each renderer's statistics; its
+ * ms_total is the batch's device time.  Blocks until the batch is done.  The
+ * graph is captured at the first render and again when a renderer's buffers
+ * or cache size changed.  The renderers must outlive the batch and are not
+ * used elsewhere while spr_batch_render runs; a renderer may be in several
+ * batches. */
+typedef struct spr_batch spr_batch;
+int spr_batch_create(spr_renderer *const *renderers, int n, spr_batch **out);
+int spr_batch_destroy(spr_batch *b);
+int spr_batch_render(spr_batch *b, spr_stream stream, int max_passes, spr_render_stats *stats);
+
 /* device bytes the renderer holds now (buffers grown by earlier renders
  * included) */
 int spr_renderer_memory(const spr_renderer *r, size_t *device_bytes);

@@ -154,6 +154,8 @@ PROTOTYPES = {
     "spr_set_cache_budget": ([_vp, _sz], _i32),
     "spr_set_speculation": ([_vp, _i32, _i32, _i32], _i32),
     "spr_set_warp_walk_threshold": ([_vp, _i64], _i32),
+    "spr_set_segment_walk": ([_vp, _i64], _i32),
+    "spr_set_intersect_staging": ([_vp, _i32], _i32),
     "spr_reset_cache": ([_vp], _i32),
     "spr_set_profiling": ([_vp, _i32], _i32),
     "spr_render_pass": ([_vp, _vp, _vp], _i32),
@@ -164,6 +166,9 @@ PROTOTYPES = {
     "spr_debug_scan_withhold": ([_vp, _vp, _i64, _i64, _i64, _vp], _i32),
     "spr_exclusive_scan_u32_noalloc": ([_vp, _vp, _i64, _vp, _vp], _i32),
     "spr_render_submit": ([_vp, _vp, _i32], _i32),
+    "spr_batch_create": ([_vp, _i32, _vp], _i32),
+    "spr_batch_destroy": ([_vp], _i32),
+    "spr_batch_render": ([_vp, _vp, _i32, _vp], _i32),
     "spr_render_query": ([_vp, _vp, _vp], _i32),
     "spr_render_collect": ([_vp, _vp, _vp], _i32),
     "spr_renderer_memory": ([_vp, _vp], _i32),

@@ -265,6 +265,14 @@ def spr_set_warp_walk_threshold(r: Renderer, n_rays: int):
     check(load().spr_set_warp_walk_threshold(r.handle, int(n_rays)))
 
 
+def spr_set_segment_walk(r: Renderer, lanes: int):
+    check(load().spr_set_segment_walk(r.handle, int(lanes)))
+
+
+def spr_set_intersect_staging(r: Renderer, on: bool):
+    check(load().spr_set_intersect_staging(r.handle, 1 if on else 0))
+
+
 def spr_reset_cache(r: Renderer):
     check(load().spr_reset_cache(r.handle))
 
@@ -289,6 +297,40 @@ def spr_render_to_convergence(r: Renderer, max_passes: int = 10000, stream=None,
     if not (allow_partial and status == _lib.SPR_ERR_NOT_CONVERGED):
         check(status)
     return rs.as_dict(), [per[i].as_dict() for i in range(min(rs.passes, max_passes, 4096))]
+
+
+class Batch:
+    """Renderers rendered together by one graph launch (spr_batch_*)."""
+
+    def __init__(self, handle, renderers):
+        self.handle = handle
+        self.renderers = list(renderers)   # kept alive with the batch
+
+    def close(self):
+        if self.handle:
+            check(load().spr_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spr_batch_create(renderers) -> Batch:
+    arr = (ctypes.c_void_p * len(renderers))(*[r.handle.value if hasattr(r.handle, "value") else r.handle
+                                              for r in renderers])
+    h = ctypes.c_void_p()
+    check(load().spr_batch_create(arr, len(renderers), ctypes.byref(h)))
+    return Batch(h, renderers)
+
+
+def spr_batch_render(b: Batch, max_passes: int = 10000, stream=None):
+    """Returns each renderer's render stats."""
+    stats = (_lib.RenderStats * len(b.renderers))()
+    check(load().spr_batch_render(b.handle, _stream(stream), int(max_passes), stats))
+    return [stats[i].as_dict() for i in range(len(b.renderers))]
 
 
 def spr_get_framebuffer(r: Renderer) -> dict:

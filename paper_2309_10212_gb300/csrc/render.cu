@@ -26,6 +26,7 @@
 #include <cstddef>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "kernels.cuh"
 #include "scan.cuh"
@@ -109,6 +110,7 @@ struct PassState {
     uint32_t fresh_lo, fresh_hi, n_used;
     uint32_t live_words;  // ceil(n_live / 32): words of the alive bitmap of this pass
     uint32_t coop_below;  // passes with fewer live rays walk one ray per warp
+    uint32_t seg_threads; // lanes the segmented walk may use (0: off); see traverse_seg_kernel
     unsigned long long tot_decoded, tot_entries, tot_evicted, tot_hits;
 };
 
@@ -138,6 +140,7 @@ struct DevParams {
     uint32_t more;    // passes this call may run
     uint32_t reset;   // 1: empty the cache before ray generation
     uint32_t coop_below;
+    uint32_t seg_threads;
     uint32_t n_views;
     View views[kMaxViews];   // the first n_views are copied
 };
@@ -554,6 +557,19 @@ struct EnterEmit {
 // with spr_set_warp_walk_threshold) walk one ray per warp
 // (traverse_coop_kernel); larger passes one ray per thread (traverse_kernel).
 constexpr uint32_t kCoopBelowDefault = 16384;
+// lanes of the segmented walk (traverse_seg_kernel): a pass of n live rays
+// gives each ray seg_threads / n lanes (a power of two up to 32, used from 2)
+constexpr uint32_t kSegThreadsDefault = 262144;   // measured best of 0, 2^18 .. 2^21 (paper scale, medium)
+
+// lanes per ray of this pass (1: the segmented walk is not used)
+__device__ __forceinline__ int seg_lanes(const PassState *ps)
+{
+    const uint32_t n = ps->nproc, budget = ps->seg_threads;
+    if (!budget || !n || budget / n < 2) return 1;
+    const uint32_t q = min(budget / n, 32u);
+    return 1 << (31 - __clz(q));
+}
+
 constexpr uint32_t kHalfWarpFrom = 4096;   // warp walks: a half warp per ray from this many rays
 
 __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__restrict__ live0,
@@ -568,6 +584,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
     const VolGeom &g = P.g;
     const uint32_t nproc = ps->nproc;
     if (nproc < ps->coop_below) return;   // few rays: traverse_coop_kernel walks them
+    if (seg_lanes(ps) > 1) return;        // traverse_seg_kernel walks them
     const int kk = (int)ps->kk;
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
     // every step moves at least one block index monotonically, so a walk
@@ -683,6 +700,7 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
     const VolGeom &g = P.g;
     const uint32_t nproc = ps->nproc;
     if (nproc >= ps->coop_below) return;
+    if (seg_lanes(ps) > 1) return;        // traverse_seg_kernel walks them
     // a half warp per ray when there are enough rays to fill the GPU (the
     // walk is then bound by instruction throughput), a whole warp per ray
     // for the last few (bound by each walk's latency)
@@ -883,6 +901,307 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
     if (gl == 0) {
         if (tot_steps) atomicAdd(&ctr[C_STEPS], tot_steps);
         if (max_seen) atomicMax(&ctr[C_MAXSTEPS], max_seen);
+    }
+}
+
+// ----------------------------------------------------- segmented traversal
+// A pass's walks are as long as its longest ray: one thread per ray leaves
+// most lanes idle behind a few rays that cross the whole volume.  The
+// segmented walk gives each live ray a group of SL lanes (a power of two,
+// SL = seg_threads / nproc rounded down, at most 32).  The ray's remaining
+// path is cut at block planes of its dominant axis (the axis of largest
+// |d|; every block index along it changes monotonically): lane j owns the
+// blocks whose index along that axis lies in the j-th of SL equal parts of
+// the range from the current block to the volume's far side.  Lane 0
+// resumes the saved walk; lane j > 0 starts at the exact crossing time T_j
+// of its first plane, in the block containing p(T_j+) (located with the
+// exact predicates, the right-limit rule of the serial walk), unless the
+// ray has left the volume by then.  Each lane then runs the serial walk
+// (walk_step, skip_level, the brick masks) until its index leaves its part,
+// the ray leaves the volume, or it holds k visible blocks.  Because the parts
+// partition the path by a coordinate that only grows (or only shrinks), the
+// concatenation of the lanes' visible blocks in lane order is the serial
+// walk's sequence; the group keeps its first k (an exclusive scan of the
+// counts) and marks only those.  Blocks are buffered in shared memory; a lane
+// that found more than kSegBuf walks its part again, writing directly.
+constexpr int kSegBuf = 32;
+constexpr int kSegThreads = 128;
+
+struct SegPart {
+    int as;        // dominant axis
+    int b0;        // index along it of the ray's current block
+    int o0, o1;    // this lane's offsets [o0, o1) from b0 along the walk
+};
+
+// The dominant axis and this lane's part; false when the part is empty.
+__device__ __forceinline__ bool seg_part(const Walk &w, const VolGeom &g, int SL, int gl, SegPart &sp)
+{
+    int as = 0;
+    float best = -1.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (w.r.ad[a] > best) {
+            best = w.r.ad[a];
+            as = a;
+        }
+    sp.as = as;
+    const int bq = as == 0 ? w.b[0] : (as == 1 ? w.b[1] : w.b[2]);
+    const int sg = as == 0 ? w.r.sgn[0] : (as == 1 ? w.r.sgn[1] : w.r.sgn[2]);
+    const int tbq = as == 0 ? g.tb[0] : (as == 1 ? g.tb[1] : g.tb[2]);
+    sp.b0 = bq;
+    const int span = sg > 0 ? tbq - bq : bq + 1;
+    // rounded up, so that lane 0's part always holds the current block (only
+    // lane 0 resumes the saved walk); later lanes may get empty parts
+    sp.o0 = (int)(((int64_t)gl * span + SL - 1) / SL);
+    sp.o1 = (int)(((int64_t)(gl + 1) * span + SL - 1) / SL);
+    return sp.o0 < sp.o1;
+}
+
+__device__ __forceinline__ int seg_offset(const Walk &w, const SegPart &sp)
+{
+    const int bq = sp.as == 0 ? w.b[0] : (sp.as == 1 ? w.b[1] : w.b[2]);
+    const int sg = sp.as == 0 ? w.r.sgn[0] : (sp.as == 1 ? w.r.sgn[1] : w.r.sgn[2]);
+    return sg > 0 ? bq - sp.b0 : sp.b0 - bq;
+}
+
+// Place a lane's walk at the start of its part: lane 0 resumes the saved
+// walk (stepping first when the saved block was already taken), lane j > 0
+// starts in the block holding p(T_j+).  False when nothing is left to walk.
+__device__ __forceinline__ bool seg_start(Walk &w, const VolGeom &g, const SegPart &sp, int gl, const int b_saved[3],
+                                          bool step_first)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) w.b[a] = b_saved[a];
+    if (gl == 0) {
+        walk_init(w, g);
+        return step_first ? walk_step(w, g) : true;
+    }
+    const int as = sp.as;
+    const int sg = as == 0 ? w.r.sgn[0] : (as == 1 ? w.r.sgn[1] : w.r.sgn[2]);
+    const int first = sg > 0 ? sp.b0 + sp.o0 : sp.b0 - sp.o0;        // first block index of the part
+    const float X = (float)(sg > 0 ? 4 * first : 4 * (first + 1));   // the plane entering it
+    const Tq T = plane_t(w.r, as, X);
+    // the time the ray leaves the volume: its first far-plane crossing
+    Tq tout{0.f, 1.f};
+    bool have = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (w.r.sgn[a] == 0) continue;
+        const Tq tf = plane_t(w.r, a, w.r.sgn[a] > 0 ? (float)(g.dims[a] - 1) : 0.f);
+        if (!have || tcmp(tf, tout) < 0) {
+            tout = tf;
+            have = true;
+        }
+    }
+    if (!have || tcmp(T, tout) >= 0) return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) w.b[a] = a == as ? first : locate_block(w.r, a, T, g.tb[a]);
+    walk_init(w, g);
+    return true;
+}
+
+// One lane's walk over its part.  Emit mode 0 buffers up to kSegBuf blocks
+// (and the step count at each) in shared memory; mode 1 writes blocks
+// q < n_write directly to out[q] and marks them.  Returns the visible blocks
+// found (at most cap); *end_steps the steps taken, *exited whether the walk
+// left the volume, *last the last block written in mode 1.
+struct SegOut {
+    uint32_t *blk;      // shared: [kSegBuf][kSegThreads], this thread's column
+    uint16_t *stp;
+    uint32_t *out;      // mode 1
+    uint32_t *eray;     // mode 1, per-ray speculation (may be null)
+    uint32_t ray_pos;
+    uint32_t *vis_bits, *act_bits;
+};
+
+template <int MODE>
+__device__ __forceinline__ int seg_walk(Walk &w, const Geo &P, const SegPart &sp, int view, int cap, int n_write, const SegOut &o,
+                        int max_steps, uint32_t *ctr, int *end_steps, bool *exited, uint32_t *last)
+{
+    const VolGeom &g = P.g;
+    const unsigned long long *fm = P.occ.fmask + view * P.fstride, *sm = P.occ.smask + view * P.sstride;
+    const uint32_t nb0 = g.nb[0], nb1 = g.nb[1], nc0 = g.nc[0], nc1 = g.nc[1];
+    const uint32_t ns0 = P.occ.ns[0], ns1 = P.occ.ns[1];
+    int cnt = 0, steps = 0;
+    bool alive = true;
+    uint32_t cur_s = 0xFFFFFFFFu, cur_c = 0xFFFFFFFFu;
+    unsigned long long smask = 0ull, fmask = 0ull;
+    while (alive) {
+        if (seg_offset(w, sp) >= sp.o1) break;   // the next lane's part
+        if (++steps > max_steps) {
+            atomicOr(&ctr[C_BAD], 2u);
+            alive = false;
+            break;
+        }
+        const int *b = w.b;
+        const uint32_t sc = (uint32_t)(b[0] >> 4) + ns0 * ((uint32_t)(b[1] >> 4) + ns1 * (uint32_t)(b[2] >> 4));
+        if (sc != cur_s) {
+            smask = __ldg(sm + sc);
+            cur_s = sc;
+        }
+        if (!((smask >> (((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) & 1ull)) {
+            alive = skip_level(w, g, smask ? 4 : 16, smask ? g.tc : P.occ.ts);
+            continue;
+        }
+        const uint32_t c = (uint32_t)(b[0] >> 2) + nc0 * ((uint32_t)(b[1] >> 2) + nc1 * (uint32_t)(b[2] >> 2));
+        if (c != cur_c) {
+            fmask = __ldg(fm + c);
+            cur_c = c;
+        }
+        if ((fmask >> ((b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) & 1ull) {
+            const uint32_t blin = (uint32_t)b[0] + nb0 * ((uint32_t)b[1] + nb1 * (uint32_t)b[2]);
+            if (MODE == 0) {
+                if (cnt < kSegBuf) {
+                    o.blk[cnt * kSegThreads] = blin;
+                    o.stp[cnt * kSegThreads] = (uint16_t)min(steps, 65535);
+                }
+            } else if (cnt < n_write) {
+                o.out[cnt] = blin;
+                if (o.eray) o.eray[cnt] = o.ray_pos;
+                set_bit(o.vis_bits, blin);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    int x = b[0] + (q & 1), y = b[1] + ((q >> 1) & 1), z = b[2] + (q >> 2);
+                    if (x < g.nb[0] && y < g.nb[1] && z < g.nb[2])
+                        set_bit(o.act_bits, (uint32_t)x + nb0 * ((uint32_t)y + nb1 * (uint32_t)z));
+                }
+                *last = blin;
+            }
+            if (++cnt == cap) break;
+            if (MODE == 1 && cnt >= n_write) break;
+        }
+        alive = walk_step(w, g);
+    }
+    *end_steps = steps;
+    *exited = !alive;
+    return cnt;
+}
+
+__global__ void __launch_bounds__(kSegThreads, 5) traverse_seg_kernel(Geo P, const uint32_t *__restrict__ live0,
+                                                                   const uint32_t *__restrict__ live1,
+                                                                   const PassState *__restrict__ ps,
+                                                                   const uint64_t *__restrict__ state_in,
+                                                                   uint64_t *__restrict__ state_out,
+                                                                   uint32_t *__restrict__ rbid,
+                                                                   uint32_t *vis_bits, uint32_t *act_bits,
+                                                                   uint32_t *ctr, Spec S)
+{
+    __shared__ uint32_t s_blk[kSegBuf * kSegThreads];
+    __shared__ uint16_t s_stp[kSegBuf * kSegThreads];
+    const int SL = seg_lanes(ps);
+    if (SL < 2) return;
+    const VolGeom &g = P.g;
+    const uint32_t nproc = ps->nproc;
+    const int kk = (int)ps->kk;
+    const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
+    const int max_steps = 2 * (g.tb[0] + g.tb[1] + g.tb[2]) + 8;
+    const int lg = 31 - __clz(SL);
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (SL - 1);
+    const unsigned gmask = SL == 32 ? 0xFFFFFFFFu : (((1u << SL) - 1u) << (lane & ~(SL - 1)));
+    const uint32_t nb0 = g.nb[0], nb1 = g.nb[1];
+    SegOut o{s_blk + threadIdx.x, s_stp + threadIdx.x, nullptr, nullptr, 0u, vis_bits, act_bits};
+    uint32_t tot_steps = 0, max_seen = 0;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> lg; i < nproc;
+         i += ((int64_t)gridDim.x * blockDim.x) >> lg) {
+        const uint32_t ray = live[i];
+        Walk w;
+        int view, px, py;
+        ray_pixel(P, ray, view, px, py);
+        {
+            const Cam &cam = P.views[view].cam;
+            make_ray(w.r, cam.eye, cam.p00, cam.du, cam.dv, px, py);
+        }
+        const uint64_t st = state_in[ray];
+        const int b_saved[3] = {(int)(st & 0xFFFF), (int)((st >> 16) & 0xFFFF), (int)((st >> 32) & 0xFFFF)};
+        const uint64_t flags = st >> 48;
+        const uint64_t off = S.koff ? S.koff[i] : (uint64_t)i * kk;
+        const int ki = S.koff ? (int)S.kray[i] : kk;
+        uint32_t *out = rbid + off;
+
+        // 1. this lane's part, walked with the blocks buffered
+        int cnt = 0, steps = 0;
+        bool exited = false;
+        SegPart sp;
+        bool active = false;
+        if (!(flags & kDone)) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) w.b[a] = b_saved[a];
+            if (seg_part(w, g, SL, gl, sp)) active = seg_start(w, g, sp, gl, b_saved, (flags & kStep) != 0);
+            else if (gl == 0) active = false;
+            if (gl == 0 && !active) exited = true;   // lane 0's step left the volume
+        } else {
+            exited = true;
+        }
+        uint32_t dummy = 0;
+        if (active) cnt = seg_walk<0>(w, P, sp, view, ki, 0, o, max_steps, ctr, &steps, &exited, &dummy);
+        // 2. the group's order: exclusive scan of the counts
+        int incl = cnt;
+        for (int d = 1; d < SL; d <<= 1) {
+            const int y = __shfl_up_sync(gmask, incl, d, SL);
+            if (gl >= d) incl += y;
+        }
+        const int pre = incl - cnt;
+        const int total = __shfl_sync(gmask, incl, SL - 1, SL);
+        const int n_write = max(0, min(cnt, ki - pre));
+        // 3. the first k blocks of the ray: written and marked
+        uint32_t last = kNone;
+        if (n_write > 0 && n_write <= kSegBuf) {
+            for (int q = 0; q < n_write; ++q) {
+                const uint32_t blin = s_blk[q * kSegThreads + threadIdx.x];
+                out[pre + q] = blin;
+                if (S.eray) S.eray[off + pre + q] = (uint32_t)i;
+                set_bit(vis_bits, blin);
+                const int bx = (int)(blin % nb0), by = (int)((blin / nb0) % nb1), bz = (int)(blin / (nb0 * nb1));
+#pragma unroll
+                for (int q2 = 0; q2 < 8; ++q2) {
+                    int x = bx + (q2 & 1), y = by + ((q2 >> 1) & 1), z = bz + (q2 >> 2);
+                    if (x < g.nb[0] && y < g.nb[1] && z < g.nb[2])
+                        set_bit(act_bits, (uint32_t)x + nb0 * ((uint32_t)y + nb1 * (uint32_t)z));
+                }
+                last = blin;
+            }
+        } else if (n_write > 0) {   // more than the buffer holds: walk the part again, writing
+            SegOut o2 = o;
+            o2.out = out + pre;
+            o2.eray = S.eray ? S.eray + off + pre : nullptr;
+            o2.ray_pos = (uint32_t)i;
+            int s2 = 0;
+            bool e2 = false;
+            seg_start(w, g, sp, gl, b_saved, (flags & kStep) != 0);
+            seg_walk<1>(w, P, sp, view, ki, n_write, o2, max_steps, ctr, &s2, &e2, &last);
+        }
+        for (int j = min(total, ki) + gl; j < ki; j += SL) out[j] = kNone;
+        // 4. state: after the k-th block, or done (every part walked, fewer
+        // than k found: the ray leaves the volume)
+        const bool holds_kth = pre < ki && pre + cnt >= ki;
+        if (total >= ki) {
+            if (holds_kth) {
+                const int bq[3] = {(int)(last % nb0), (int)((last / nb0) % nb1), (int)(last / (nb0 * nb1))};
+                state_out[ray] = pack_state(bq, kStep);
+            }
+        } else if (gl == 0) {
+            state_out[ray] = pack_state(b_saved, kDone);
+        }
+        // useful steps: whole parts before the k-th block, up to it in its part
+        int useful = 0;
+        if (pre < ki) {
+            if (holds_kth) {
+                const int q = ki - 1 - pre;
+                useful = q < kSegBuf ? (int)s_stp[q * kSegThreads + threadIdx.x] : steps;
+            } else {
+                useful = steps;
+            }
+        }
+        tot_steps += (uint32_t)useful;
+        max_seen = max(max_seen, (uint32_t)useful);
+        (void)exited;
+    }
+    warp_add(&ctr[C_STEPS], tot_steps);
+    {
+        unsigned m = __activemask();
+        uint32_t mx = __reduce_max_sync(m, max_seen);
+        if ((threadIdx.x & 31) == (unsigned)(__ffs(m) - 1) && mx) atomicMax(&ctr[C_MAXSTEPS], mx);
     }
 }
 
@@ -1271,20 +1590,40 @@ __device__ __forceinline__ uint32_t pick8(const uint32_t s[8], int k)
 
 // Intersect the ray with the isosurface inside block (bx,by,bz).  On a hit,
 // returns the 44 low bits of the resolve key: depth bits, local cell, grey.
-__device__ bool intersect_block(const RT &R, const Ray &r, float isov, int bx, int by, int bz, uint64_t &payload)
+// The block's dual grid (its 4^3 voxels and the +x/+y/+z neighbours' face,
+// edge and corner voxels, 5^3 values) as the intersection reads it: local
+// corner (lx, ly, lz), each in 0..4.
+// GlobalCorners reads each corner from the cache slot holding it (L1-cached
+// loads); SharedCorners from a copy of the 5^3 values staged in shared memory.
+struct GlobalCorners {
+    const float *cache;
+    uint32_t slots[8];   // own, +x, +y, +xy, +z, +xz, +yz, +xyz
+    __device__ __forceinline__ float operator()(int lx, int ly, int lz) const
+    {
+        const int nsel = (lx >> 2) | ((ly >> 2) << 1) | ((lz >> 2) << 2);
+        const uint32_t slot = pick8(slots, nsel);
+        return __ldg(cache + (uint64_t)slot * 64 + (lx & 3) + 4 * (ly & 3) + 16 * (lz & 3));
+    }
+};
+
+struct SharedCorners {
+    const float *v;   // 125 values, x fastest
+    __device__ __forceinline__ float operator()(int lx, int ly, int lz) const { return v[lx + 5 * ly + 25 * lz]; }
+};
+
+// cells per axis of block (bx, by, bz) that exist (1..4)
+__device__ __forceinline__ void block_extent(const VolGeom &g, int bx, int by, int bz, int ext[3])
+{
+    ext[0] = min(4, g.dims[0] - 1 - 4 * bx);
+    ext[1] = min(4, g.dims[1] - 1 - 4 * by);
+    ext[2] = min(4, g.dims[2] - 1 - 4 * bz);
+}
+
+// the cache slots of a block and of the +x/+y/+z neighbours its cells reach
+__device__ __forceinline__ void neighbour_slots(const RT &R, int bx, int by, int bz, const int ext[3],
+                                                uint32_t slots[8])
 {
     const VolGeom &g = R.P.g;
-    const float iso = isov;
-    const int bq[3] = {bx, by, bz};
-    float o[3];
-    int ext[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        o[a] = __fsub_rn(r.e[a], (float)(4 * bq[a]));   // exact
-        ext[a] = min(4, g.dims[a] - 1 - 4 * bq[a]);
-    }
-    // neighbour slots: own, +x, +y, +xy, +z, +xz, +yz, +xyz
-    uint32_t slots[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         int x = bx + (k & 1), y = by + ((k >> 1) & 1), z = bz + (k >> 2);
@@ -1293,6 +1632,20 @@ __device__ bool intersect_block(const RT &R, const Ray &r, float isov, int bx, i
                        ? R.blk_slot[x + (int64_t)g.nb[0] * (y + (int64_t)g.nb[1] * z)]
                        : 0u;
     }
+}
+
+template <class Corners>
+__device__ bool intersect_block(const RT &R, const Ray &r, float isov, int bx, int by, int bz, const Corners &corner,
+                                uint64_t &payload)
+{
+    const VolGeom &g = R.P.g;
+    const float iso = isov;
+    const int bq[3] = {bx, by, bz};
+    float o[3];
+    int ext[3];
+    block_extent(g, bx, by, bz, ext);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) o[a] = __fsub_rn(r.e[a], (float)(4 * bq[a]));   // exact
     // entry into the block: the latest near-plane crossing (exact; ties go to
     // the higher axis, which is crossed last)
     int ain = -1;
@@ -1372,10 +1725,7 @@ __device__ bool intersect_block(const RT &R, const Ray &r, float isov, int bx, i
             int below = 0, above = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                int lx = c[0] + (k & 1), ly = c[1] + ((k >> 1) & 1), lz = c[2] + (k >> 2);
-                int nsel = (lx >> 2) | ((ly >> 2) << 1) | ((lz >> 2) << 2);
-                uint32_t slot = pick8(slots, nsel);
-                f.v[k] = __ldg(R.cache + (uint64_t)slot * 64 + (lx & 3) + 4 * (ly & 3) + 16 * (lz & 3));
+                f.v[k] = corner(c[0] + (k & 1), c[1] + ((k >> 1) & 1), c[2] + (k >> 2));
                 below += f.v[k] < iso;
                 above += f.v[k] > iso;
             }
@@ -1473,8 +1823,109 @@ __global__ void __launch_bounds__(128, 4) intersect_kernel(RT R, const uint32_t 
         const float iso = vw.iso;
         make_ray(r, vw.cam.eye, vw.cam.p00, vw.cam.du, vw.cam.dv, px, py);
         int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((uint32_t)g.nb[0] * g.nb[1]));
+        GlobalCorners gc;
+        gc.cache = R.cache;
+        {
+            int ext[3];
+            block_extent(g, bx, by, bz, ext);
+            neighbour_slots(R, bx, by, bz, ext, gc.slots);
+        }
         uint64_t payload;
-        if (intersect_block(R, r, iso, bx, by, bz, payload)) atomicMin(keys + ray, ((uint64_t)j << 52) | payload);
+        if (intersect_block(R, r, iso, bx, by, bz, gc, payload)) atomicMin(keys + ray, ((uint64_t)j << 52) | payload);
+    }
+}
+
+// The intersection with each block's dual grid staged in shared memory, as
+// Sec. 3.7's work groups do: a warp takes 32 entries from the queue (entries
+// are grouped by block, so their blocks form runs), copies the 5^3 values of
+// each distinct block among them from the cache slots into shared memory
+// (4 values per lane and block), then intersects its entries reading corners
+// from there.  Same arithmetic on the same values as intersect_kernel, so the
+// same keys.  It pays when blocks carry several entries each (one staging
+// serves them all); the per-cell loads of intersect_kernel touch only the
+// corners of the cells a ray crosses.
+constexpr int kStageWarps = 3;   // 3 x 16 KB: the static shared-memory limit
+
+__global__ void __launch_bounds__(32 * kStageWarps, 4) intersect_staged_kernel(
+    RT R, const uint32_t *__restrict__ E, const uint32_t *__restrict__ rbid, const uint32_t *__restrict__ live0,
+    const uint32_t *__restrict__ live1, const PassState *__restrict__ ps, unsigned long long *keys, uint32_t *ctr,
+    Spec S)
+{
+    __shared__ float s_grid[kStageWarps][32][128];
+    if (ctr[C_OVERFLOW]) return;
+    const uint32_t kk = ps->kk;
+    const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
+    const uint32_t n = ctr[C_NENT];
+    const VolGeom &g = R.P.g;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (;;) {
+        const uint32_t base = warp_take(&ctr[C_QISECT]);
+        if (base >= n) break;
+        const uint32_t idx = base + lane;
+        const bool valid = idx < n;
+        const uint32_t e = valid ? E[idx] : 0u;
+        const uint32_t b = valid ? rbid[e] : kNone;
+        const uint32_t bprev = __shfl_up_sync(0xFFFFFFFFu, b, 1);
+        const bool start = valid && (lane == 0 || b != bprev);
+        const unsigned starts = __ballot_sync(0xFFFFFFFFu, start);
+        const int my_g = __popc(starts & ((2u << lane) - 1u)) - 1;   // this entry's block among the warp's
+        // stage the distinct blocks, one after another
+        unsigned rem = starts;
+        for (int gi = 0; rem; ++gi) {
+            const int src = __ffs(rem) - 1;
+            rem &= rem - 1u;
+            const uint32_t bg = __shfl_sync(0xFFFFFFFFu, b, src);
+            const int bx = (int)(bg % g.nb[0]), by = (int)((bg / g.nb[0]) % g.nb[1]),
+                      bz = (int)(bg / ((uint32_t)g.nb[0] * g.nb[1]));
+            int ext[3];
+            block_extent(g, bx, by, bz, ext);
+            uint32_t my_slot = 0u;
+            if (lane < 8) {
+                const int k = lane;
+                const int x = bx + (k & 1), y = by + ((k >> 1) & 1), z = bz + (k >> 2);
+                const bool need = (!(k & 1) || ext[0] == 4) && (!(k & 2) || ext[1] == 4) && (!(k & 4) || ext[2] == 4);
+                my_slot = (need && x < g.nb[0] && y < g.nb[1] && z < g.nb[2])
+                              ? R.blk_slot[x + (int64_t)g.nb[0] * (y + (int64_t)g.nb[1] * z)]
+                              : 0u;
+            }
+            float *dst = s_grid[w][gi];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int q = lane + 32 * t;
+                const int lx = q % 5, ly = (q / 5) % 5, lz = q / 25;
+                const int nsel = (lx >> 2) | ((ly >> 2) << 1) | ((lz >> 2) << 2);
+                const uint32_t slot = __shfl_sync(0xFFFFFFFFu, my_slot, nsel);
+                // corners the block's cells can reach: up to ext along each axis
+                if (q < 125 && lx <= ext[0] && ly <= ext[1] && lz <= ext[2])
+                    dst[q] = __ldg(R.cache + (uint64_t)slot * 64 + (lx & 3) + 4 * (ly & 3) + 16 * (lz & 3));
+            }
+        }
+        __syncwarp();
+        if (valid) {
+            uint32_t i, j;
+            if (S.koff) {
+                i = S.eray[e];
+                j = e - S.koff[i];
+            } else {
+                i = e / kk;
+                j = e - i * kk;
+            }
+            const uint32_t ray = live[i];
+            // a hit already recorded from an earlier block of this ray wins
+            if ((uint32_t)(__ldcg(keys + ray) >> 52) >= j) {
+                Ray r;
+                int view, px, py;
+                ray_pixel(R.P, ray, view, px, py);
+                const View &vw = R.P.views[view];
+                make_ray(r, vw.cam.eye, vw.cam.p00, vw.cam.du, vw.cam.dv, px, py);
+                const int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]),
+                          bz = (int)(b / ((uint32_t)g.nb[0] * g.nb[1]));
+                uint64_t payload;
+                if (intersect_block(R, r, vw.iso, bx, by, bz, SharedCorners{s_grid[w][my_g]}, payload))
+                    atomicMin(keys + ray, ((uint64_t)j << 52) | payload);
+            }
+        }
+        __syncwarp();   // the staging area is rewritten by the next take
     }
 }
 
@@ -1854,6 +2305,7 @@ __global__ void start_kernel(PassState *ps, const DevParams *p, uint32_t *ctr, u
             ps->k_max = p->k_max;
             ps->npix = p->npix;
             ps->coop_below = p->coop_below;
+            ps->seg_threads = p->seg_threads;
         }
     }
     if (!p->reset) return;
@@ -1882,6 +2334,7 @@ __global__ void config_kernel(PassState *ps, const DevParams *p)
     ps->k_max = p->k_max;
     ps->npix = p->npix;
     ps->coop_below = p->coop_below;
+    ps->seg_threads = p->seg_threads;
 }
 
 // after ray generation: the live list is list 0 and the pass count restarts
@@ -1948,6 +2401,8 @@ struct spr_renderer {
     float iso = 0.5f;             // isovalue given to views by spr_set_isovalue
     int spec_mode = SPR_SPEC_ADAPTIVE, k_fixed = 1, k_max = 64;
     uint32_t coop_below = kCoopBelowDefault;
+    uint32_t seg_threads = kSegThreadsDefault;
+    bool isect_staged = false;    // intersect_staged_kernel instead of intersect_kernel
     int64_t n_slots = 0;
     bool profiling = false;
 
@@ -2009,6 +2464,7 @@ struct spr_renderer {
     cudaGraphExec_t gexec = nullptr;
     cudaGraphExec_t gprof = nullptr;  // one attempt with event nodes between stages
     int graph_kernels = 0;        // kernels in one pass of the body
+    uint64_t graph_gen = 0;       // counts drop_graph calls (a batch's captured copies go stale with them)
     // a render enqueued by spr_render_submit and not yet collected
     bool busy = false;
     cudaStream_t sub_stream = nullptr;
@@ -2021,6 +2477,7 @@ namespace {
 
 void drop_graph(spr_renderer *r)
 {
+    ++r->graph_gen;
     if (r->gexec) cudaGraphExecDestroy(r->gexec);
     if (r->graph) cudaGraphDestroy(r->graph);
     if (r->gprof) cudaGraphExecDestroy(r->gprof);
@@ -2201,6 +2658,7 @@ int write_params(spr_renderer *r, uint32_t more, uint32_t reset)
     h.more = more;
     h.reset = reset;
     h.coop_below = r->coop_below;
+    h.seg_threads = r->seg_threads;
     return SPR_OK;
 }
 
@@ -2387,6 +2845,12 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
         make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
         r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
     count_launch();
+    if (r->seg_threads) {
+        traverse_seg_kernel<<<device_sm_count() * 16, kSegThreads, 0, s>>>(
+            make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
+            r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
+        count_launch();
+    }
     SPR_CUDA_TRY(cudaGetLastError());
     if (events) SPR_CUDA_TRY(record(r->ev[1], s, capturing));
     if (fork) {
@@ -2460,8 +2924,13 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
 
     // (e) intersect the entries, block by block
     RT R{make_geo(r), r->cache.as<float>(), r->blk_slot.as<uint32_t>()};
-    intersect_kernel<<<r->grid_isect, 128, 0, s>>>(R, r->E.as<uint32_t>(), r->rbid.as<uint32_t>(), live0, live1, ps,
-                                                   r->keys.as<unsigned long long>(), ctr, S);
+    if (r->isect_staged)
+        intersect_staged_kernel<<<device_sm_count() * 4, 32 * kStageWarps, 0, s>>>(
+            R, r->E.as<uint32_t>(), r->rbid.as<uint32_t>(), live0, live1, ps, r->keys.as<unsigned long long>(), ctr,
+            S);
+    else
+        intersect_kernel<<<r->grid_isect, 128, 0, s>>>(R, r->E.as<uint32_t>(), r->rbid.as<uint32_t>(), live0, live1,
+                                                       ps, r->keys.as<unsigned long long>(), ctr, S);
     count_launch();
     SPR_CUDA_TRY(cudaGetLastError());
     if (events) SPR_CUDA_TRY(record(r->ev[5], s, capturing));
@@ -2646,10 +3115,10 @@ int alloc_view_buffers(spr_renderer *r)
 // The start of a render as one graph: copy the parameter block, apply the
 // speculation settings, empty the cache if asked, generate rays (with_raygen)
 // and set the pass limit.  Kernels in it: 4 with ray generation, else 2.
-int build_start_graph(spr_renderer *r, bool with_raygen)
+// The start of a render captured into a new graph g (not instantiated).
+int capture_start_graph(spr_renderer *r, bool with_raygen, cudaGraph_t *out)
 {
-    cudaGraphExec_t &ge = with_raygen ? r->gstart : r->glimit;
-    if (ge) return SPR_OK;
+    *out = nullptr;
     if (!r->cap_stream) SPR_CUDA_TRY(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
     cudaStream_t cs = r->cap_stream;
     DevParams *dp = r->camd.as<DevParams>();
@@ -2674,7 +3143,17 @@ int build_start_graph(spr_renderer *r, bool with_raygen)
         if (rc != SPR_OK) return rc;
         return set_error(SPR_ERR_CUDA, "start capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&ge, g, 0);
+    *out = g;
+    return SPR_OK;
+}
+
+int build_start_graph(spr_renderer *r, bool with_raygen)
+{
+    cudaGraphExec_t &ge = with_raygen ? r->gstart : r->glimit;
+    if (ge) return SPR_OK;
+    cudaGraph_t g = nullptr;
+    SPR_TRY(capture_start_graph(r, with_raygen, &g));
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         ge = nullptr;
@@ -2998,6 +3477,29 @@ extern "C" int spr_set_warp_walk_threshold(spr_renderer *r, int64_t n_rays)
     if (n_rays < 0) return set_error(SPR_ERR_INVALID_ARG, "n_rays must be non-negative");
     r->coop_below = (uint32_t)std::min<int64_t>(n_rays, 0xFFFFFFFFll);
     r->params_dirty = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_set_segment_walk(spr_renderer *r, int64_t lanes)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
+    if (lanes < 0) return set_error(SPR_ERR_INVALID_ARG, "negative lane budget");
+    const uint32_t v = (uint32_t)std::min<int64_t>(lanes, 0x7FFFFFFFll);
+    if ((v != 0) != (r->seg_threads != 0)) drop_graph(r);   // the pass graph gains or loses the kernel
+    r->seg_threads = v;
+    r->params_dirty = true;
+    return SPR_OK;
+}
+
+extern "C" int spr_set_intersect_staging(spr_renderer *r, int on)
+{
+    clear_error();
+    if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
+    SPR_TRY(check_idle(r));
+    if ((on != 0) != r->isect_staged) drop_graph(r);   // the pass graph holds the kernel
+    r->isect_staged = on != 0;
     return SPR_OK;
 }
 
@@ -3399,4 +3901,181 @@ extern "C" int spr_debug_scan_withhold(const uint32_t *in, uint32_t *out, int64_
     clear_error();
     if (spin_limit < 1) return set_error(SPR_ERR_INVALID_ARG, "spin_limit must be positive");
     return scan_impl(in, out, n, nullptr, withhold_tile, spin_limit, as_stream(stream));
+}
+
+// ------------------------------------------------------------------ batch
+// Several renderers -- of different volumes, image sizes and view counts --
+// rendered by one graph launch.  Each keeps everything its own render uses
+// (cache, brick masks, wavefront, scan scratch, pass state); the graph holds,
+// per renderer, the start of its render (parameter copy, ray generation) as
+// a child graph followed by its pass loop (a conditional while node over one
+// pass attempt).  The branches have no edges between them, so the device runs
+// the renders concurrently, and the small passes of one overlap the others'.
+struct spr_batch {
+    std::vector<spr_renderer *> rs;
+    std::vector<uint64_t> gens;        // each renderer's graph generation at capture
+    std::vector<int64_t> n_slots;      // and its cache size
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void batch_drop(spr_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+int batch_build(spr_batch *b)
+{
+    batch_drop(b);
+    cudaGraph_t g = nullptr;
+    SPR_CUDA_TRY(cudaGraphCreate(&g, 0));
+    int rc = SPR_OK;
+    for (spr_renderer *r : b->rs) {
+        cudaGraph_t sg = nullptr;
+        if ((rc = capture_start_graph(r, true, &sg)) != SPR_OK) break;
+        cudaGraphNode_t start = nullptr;
+        cudaError_t e = cudaGraphAddChildGraphNode(&start, g, nullptr, 0, sg);
+        cudaGraphDestroy(sg);   // the node holds its own copy
+        cudaGraphConditionalHandle h;
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t loop = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&loop, g, &start, nullptr, 1, &cp);
+        if (e != cudaSuccess) {
+            rc = set_error(SPR_ERR_CUDA, "batch graph: %s", cudaGetErrorString(e));
+            break;
+        }
+        e = cudaStreamBeginCaptureToGraph(r->cap_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        const int64_t saved = r->launches;
+        int rc2 = e == cudaSuccess ? enqueue_attempt(r, r->cap_stream, false, h, 1) : SPR_OK;
+        cudaGraph_t captured = nullptr;
+        cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(r->cap_stream, &captured) : e;
+        r->launches = saved;
+        if (rc2 != SPR_OK) {
+            rc = rc2;
+            break;
+        }
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            rc = set_error(SPR_ERR_CUDA, "batch pass capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+            break;
+        }
+    }
+    if (rc == SPR_OK) {
+        cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            rc = set_error(SPR_ERR_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    if (rc != SPR_OK) {
+        cudaGraphDestroy(g);
+        return rc;
+    }
+    b->graph = g;
+    for (size_t i = 0; i < b->rs.size(); ++i) {
+        b->gens[i] = b->rs[i]->graph_gen;
+        b->n_slots[i] = b->rs[i]->n_slots;
+    }
+    return SPR_OK;
+}
+
+}  // namespace
+
+extern "C" int spr_batch_create(spr_renderer *const *renderers, int n, spr_batch **out)
+{
+    clear_error();
+    if (!out || !renderers || n < 1) return set_error(SPR_ERR_INVALID_ARG, "a batch needs renderers");
+    if (n > 256) return set_error(SPR_ERR_INVALID_ARG, "at most 256 renderers in a batch");
+    for (int i = 0; i < n; ++i) {
+        if (!renderers[i]) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer %d", i);
+        for (int j = 0; j < i; ++j)
+            if (renderers[j] == renderers[i]) return set_error(SPR_ERR_INVALID_ARG, "renderer %d is listed twice", i);
+    }
+    spr_batch *b = new (std::nothrow) spr_batch;
+    if (!b) return set_error(SPR_ERR_OUT_OF_MEMORY, "host allocation failed");
+    b->rs.assign(renderers, renderers + n);
+    b->gens.assign((size_t)n, ~0ull);
+    b->n_slots.assign((size_t)n, -1);
+    *out = b;
+    return SPR_OK;
+}
+
+extern "C" int spr_batch_destroy(spr_batch *b)
+{
+    clear_error();
+    if (!b) return SPR_OK;
+    cudaDeviceSynchronize();
+    batch_drop(b);
+    delete b;
+    return SPR_OK;
+}
+
+extern "C" int spr_batch_render(spr_batch *b, spr_stream stream, int max_passes, spr_render_stats *stats)
+{
+    clear_error();
+    if (!b) return set_error(SPR_ERR_INVALID_ARG, "NULL batch");
+    if (max_passes < 1) return set_error(SPR_ERR_INVALID_ARG, "max_passes must be positive");
+    cudaStream_t s = as_stream(stream);
+    for (spr_renderer *r : b->rs) {
+        SPR_TRY(check_ready(r));
+        SPR_TRY(check_idle(r));
+        if (r->profiling) return set_error(SPR_ERR_INVALID_ARG, "profiled renders are host-driven: turn profiling off");
+        if (!r->need_raygen)
+            return set_error(SPR_ERR_INVALID_ARG, "a batch render starts every render at ray generation: "
+                                                  "set a camera or an isovalue of each renderer first");
+    }
+    for (spr_renderer *r : b->rs) {
+        SPR_TRY(ensure_entry_buffers(r, s));
+        SPR_TRY(ensure_scan_scratch(r, s));
+    }
+    bool stale = !b->exec;
+    for (size_t i = 0; i < b->rs.size(); ++i)
+        stale |= b->gens[i] != b->rs[i]->graph_gen || b->n_slots[i] != b->rs[i]->n_slots;
+    if (stale) SPR_TRY(batch_build(b));
+    for (spr_renderer *r : b->rs) {
+        r->launches = 0;
+        if (r->cache_dirty && !r->cache_init) SPR_TRY(reset_cache(r, s));
+        const uint32_t reset = r->cache_dirty ? 1u : 0u;
+        SPR_TRY(update_occupancy(r, s));
+        SPR_TRY(clear_bits_if_dirty(r, s));
+        SPR_TRY(write_params(r, (uint32_t)max_passes, reset));
+        *(volatile uint32_t *)&r->h_ps->pass = 0u;
+        r->sub_before = *r->h_ps;
+        SPR_CUDA_TRY(cudaEventRecord(r->ev[7], s));
+        SPR_CUDA_TRY(cudaEventRecord(r->ev[1], s));   // no separate ray-generation time in a batch
+    }
+    SPR_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    for (spr_renderer *r : b->rs) {
+        SPR_CUDA_TRY(cudaEventRecord(r->ev_upload, s));
+        SPR_CUDA_TRY(cudaEventRecord(r->ev[0], s));
+        r->launches += 4;   // the start graph's kernels
+        r->cache_dirty = false;
+        r->params_dirty = false;
+        r->need_raygen = false;
+        r->pass = 0;
+        r->sub_fresh = true;
+        r->sub_first = 0;
+        r->sub_stream = s;
+        r->busy = true;
+    }
+    int rc = SPR_OK;
+    for (size_t i = 0; i < b->rs.size(); ++i) {
+        struct Scope {
+            Scope(int64_t *p) { g_launch_counter = p; }
+            ~Scope() { g_launch_counter = nullptr; }
+        } scope(&b->rs[i]->launches);
+        int ri = collect_render(b->rs[i], stats ? &stats[i] : nullptr, nullptr);
+        if (rc == SPR_OK) rc = ri;
+    }
+    return rc;
 }

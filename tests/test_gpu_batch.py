@@ -194,3 +194,86 @@ def test_batch_counters_match_pass_simulator(spr, orc, spec, sim, slots):
     assert rs["blocks_decoded"] == int(st["n_decoded"].sum())
     if slots:
         assert st["retries"].sum() > 0
+
+
+def _renderer(spr, vols, sc, slots, spec, views=None):
+    import torch
+    key = (sc.dims, sc.rate, id(sc.comp))
+    if key not in vols:
+        vols[key] = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    r = spr.spr_create_renderer(vols[key], sc.W, sc.H)
+    spr.spr_set_cache_budget(r, 256 * slots)
+    if spec.get("mode") == "fixed":
+        spr.spr_set_speculation(r, spr.SPR_SPEC_FIXED, k=spec["k"])
+    else:
+        spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=spec.get("k_max", 64))
+    views = views or [sc]
+    spr.spr_set_view_count(r, len(views))
+    for i, v in enumerate(views):
+        spr.spr_set_view(r, i, v.cam, v.iso)
+    return r
+
+
+def test_multi_volume_batch_equals_lone_renders(spr, orc):
+    """Three volumes of different sizes and rates, image sizes, view counts,
+    speculation rules and cache budgets rendered by one graph launch: every
+    image (and final pass) equals the renderer's own render, matches the
+    oracle, and the counters equal the lone renders'.  Rendered twice (the
+    captured graph is reused), then again after one renderer's cache budget
+    changed (the graph is captured anew); caches are emptied between rounds."""
+    a = views_of(orc, (24, 20, 18), 51, 1, 48, 40, (0.6,))
+    b = views_of(orc, (40, 36, 30), 52, 2, 64, 48, (0.45, 0.65))
+    c = views_of(orc, (64, 64, 64), 53, 1, 96, 64, (0.5,))
+    groups = [(a, 60, dict(mode="fixed", k=2)), (b, 400, dict(k_max=64)), (c, 1000, dict(k_max=16))]
+    vols = {}
+    rs = [_renderer(spr, vols, g[0], slots, spec, views=g) for g, slots, spec in groups]
+    batch = spr.spr_batch_create(rs)
+    try:
+        for rnd in range(3):
+            if rnd == 2:
+                spr.spr_set_cache_budget(rs[1], 256 * 300)
+            if rnd:
+                for r, (g, _, _) in zip(rs, groups):   # fresh renders from cold caches
+                    spr.spr_reset_cache(r)
+                    for i, sc in enumerate(g):
+                        spr.spr_set_view(r, i, sc.cam, sc.iso)
+            stats = spr.spr_batch_render(batch)
+            for r, (g, slots, spec), st in zip(rs, groups, stats):
+                assert st["converged"] == 1
+                fb = spr.spr_read_framebuffer(r)
+                n = g[0].W * g[0].H
+                # the renderer alone, same settings
+                lone = _renderer(spr, vols, g[0], slots if not (rnd == 2 and r is rs[1]) else 300, spec, views=g)
+                rs1, _ = spr.spr_render_to_convergence(lone, 100000)
+                want = spr.spr_read_framebuffer(lone)
+                lone.close()
+                for key in fb:
+                    assert np.array_equal(fb[key], want[key]), (rnd, key)
+                for k in ("passes", "blocks_decoded", "entries", "evictions", "n_hits"):
+                    assert st[k] == rs1[k], (rnd, k, st[k], rs1[k])
+                for i, sc in enumerate(g):
+                    compare(sc, {k: v[i * n:(i + 1) * n] for k, v in fb.items()})
+    finally:
+        batch.close()
+        for r in rs:
+            r.close()
+        for v in vols.values():
+            v.close()
+
+
+def test_batch_rejects_continued_and_duplicate(spr, orc):
+    a = views_of(orc, (24, 20, 18), 51, 1, 48, 40, (0.6,))
+    vols = {}
+    r = _renderer(spr, vols, a[0], 60, dict(k_max=64))
+    with pytest.raises(spr.SprError):
+        spr.spr_batch_create([r, r])
+    batch = spr.spr_batch_create([r])
+    spr.spr_batch_render(batch)
+    with pytest.raises(spr.SprError):   # no new camera: not a fresh render
+        spr.spr_batch_render(batch)
+    spr.spr_set_camera(r, a[0].cam)
+    spr.spr_batch_render(batch)
+    batch.close()
+    r.close()
+    for v in vols.values():
+        v.close()

@@ -27,7 +27,7 @@ def spr():
     return m
 
 
-def render(spr, sc, mode, k=1, k_max=64, slots=None, warp_walk=None):
+def render(spr, sc, mode, k=1, k_max=64, slots=None, warp_walk=None, seg=0):
     import torch
     v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
     r = spr.spr_create_renderer(v, sc.W, sc.H)
@@ -37,6 +37,7 @@ def render(spr, sc, mode, k=1, k_max=64, slots=None, warp_walk=None):
     spr.spr_set_cache_budget(r, 256 * (slots if slots else max(8, nb)))
     if warp_walk is not None:
         spr.spr_set_warp_walk_threshold(r, warp_walk)
+    spr.spr_set_segment_walk(r, seg)
     spr.spr_set_speculation(r, mode, k=k, k_max=k_max)
     rs, passes = spr.spr_render_to_convergence(r, 100000)
     fb = spr.spr_read_framebuffer(r)
@@ -58,13 +59,13 @@ def test_hashed_counts_keep_the_image(spr, orc, dims, seed, k_max):
     compare(sc, got)
 
 
-@pytest.mark.parametrize("warp_walk", [0, 1 << 30])
-def test_hashed_counts_both_walks(spr, orc, warp_walk):
-    """The thread-per-ray and the warp-per-ray walks take the same per-ray
-    counts and give the same image and counters."""
+@pytest.mark.parametrize("warp_walk,seg", [(0, 0), (1 << 30, 0), (0, 1 << 30), (0, 2 * 96 * 64)])
+def test_hashed_counts_both_walks(spr, orc, warp_walk, seg):
+    """The thread-per-ray, warp-per-ray and segmented walks take the same
+    per-ray counts and give the same image and counters."""
     sc = value_scene(orc, (48, 40, 36), 44, 96, 64)
     a, rsa, pa = render(spr, sc, spr.SPR_SPEC_HASHED, k_max=9, warp_walk=0)
-    b, rsb, pb = render(spr, sc, spr.SPR_SPEC_HASHED, k_max=9, warp_walk=warp_walk)
+    b, rsb, pb = render(spr, sc, spr.SPR_SPEC_HASHED, k_max=9, warp_walk=warp_walk, seg=seg)
     for key in FB_KEYS:
         assert np.array_equal(a[key], b[key]), key
     keys = ("n_active", "n_entries", "n_visible", "n_requested", "n_decoded", "n_term_hit", "n_term_miss")

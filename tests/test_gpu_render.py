@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import synth
+from parity import check_counters, resolved_pix
 
 pytestmark = pytest.mark.gpu
 
@@ -136,37 +137,6 @@ def test_small_workload_k1_k4_and_cache(spr, orc):
     for key in results[0]:
         if key != "final_pass":          # the pass a pixel finishes in depends on k
             assert np.array_equal(results[0][key], results[1][key]), key
-
-
-def resolved_pix(sc, fb):
-    """The oracle's per-pixel records with every ambiguous pixel (where a
-    correct single-precision renderer may pick either of two answers) set to
-    the GPU's answer after checking that the answer is a valid one: a hit in
-    one of the ray's visible blocks (in its full visible list), or a miss.
-    The pass simulator run on these records is then exact for the whole
-    image, so its counters are compared unconditionally."""
-    pix = sc.pix.copy()
-    amb = np.nonzero(pix["amb"] != 0)[0]
-    for p in amb:
-        lst = sc.vis[sc.off[p]:sc.off[p] + pix["n_visible"][p]]
-        if fb["status"][p] == 1:
-            where = np.nonzero(lst == fb["block"][p])[0]
-            assert where.size == 1, "pixel %d hit block %d outside its visible list" % (p, fb["block"][p])
-            pix["hit"][p] = 1
-            pix["hit_index"][p] = int(where[0])
-        else:
-            assert fb["status"][p] == 2, p
-            pix["hit"][p] = 0
-            pix["hit_index"][p] = -1
-    return pix
-
-
-def check_counters(st, passes):
-    assert len(st) == len(passes)
-    for s, p in zip(st, passes):
-        for name in ("n_active", "k", "k_used", "n_processed", "retries", "n_entries", "n_visible",
-                     "n_requested", "n_decoded", "n_evicted", "n_term_hit", "n_term_miss"):
-            assert int(s[name]) == int(p[name]), (name, s["pass"], int(s[name]), int(p[name]))
 
 
 def test_invariance_across_k_budget_and_single_pass(spr, orc):

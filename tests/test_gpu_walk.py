@@ -1,11 +1,12 @@
-"""The two traversal kernels against each other and the oracle.
+"""The traversal kernels against each other and the oracle.
 
 Passes with few live rays walk one ray per warp (the blocks of an occupied
 coarse cell found at once from exactly ranked plane crossings), the others one
-ray per thread (step by step); both implement the walk of Sec. 3.3 and must
-visit the same blocks in the same order.  With either forced for every pass
-the framebuffers and the per-pass counters are identical, and both match the
-oracle."""
+ray per thread (step by step); the segmented walk splits each ray's path at
+block planes of its dominant axis among a group of lanes.  All implement the
+walk of Sec. 3.3 and must visit the same blocks in the same order.  With any
+of them forced for every pass the framebuffers and the per-pass counters are
+identical, and all match the oracle."""
 import numpy as np
 import pytest
 
@@ -30,7 +31,7 @@ def spr():
     return m
 
 
-def render(spr, sc, walk, mode=None, k=1, k_max=64, slots=None):
+def render(spr, sc, walk, mode=None, k=1, k_max=64, slots=None, seg=0):
     import torch
     v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
     r = spr.spr_create_renderer(v, sc.W, sc.H)
@@ -43,6 +44,7 @@ def render(spr, sc, walk, mode=None, k=1, k_max=64, slots=None):
     else:
         spr.spr_set_speculation(r, spr.SPR_SPEC_ADAPTIVE, k_max=k_max)
     spr.spr_set_warp_walk_threshold(r, walk)
+    spr.spr_set_segment_walk(r, seg)
     rs, passes = spr.spr_render_to_convergence(r, 100000)
     fb = spr.spr_read_framebuffer(r)
     r.close()
@@ -119,5 +121,72 @@ def test_threshold_rejects_negative(spr, orc):
     r = spr.spr_create_renderer(v, 16, 16)
     with pytest.raises(spr.SprError):
         spr.spr_set_warp_walk_threshold(r, -1)
+    r.close()
+    v.close()
+
+
+# lane budgets of the segmented walk: 32 lanes per ray in every pass of these
+# small images, and about two lanes per ray in the first pass (more later)
+SEG_ALL = 1 << 30
+
+
+@pytest.mark.parametrize("dims,seed,W,H", [((33, 17, 26), 4, 64, 48), ((64, 64, 64), 5, 128, 96),
+                                           ((48, 40, 44), 21, 80, 64)])
+@pytest.mark.parametrize("spec", [("fixed", 1), ("fixed", 3), ("adaptive", 64)])
+@pytest.mark.parametrize("seg", ["all", "two"])
+def test_segment_walk_equals_thread_walk(spr, orc, dims, seed, W, H, spec, seg):
+    sc = value_scene(orc, dims, seed, W, H)
+    mode, k = spec
+    kw = dict(mode="fixed", k=k) if mode == "fixed" else dict(k_max=k)
+    a = render(spr, sc, THREAD, **kw)
+    b = render(spr, sc, THREAD, seg=SEG_ALL if seg == "all" else 2 * W * H, **kw)
+    same(a, b)
+    compare(sc, b[0])
+
+
+def test_segment_walk_many_blocks_per_lane(spr, orc):
+    """k = 4096 with two lanes per ray: a lane finds more visible blocks than
+    its shared-memory buffer holds and walks its part again, writing
+    directly; k = 40 with 32 lanes: most lanes' parts end before the k-th."""
+    sc = value_scene(orc, (64, 64, 64), 5, 96, 64)
+    for k, seg in ((4096, 2 * 96 * 64), (40, SEG_ALL), (33, 4 * 96 * 64)):
+        a = render(spr, sc, THREAD, mode="fixed", k=k)
+        b = render(spr, sc, THREAD, mode="fixed", k=k, seg=seg)
+        same(a, b)
+        compare(sc, b[0])
+
+
+def test_segment_walk_tight_cache(spr, orc):
+    sc = value_scene(orc, (48, 40, 44), 21, 80, 64)
+    a = render(spr, sc, THREAD, slots=24)
+    for seg in (SEG_ALL, 2 * 80 * 64):
+        b = render(spr, sc, THREAD, slots=24, seg=seg)
+        same(a, b)
+    assert any(p["retries"] for p in a[2])
+
+
+def test_segment_walk_diagonal_and_inside(spr, orc):
+    dims = (40, 40, 40)
+    vol = synth.volumes.value_noise(dims, seed=31, ref=40)
+    iso = float(np.float32(np.quantile(vol, 0.7)))
+    cam = synth.cameras.look_at((-12.0, -12.0, -12.0), (39.0, 39.0, 39.0), (0, 0, 1), 30.0, 64, 64)
+    sc = Scene(orc, dims, vol, 8, iso, cam, 64, 64)
+    for k in (1, 4, 64):
+        same(render(spr, sc, THREAD, mode="fixed", k=k), render(spr, sc, THREAD, mode="fixed", k=k, seg=SEG_ALL))
+    dims = (32, 32, 32)
+    vol = synth.volumes.value_noise(dims, seed=8, ref=32)
+    iso = float(np.float32(np.quantile(vol, 0.8)))
+    cam = synth.cameras.look_at((15.5, 16.25, 14.0), (31, 31, 31), (0, 0, 1), 70.0, 64, 64)
+    sc = Scene(orc, dims, vol, 8, iso, cam, 64, 64)
+    same(render(spr, sc, THREAD, mode="fixed", k=2), render(spr, sc, THREAD, mode="fixed", k=2, seg=SEG_ALL))
+
+
+def test_segment_walk_rejects_negative(spr, orc):
+    sc = value_scene(orc, (16, 16, 16), 2, 16, 16)
+    import torch
+    v = spr.spr_create_volume(sc.dims, sc.rate, torch.from_numpy(sc.comp).cuda())
+    r = spr.spr_create_renderer(v, 16, 16)
+    with pytest.raises(spr.SprError):
+        spr.spr_set_segment_walk(r, -1)
     r.close()
     v.close()
