@@ -26,6 +26,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -961,6 +962,8 @@ def measure_workload(wl, args, spr, _lib, torch, stream, rank, world, dist, loca
         spr.spr_set_warp_walk_threshold(r, args.warp_walk)
     if args.seg_lanes >= 0:
         spr.spr_set_segment_walk(r, args.seg_lanes)
+    if args.isect_staged:
+        spr.spr_set_intersect_staging(r, True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     L = _lib.load()
@@ -1205,6 +1208,12 @@ def main():
                     help="live-ray count below which a pass walks one ray per warp (-1: the library default)")
     ap.add_argument("--seg-lanes", type=int, default=-1,
                     help="lane budget of the segmented walk (-1: the library default, 0: off)")
+    ap.add_argument("--isect-staged", action="store_true",
+                    help="intersect from dual grids staged in shared memory (a variant; results unchanged)")
+    ap.add_argument("--cache-mb", type=int, default=0,
+                    help="override the workload's block-cache budget (MB; 0 keeps it)")
+    ap.add_argument("--fixed-k", type=int, default=0,
+                    help="fixed speculation count instead of the workload's rule (sweeps; 0 keeps it)")
     ap.add_argument("--k-max", type=int, default=0,
                     help="override the workload's speculation limit (k sweeps; 0 keeps it)")
     args = ap.parse_args()
@@ -1213,6 +1222,12 @@ def main():
         wl["dims"] = tuple(args.dims)
         wl["name"] = wl["name"].replace("2048x2048x1920", "x".join(map(str, args.dims))).replace(
             "512^3", "x".join(map(str, args.dims)))
+    if args.cache_mb > 0:
+        wl["cache_bytes"] = args.cache_mb << 20
+        wl["name"] = re.sub(r"cache [^,]*", "cache %d MB" % args.cache_mb, wl["name"], count=1)
+    if args.fixed_k > 0:
+        wl["spec"], wl["k"] = "fixed", args.fixed_k
+        wl["name"] = wl["name"].rsplit(", adaptive", 1)[0] + ", fixed k=%d" % args.fixed_k
     if args.k_max > 0:
         wl["k"] = args.k_max
         wl["name"] = wl["name"].rsplit("k<=", 1)[0] + f"k<={args.k_max}" if "k<=" in wl["name"] else wl["name"]
