@@ -2790,6 +2790,16 @@ Trace make_trace(spr_renderer *r)
     return T;
 }
 
+// Whether a pass can ever walk one ray per warp: the warp walks take passes
+// of fewer than coop_below rays that the segmented walk leaves alone (fewer
+// than two lanes per ray), which cannot happen when seg_threads >= 2 *
+// coop_below; then their kernels are not launched (an idle launch of 2,432
+// CTAs costs about 5 us per pass).
+bool coop_walks_possible(const spr_renderer *r)
+{
+    return r->coop_below > 0 && (r->seg_threads == 0 || (uint64_t)r->seg_threads < 2ull * r->coop_below);
+}
+
 int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphConditionalHandle h, int use_h,
                     bool capturing = false)
 {
@@ -2837,14 +2847,16 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
         make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
         r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
     count_launch();
-    traverse_coop_kernel<32><<<device_sm_count() * 16, 128, 0, s>>>(
-        make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
-        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
-    count_launch();
-    traverse_coop_kernel<16><<<device_sm_count() * 16, 128, 0, s>>>(
-        make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
-        r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
-    count_launch();
+    if (coop_walks_possible(r)) {
+        traverse_coop_kernel<32><<<device_sm_count() * 16, 128, 0, s>>>(
+            make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
+            r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
+        count_launch();
+        traverse_coop_kernel<16><<<device_sm_count() * 16, 128, 0, s>>>(
+            make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
+            r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->act_bits.as<uint32_t>(), ctr, S);
+        count_launch();
+    }
     if (r->seg_threads) {
         traverse_seg_kernel<<<device_sm_count() * 16, kSegThreads, 0, s>>>(
             make_geo(r), live0, live1, ps, r->state_in.as<uint64_t>(), r->state_out.as<uint64_t>(),
@@ -2873,14 +2885,14 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
                                  r->nbrays.as<uint32_t>()},
                         ctr + C_NVIS, s));
     if (fork) SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_act, 0));
-    count_entries_kernel<<<grid_for(cap, 256, 16), 256, 0, s>>>(
+    count_entries_kernel<<<grid_for(cap, 256, 4), 256, 0, s>>>(
         ps, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
         r->nbrays.as<uint32_t>(), r->erank.as<uint32_t>(), ctr, S);
     count_launch();
     SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, cap, ctr + C_NVIS,
                         ArrayCount{r->nbrays.as<uint32_t>(), ctr + C_OVERFLOW},
                         ArrayEmit{r->obrays.as<uint32_t>()}, ctr + C_NENT, s));
-    scatter_entries_kernel<<<grid_for(cap, 256, 16), 256, 0, s>>>(
+    scatter_entries_kernel<<<grid_for(cap, 256, 4), 256, 0, s>>>(
         ps, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
         r->obrays.as<uint32_t>(), r->erank.as<uint32_t>(), r->E.as<uint32_t>(), ctr, S);
     count_launch();
@@ -2897,7 +2909,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     SPR_TRY(run_compact(r->scan_status[1], r->scan_ticket[1], flags, r->n_slots, &ps->n_used,
                         VictimCount{lp, r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
                         VictimEmit{lp, ctr, r->victim.as<uint32_t>(), (uint32_t)r->n_slots}, ctr + C_NUNTOUCHED, sa));
-    assign_kernel<<<grid_for(r->cap_act, 256, 8), 256, 0, sa>>>(r->miss.as<uint32_t>(), r->victim.as<uint32_t>(),
+    assign_kernel<<<grid_for(r->cap_act, 256, 4), 256, 0, sa>>>(r->miss.as<uint32_t>(), r->victim.as<uint32_t>(),
                                                                r->blk_slot.as<uint32_t>(), r->slot_blk.as<uint32_t>(),
                                                                r->touched.as<uint8_t>(), ctr, ps, (uint32_t)r->n_slots);
     count_launch();
@@ -3475,7 +3487,9 @@ extern "C" int spr_set_warp_walk_threshold(spr_renderer *r, int64_t n_rays)
     if (!r) return set_error(SPR_ERR_INVALID_ARG, "NULL renderer");
     SPR_TRY(check_idle(r));
     if (n_rays < 0) return set_error(SPR_ERR_INVALID_ARG, "n_rays must be non-negative");
+    const bool before = coop_walks_possible(r);
     r->coop_below = (uint32_t)std::min<int64_t>(n_rays, 0xFFFFFFFFll);
+    if (coop_walks_possible(r) != before) drop_graph(r);   // the pass graph gains or loses the warp walks
     r->params_dirty = true;
     return SPR_OK;
 }
@@ -3487,8 +3501,11 @@ extern "C" int spr_set_segment_walk(spr_renderer *r, int64_t lanes)
     SPR_TRY(check_idle(r));
     if (lanes < 0) return set_error(SPR_ERR_INVALID_ARG, "negative lane budget");
     const uint32_t v = (uint32_t)std::min<int64_t>(lanes, 0x7FFFFFFFll);
-    if ((v != 0) != (r->seg_threads != 0)) drop_graph(r);   // the pass graph gains or loses the kernel
+    const bool before = coop_walks_possible(r);
+    const bool had_seg = r->seg_threads != 0;
     r->seg_threads = v;
+    // the pass graph gains or loses the segmented or the warp walks
+    if ((v != 0) != had_seg || coop_walks_possible(r) != before) drop_graph(r);
     r->params_dirty = true;
     return SPR_OK;
 }
