@@ -924,7 +924,7 @@ def stage_rooflines(prof_stats, stage, rate, pk):
                 for p in per_pass)
     out = {}
     for name, kernel, nbytes, units in (
-            ("traverse", "traverse_kernel / traverse_coop_kernel", trav,
+            ("traverse", "traverse_kernel / traverse_seg_kernel", trav,
              "live rays x %d B + speculated slots x %d B + walk steps x %d B" %
              (TRAV_BYTES_PER_RAY, TRAV_BYTES_PER_SLOT, TRAV_BYTES_PER_STEP)),
             ("decode", "decode_list_kernel", dec, "decoded blocks x %d B" % decode_bytes_per_block(rate)),
