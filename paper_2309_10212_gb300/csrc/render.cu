@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -39,6 +40,10 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint64_t kNoKey = ~0ull;
 constexpr uint64_t kStep = 1;   // state flag: the saved block was already taken
 constexpr uint64_t kDone = 2;   // state flag: the walk left the volume
+// state flag set by ray generation: the saved block is where the ray enters
+// the box of blocks that hold the isovalue, not where it enters the volume
+// (the blocks before it hold nothing); cleared by the first walk
+constexpr uint64_t kBoxed = 4;
 
 // counter record, device resident, read by the host once per pass
 enum Ctr {
@@ -152,11 +157,33 @@ struct DevParams {
 // when coarse cell 4s+(x,y,z) of super cell s has a nonzero fmask.  A walk
 // loads one word when it enters a coarse or super cell and then steps through
 // that cell's blocks without touching memory.
+//
+// The occupied box of a view: the lowest and highest block index per axis
+// among the blocks that hold its isovalue, {lo x, y, z, -, hi x, y, z, -}
+// (lo > hi when no block does).  A ray meets a visible block only while it
+// is inside the box, so its walk starts where it enters the box and ends
+// where it leaves it.
 struct Occ {
     const unsigned long long *fmask, *smask;
+    const int *box;   // 8 ints per view
     int ns[3];   // super grid over the coarse grid: ceil(nc / 4)
     int ts[3];   // super cells the traversal can visit: ceil(tc / 4)
 };
+
+// A walk has passed the occupied box once a block index goes beyond the
+// box's last index in the walk's direction (indices change monotonically, so
+// no later block is in the box): sgn_a * b_a > lim_a with lim_a = hi_a for
+// sgn_a > 0, -lo_a for sgn_a < 0 and INT_MAX for sgn_a = 0.
+__device__ __forceinline__ void box_limits(const int sgn[3], const int *bx, int lim[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) lim[a] = sgn[a] > 0 ? bx[4 + a] : (sgn[a] < 0 ? -bx[a] : INT_MAX);
+}
+
+__device__ __forceinline__ bool past_box(const int b[3], const int sgn[3], const int lim[3])
+{
+    return sgn[0] * b[0] > lim[0] || sgn[1] * b[1] > lim[1] || sgn[2] * b[2] > lim[2];
+}
 
 // camera and isovalue live in device memory (read at kernel start), so that a
 // captured pass graph stays valid when they change
@@ -409,9 +436,15 @@ __device__ __forceinline__ void warp_add(uint32_t *ctr, uint32_t v)
 
 // ------------------------------------------------------------- occupancy
 // one thread per coarse cell: the bits of its 4^3 blocks
+// and the occupied box: at launch box (8 ints) holds lo values above every
+// block index and hi values of -1; blockDim is a multiple of 32
 __global__ void fmask_kernel(const float2 *__restrict__ fine, VolGeom g, float iso,
-                             unsigned long long *__restrict__ fmask)
+                             unsigned long long *__restrict__ fmask, int *box)
 {
+    __shared__ int s_box[6];
+    if (threadIdx.x < 6) s_box[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : -1;
+    __syncthreads();
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncoarse;
          c += (int64_t)gridDim.x * blockDim.x) {
         int cx = (int)(c % g.nc[0]), cy = (int)((c / g.nc[0]) % g.nc[1]), cz = (int)(c / ((int64_t)g.nc[0] * g.nc[1]));
@@ -419,10 +452,30 @@ __global__ void fmask_kernel(const float2 *__restrict__ fine, VolGeom g, float i
         for (int k = 0; k < 64; ++k) {
             int x = 4 * cx + (k & 3), y = 4 * cy + ((k >> 2) & 3), z = 4 * cz + (k >> 4);
             if (x < g.nb[0] && y < g.nb[1] && z < g.nb[2] &&
-                holds(fine[x + (int64_t)g.nb[0] * (y + (int64_t)g.nb[1] * z)], iso))
+                holds(fine[x + (int64_t)g.nb[0] * (y + (int64_t)g.nb[1] * z)], iso)) {
                 m |= 1ull << k;
+                lo[0] = min(lo[0], x);
+                lo[1] = min(lo[1], y);
+                lo[2] = min(lo[2], z);
+                hi[0] = max(hi[0], x);
+                hi[1] = max(hi[1], y);
+                hi[2] = max(hi[2], z);
+            }
         }
         fmask[c] = m;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int l = __reduce_min_sync(0xFFFFFFFFu, lo[a]), h = __reduce_max_sync(0xFFFFFFFFu, hi[a]);
+        if ((threadIdx.x & 31) == 0 && h >= 0) {
+            atomicMin(&s_box[a], l);
+            atomicMax(&s_box[3 + a], h);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 && s_box[3 + threadIdx.x] >= 0) {
+        atomicMin(box + threadIdx.x, s_box[threadIdx.x]);
+        atomicMax(box + 4 + threadIdx.x, s_box[3 + threadIdx.x]);
     }
 }
 
@@ -520,7 +573,36 @@ __global__ void __launch_bounds__(256) raygen_kernel(Geo P, int H, uint64_t *__r
             } else {
                 int b[3];
                 for (int a = 0; a < 3; ++a) b[a] = locate_block(r, a, tin, g.tb[a]);
-                state[p] = pack_state(b, 0);
+                // the part of the ray inside the occupied box: per axis the
+                // blocks lo..hi are those the ray is in for t in [t(near), t(far))
+                const int *bx = P.occ.box + 8 * view;
+                Tq t0 = tin, t1 = tout;
+                bool none = false, moved = false;
+                for (int a = 0; a < 3; ++a) {
+                    const int lo = bx[a], hi = bx[4 + a];
+                    if (lo > hi || (r.sgn[a] == 0 && (b[a] < lo || b[a] > hi))) {
+                        none = true;
+                        break;
+                    }
+                    if (r.sgn[a] == 0) continue;
+                    const Tq tn = plane_t(r, a, (float)(r.sgn[a] > 0 ? 4 * lo : 4 * (hi + 1)));
+                    const Tq tf = plane_t(r, a, (float)(r.sgn[a] > 0 ? 4 * (hi + 1) : 4 * lo));
+                    if (tcmp(tn, t0) > 0) {
+                        t0 = tn;
+                        moved = true;
+                    }
+                    if (tcmp(tf, t1) < 0) t1 = tf;
+                }
+                // a ray that misses the box stays live with its walk done,
+                // so the live count (and the speculation it sets) is unchanged
+                uint64_t fl = 0;
+                if (none || tcmp(t0, t1) >= 0) {
+                    fl = kDone;
+                } else if (moved) {
+                    for (int a = 0; a < 3; ++a) b[a] = locate_block(r, a, t0, g.tb[a]);
+                    fl = kBoxed;
+                }
+                state[p] = pack_state(b, fl);
                 status[p] = 0;
                 in = true;
             }
@@ -617,7 +699,9 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
             walk_init(w, g);
             if (flags & kStep) alive = walk_step(w, g);
         }
-        flags &= ~kStep;
+        flags &= ~(kStep | kBoxed);
+        int lim[3];
+        box_limits(w.r.sgn, P.occ.box + 8 * view, lim);
         int steps = 0;
         uint32_t cur_s = 0xFFFFFFFFu, cur_c = 0xFFFFFFFFu;
         unsigned long long smask = 0ull, fmask = 0ull;
@@ -628,6 +712,10 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
                 break;
             }
             const int *b = w.b;
+            if (past_box(b, w.r.sgn, lim)) {
+                alive = false;
+                break;
+            }
             uint32_t sc = (uint32_t)(b[0] >> 4) + ns0 * ((uint32_t)(b[1] >> 4) + ns1 * (uint32_t)(b[2] >> 4));
             if (sc != cur_s) {
                 smask = __ldg(sm + sc);
@@ -747,7 +835,9 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
             walk_init(w, g);
             if (flags & kStep) alive = walk_step(w, g);
         }
-        flags &= ~kStep;
+        flags &= ~(kStep | kBoxed);
+        int lim[3];
+        box_limits(w.r.sgn, P.occ.box + 8 * view, lim);
         int steps = 0;
         while (alive) {   // uniform across the group: every lane holds the same walk
             if (++steps > max_steps) {
@@ -756,6 +846,10 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
                 break;
             }
             const int *b = w.b;
+            if (past_box(b, w.r.sgn, lim)) {
+                alive = false;
+                break;
+            }
             const uint32_t sc =
                 (uint32_t)(b[0] >> 4) + ns0 * ((uint32_t)(b[1] >> 4) + ns1 * (uint32_t)(b[2] >> 4));
             const uint32_t c =
@@ -912,7 +1006,8 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
 // path is cut at block planes of its dominant axis (the axis of largest
 // |d|; every block index along it changes monotonically): lane j owns the
 // blocks whose index along that axis lies in the j-th of SL equal parts of
-// the range from the current block to the volume's far side.  Lane 0
+// the range from the current block to the far side of the occupied box (the
+// walk ends there).  Lane 0
 // resumes the saved walk; lane j > 0 starts at the exact crossing time T_j
 // of its first plane, in the block containing p(T_j+) (located with the
 // exact predicates, the right-limit rule of the serial walk), unless the
@@ -934,7 +1029,9 @@ struct SegPart {
 };
 
 // The dominant axis and this lane's part; false when the part is empty.
-__device__ __forceinline__ bool seg_part(const Walk &w, const VolGeom &g, int SL, int gl, SegPart &sp)
+// The parts end at the far side of the occupied box bx (the walk stops
+// there), never before the current block.
+__device__ __forceinline__ bool seg_part(const Walk &w, const VolGeom &g, const int *bx, int SL, int gl, SegPart &sp)
 {
     int as = 0;
     float best = -1.f;
@@ -949,7 +1046,8 @@ __device__ __forceinline__ bool seg_part(const Walk &w, const VolGeom &g, int SL
     const int sg = as == 0 ? w.r.sgn[0] : (as == 1 ? w.r.sgn[1] : w.r.sgn[2]);
     const int tbq = as == 0 ? g.tb[0] : (as == 1 ? g.tb[1] : g.tb[2]);
     sp.b0 = bq;
-    const int span = sg > 0 ? tbq - bq : bq + 1;
+    const int loq = bx[as], hiq = bx[4 + as];
+    const int span = max(1, sg > 0 ? min(tbq, hiq + 1) - bq : bq - max(loq, 0) + 1);
     // rounded up, so that lane 0's part always holds the current block (only
     // lane 0 resumes the saved walk); later lanes may get empty parts
     sp.o0 = (int)(((int64_t)gl * span + SL - 1) / SL);
@@ -1022,6 +1120,8 @@ __device__ __forceinline__ int seg_walk(Walk &w, const Geo &P, const SegPart &sp
     const unsigned long long *fm = P.occ.fmask + view * P.fstride, *sm = P.occ.smask + view * P.sstride;
     const uint32_t nb0 = g.nb[0], nb1 = g.nb[1], nc0 = g.nc[0], nc1 = g.nc[1];
     const uint32_t ns0 = P.occ.ns[0], ns1 = P.occ.ns[1];
+    int lim[3];
+    box_limits(w.r.sgn, P.occ.box + 8 * view, lim);
     int cnt = 0, steps = 0;
     bool alive = true;
     uint32_t cur_s = 0xFFFFFFFFu, cur_c = 0xFFFFFFFFu;
@@ -1034,6 +1134,10 @@ __device__ __forceinline__ int seg_walk(Walk &w, const Geo &P, const SegPart &sp
             break;
         }
         const int *b = w.b;
+        if (past_box(b, w.r.sgn, lim)) {
+            alive = false;
+            break;
+        }
         const uint32_t sc = (uint32_t)(b[0] >> 4) + ns0 * ((uint32_t)(b[1] >> 4) + ns1 * (uint32_t)(b[2] >> 4));
         if (sc != cur_s) {
             smask = __ldg(sm + sc);
@@ -1077,7 +1181,7 @@ __device__ __forceinline__ int seg_walk(Walk &w, const Geo &P, const SegPart &sp
     return cnt;
 }
 
-__global__ void __launch_bounds__(kSegThreads, 5) traverse_seg_kernel(Geo P, const uint32_t *__restrict__ live0,
+__global__ void __launch_bounds__(kSegThreads, 6) traverse_seg_kernel(Geo P, const uint32_t *__restrict__ live0,
                                                                    const uint32_t *__restrict__ live1,
                                                                    const PassState *__restrict__ ps,
                                                                    const uint64_t *__restrict__ state_in,
@@ -1127,7 +1231,7 @@ __global__ void __launch_bounds__(kSegThreads, 5) traverse_seg_kernel(Geo P, con
         if (!(flags & kDone)) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) w.b[a] = b_saved[a];
-            if (seg_part(w, g, SL, gl, sp)) active = seg_start(w, g, sp, gl, b_saved, (flags & kStep) != 0);
+            if (seg_part(w, g, P.occ.box + 8 * view, SL, gl, sp)) active = seg_start(w, g, sp, gl, b_saved, (flags & kStep) != 0);
             else if (gl == 0) active = false;
             if (gl == 0 && !active) exited = true;   // lane 0's step left the volume
         } else {
@@ -2056,7 +2160,20 @@ __device__ __noinline__ void ray_features(const Geo &P, const PassState *ps, uin
     const View &vw = P.views[view];
     Ray r;
     make_ray(r, vw.cam.eye, vw.cam.p00, vw.cam.du, vw.cam.dv, px, py);
-    const int b0 = (int)(st & 0xFFFF), b1 = (int)((st >> 16) & 0xFFFF), b2 = (int)((st >> 32) & 0xFFFF);
+    int b0 = (int)(st & 0xFFFF), b1 = (int)((st >> 16) & 0xFFFF), b2 = (int)((st >> 32) & 0xFFFF);
+    if ((st >> 48) & kBoxed) {
+        // a walk not yet started from the occupied box: the features are
+        // those of the block where the ray enters the volume
+        Tq tin{0.f, 1.f};
+        for (int a = 0; a < 3; ++a) {
+            if (r.sgn[a] == 0) continue;
+            const Tq tn = plane_t(r, a, r.sgn[a] > 0 ? 0.f : (float)(g.dims[a] - 1));
+            if (tcmp(tn, tin) > 0) tin = tn;
+        }
+        b0 = locate_block(r, 0, tin, g.tb[0]);
+        b1 = locate_block(r, 1, tin, g.tb[1]);
+        b2 = locate_block(r, 2, tin, g.tb[2]);
+    }
     const float dn = sqrtf(r.d[0] * r.d[0] + r.d[1] * r.d[1] + r.d[2] * r.d[2]);
     const float ex = (float)(g.dims[0] - 1), ey = (float)(g.dims[1] - 1), ez = (float)(g.dims[2] - 1);
     const float diag = sqrtf(ex * ex + ey * ey + ez * ez);
@@ -2436,6 +2553,7 @@ struct spr_renderer {
     DevBuf cache, blk_slot, slot_blk, lru[2], touched, miss, victim;
     int64_t launches = 0;         // kernels launched since the last render started
     DevBuf occ_fine, occ_super;   // brick masks per coarse cell and per super cell
+    DevBuf occ_box;               // occupied box per view (8 ints)
     Occ occ{};
     float occ_iso[kMaxViews];     // isovalue each view's brick masks were built for
     // look-back scratch, one set per branch of a pass that can run a scan
@@ -2501,7 +2619,7 @@ void free_all(spr_renderer *r)
                       &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
                       &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
                       &r->scan_ticket[1], &r->scan_ticket[2], &r->ctr, &r->occ_fine, &r->occ_super,
-                      &r->ps, &r->camd, &r->lbits, &r->kray, &r->koff, &r->eray, &r->policy,
+                      &r->occ_box, &r->ps, &r->camd, &r->lbits, &r->kray, &r->koff, &r->eray, &r->policy,
                       &r->tr_count, &r->tr_taken, &r->tr_need};
     for (DevBuf *b : bufs) buf_free(*b, nullptr);
     if (r->h_ctr) cudaFreeHost(r->h_ctr);
@@ -2627,7 +2745,10 @@ int update_occupancy(spr_renderer *r, cudaStream_t s)
         if (r->occ_iso[v] == iso) continue;
         unsigned long long *fm = r->occ_fine.as<unsigned long long>() + v * g.ncoarse;
         unsigned long long *sm = r->occ_super.as<unsigned long long>() + v * ns;
-        fmask_kernel<<<grid_for(g.ncoarse, 128, 16), 128, 0, s>>>(r->vol->fine.as<float2>(), g, iso, fm);
+        int *box = r->occ_box.as<int>() + 8 * v;
+        SPR_CUDA_TRY(cudaMemsetAsync(box, 0x7F, 4 * sizeof(int), s));       // lo: 0x7F7F7F7F
+        SPR_CUDA_TRY(cudaMemsetAsync(box + 4, 0xFF, 4 * sizeof(int), s));   // hi: -1
+        fmask_kernel<<<grid_for(g.ncoarse, 128, 16), 128, 0, s>>>(r->vol->fine.as<float2>(), g, iso, fm, box);
         smask_kernel<<<grid_for(ns, 128, 16), 128, 0, s>>>(fm, g, r->occ, sm);
         count_launch(2);
         SPR_CUDA_TRY(cudaGetLastError());
@@ -3103,7 +3224,7 @@ int alloc_view_buffers(spr_renderer *r)
     cudaStream_t s = nullptr;
     DevBuf *bufs[] = {&r->state_in, &r->state_out, &r->status, &r->live[0], &r->live[1], &r->keys,
                       &r->fb_depth, &r->fb_rgba, &r->fb_block, &r->fb_cell, &r->fb_final, &r->lbits,
-                      &r->occ_fine, &r->occ_super};
+                      &r->occ_fine, &r->occ_super, &r->occ_box};
     for (DevBuf *b : bufs) buf_free(*b, s);
     const int64_t np = r->npix_cap;
     const int64_t ns = (int64_t)r->occ.ns[0] * r->occ.ns[1] * r->occ.ns[2];
@@ -3116,10 +3237,12 @@ int alloc_view_buffers(spr_renderer *r)
         (rc = buf_alloc(r->fb_final, 4 * np, s)) ||
         (rc = buf_alloc(r->lbits, 4 * (tiled_ray_count(r->W, r->H) * r->view_cap / 32 + 1), s)) ||
         (rc = buf_alloc(r->occ_fine, 8 * r->vol->g.ncoarse * r->view_cap, s)) ||
-        (rc = buf_alloc(r->occ_super, 8 * ns * r->view_cap, s)))
+        (rc = buf_alloc(r->occ_super, 8 * ns * r->view_cap, s)) ||
+        (rc = buf_alloc(r->occ_box, 32 * r->view_cap, s)))
         return rc;
     r->occ.fmask = r->occ_fine.as<unsigned long long>();
     r->occ.smask = r->occ_super.as<unsigned long long>();
+    r->occ.box = r->occ_box.as<int>();
     for (int v = 0; v < kMaxViews; ++v) r->occ_iso[v] = NAN;
     return SPR_OK;
 }
