@@ -269,6 +269,15 @@ def mixing_layer(dims=(2048, 2048, 1920), device=None, slab: int = 64, seed: int
     return vol if device is not None else vol.numpy()
 
 
+def sphere(dims, centre, radius: float) -> np.ndarray:
+    """float32, 1 at the centre falling linearly to 0 at 2 x radius: the
+    level 0.5 is the sphere of the given radius.  Placed off-centre it gives
+    a volume whose blocks of that level fill a small corner."""
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in dims[::-1]], indexing="ij")
+    d = np.sqrt((x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2)
+    return np.clip(1.0 - d / (2.0 * radius), 0.0, 1.0).astype(np.float32)
+
+
 def u8_to_f32(u8):
     """The value the renderer sees for an 8-bit voxel: (float)u / 255.0f."""
     if isinstance(u8, np.ndarray):

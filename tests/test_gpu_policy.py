@@ -200,8 +200,22 @@ def features_at_entry(orc, sc, pix):
     return rays, f
 
 
-def test_trace_features_and_labels(spr, orc):
-    sc = value_scene(orc, (40, 36, 32), 53, 80, 64, lists=True)
+def sphere_scene(orc):
+    """A sphere in one corner: most rays enter the volume well before the box
+    of blocks that hold the isovalue, so their walks start inside it."""
+    from test_gpu_render import Scene
+    dims = (72, 64, 56)
+    vol = synth.volumes.sphere(dims, (54.0, 16.0, 40.0), 7.0)
+    cam = synth.cameras.look_at((-50.0, 80.0, 90.0), (54.0, 16.0, 40.0), (0, 0, 1), 40.0, 80, 64)
+    return Scene(orc, dims, vol, 8, 0.5, cam, 80, 64, lists=True)
+
+
+@pytest.mark.parametrize("scene", ["noise", "sphere"])
+def test_trace_features_and_labels(spr, orc, scene):
+    """The first pass's features are those of the block where each ray enters
+    the volume, also where the walk itself starts later, at the box of blocks
+    that hold the isovalue (the sphere scene)."""
+    sc = value_scene(orc, (40, 36, 32), 53, 80, 64, lists=True) if scene == "noise" else sphere_scene(orc)
     tr = spr.Trace(80 * 64 * 40)
     fb, rs, passes = render(spr, sc, spr.SPR_SPEC_ADAPTIVE, k_max=8, trace=tr)
     n = tr.n

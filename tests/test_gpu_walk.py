@@ -236,3 +236,60 @@ def test_sparse_volume_hyper_cells(spr, orc):
     same(a, render(spr, sc, THREAD, seg=SEG_ALL))
     same(a, render(spr, sc, WARP))
     compare(sc, a[0])
+
+
+
+def grid_camera(eye, dx, step, n):
+    """n x n rays along (dx, (i + 0.5 - n/2) step, (j + 0.5 - n/2) step): all
+    exact in float32, and for odd n the middle column has d_y = 0 and the
+    middle row d_z = 0 exactly."""
+    f = lambda v: np.asarray(v, dtype=np.float32)
+    h = -0.5 * n * step
+    return dict(eye=f(eye), p00=f((dx, h, h)), du=f((0.0, step, 0.0)), dv=f((0.0, 0.0, step)))
+
+
+# a sphere of radius 9 in one corner of a 96 x 80 x 72 volume
+BOX_DIMS, BOX_CENTRE = (96, 80, 72), (70.0, 20.0, 50.0)
+BOX_CAMS = [
+    # along +x through the sphere's centre
+    (grid_camera((-30.0, 20.3125, 50.1875), 1.0, 2.0 ** -5, 17), 17, 17),
+    # the same directions with the axis-parallel row below the box
+    (grid_camera((-30.0, 20.3125, 5.1875), 1.0, 2.0 ** -5, 17), 17, 17),
+    # eye inside the volume, outside the box, looking back along -x
+    (grid_camera((90.0, 21.3125, 49.1875), -1.0, 2.0 ** -3, 17), 17, 17),
+    # eye inside the box, outside the sphere
+    (grid_camera((78.5, 27.3125, 57.1875), -1.0, 2.0 ** -2, 17), 17, 17),
+    (synth.cameras.look_at((-60.0, -50.0, 120.0), (48.0, 40.0, 36.0), (0, 0, 1), 50.0, 48, 40), 48, 40),
+]
+
+
+def test_occupied_box(spr, orc):
+    """The box of blocks that hold the isovalue is small: the walks start
+    where each ray enters it and stop where it leaves it.  Rays that enter
+    the volume but miss the box stay live in the first pass (the live count,
+    k and every counter as without the box).  Rays with a zero direction
+    component inside and outside the box's range, an eye inside the volume
+    but outside the box and an eye inside the box: the one-thread, segmented
+    and warp walks agree and match the oracle, and the first pass holds every
+    ray that enters the volume.  An isovalue no block holds ends every ray in
+    the first pass with nothing decoded."""
+    vol = synth.volumes.sphere(BOX_DIMS, BOX_CENTRE, 9.0)
+    hits = 0
+    for cam, w, h in BOX_CAMS:
+        sc = Scene(orc, BOX_DIMS, vol, 8, 0.5, cam, w, h)
+        a = render(spr, sc, THREAD)
+        same(a, render(spr, sc, THREAD, seg=SEG_ALL))
+        same(a, render(spr, sc, WARP))
+        compare(sc, a[0])
+        n_enter = int((orc.entry_blocks(BOX_DIMS, cam, w, h) != 0xFFFFFFFF).sum())
+        assert a[2][0]["n_active"] == n_enter > 0
+        hits += int((a[0]["status"] == 1).sum())
+    assert hits > 100
+    # no block holds the isovalue: every entering ray ends in pass 1
+    cam, w, h = BOX_CAMS[-1]
+    sc = Scene(orc, BOX_DIMS, vol, 8, 2.0, cam, w, h)
+    fb, rs, passes = render(spr, sc, THREAD)
+    assert len(passes) == 1 and rs["blocks_decoded"] == 0 and rs["n_hits"] == 0
+    assert passes[0]["n_active"] == int((orc.entry_blocks(BOX_DIMS, cam, w, h) != 0xFFFFFFFF).sum()) > 0
+    assert np.all(fb["status"] == 2)
+    compare(sc, fb)
