@@ -1310,13 +1310,6 @@ __global__ void __launch_bounds__(kSegThreads, 6) traverse_seg_kernel(Geo P, con
 }
 
 // --------------------------------------------------------------- grouping
-struct BitsCount {
-    const uint32_t *bits;
-    const uint32_t *skip;
-    __device__ bool enabled() const { return !skip || !*skip; }
-    __device__ uint32_t operator()(int64_t w) const { return __popc(bits[w]); }
-};
-
 struct BitsEmit {
     const uint32_t *bits;
     uint32_t *wpre;  // optional: the prefix of each word that holds a set bit
@@ -1342,6 +1335,116 @@ __device__ __forceinline__ uint32_t vis_rank(const uint32_t *bits, const uint32_
 {
     uint32_t w = b >> 5;
     return wpre[w] + __popc(bits[w] & ((1u << (b & 31)) - 1u));
+}
+
+// Compaction of a block bitmap (one bit per block: millions of words, few
+// set bits).  The single-pass look-back is bound there by how far each
+// tile's prefix travels: the CTAs of the first wave run at once, and the
+// last of them adds hundreds of predecessors' aggregates, 32 per round.
+// Two kernels instead: bits_reduce_kernel counts each tile's bits;
+// bits_emit_kernel adds the counts of the tiles before its own (a few
+// thousand at most, read from L2), scans its words and emits their bits in
+// order.  Same outputs as a compact_kernel over the words' popcounts.
+constexpr int kBitsThreads = 256, kBitsWords = 8;
+constexpr int64_t kBitsTile = (int64_t)kBitsThreads * kBitsWords;   // words per tile
+
+inline int64_t bits_tiles(int64_t nwords) { return std::max<int64_t>(1, (nwords + kBitsTile - 1) / kBitsTile); }
+
+// this thread's 8 words (two 16-byte loads when all lie below n)
+__device__ __forceinline__ void load_words8(const uint32_t *bits, int64_t first, int64_t n, uint32_t w[kBitsWords])
+{
+    if (first + kBitsWords <= n) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(bits + first);
+        const uint4 b = *reinterpret_cast<const uint4 *>(bits + first + 4);
+        w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w;
+        w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kBitsWords; ++j) w[j] = first + j < n ? bits[first + j] : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kBitsThreads) bits_reduce_kernel(const uint32_t *__restrict__ bits, int64_t n,
+                                                                   uint32_t *__restrict__ tile_sum)
+{
+    __shared__ uint32_t s_w[kBitsThreads / 32];
+    uint32_t w[kBitsWords];
+    load_words8(bits, (int64_t)blockIdx.x * kBitsTile + (int64_t)threadIdx.x * kBitsWords, n, w);
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < kBitsWords; ++j) c += __popc(w[j]);
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int i = 0; i < kBitsThreads / 32; ++i) t += s_w[i];
+        tile_sum[blockIdx.x] = t;
+    }
+}
+
+// total (and *over = total > over_limit, when over is given) from the last
+// tile's last thread
+template <class EmitF>
+__global__ void __launch_bounds__(kBitsThreads) bits_emit_kernel(const uint32_t *__restrict__ bits, int64_t n,
+                                                                 const uint32_t *__restrict__ tile_sum, EmitF emit,
+                                                                 uint32_t *total, uint32_t *over, uint32_t over_limit)
+{
+    __shared__ uint32_t s_w[kBitsThreads / 32];
+    __shared__ uint32_t s_pre;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // the tile's prefix: the bits of the tiles before it
+    uint32_t acc = 0;
+    for (int64_t t = threadIdx.x; t < (int64_t)blockIdx.x; t += kBitsThreads) acc += tile_sum[t];
+    acc = __reduce_add_sync(0xFFFFFFFFu, acc);
+    if (lane == 0) s_w[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int i = 0; i < kBitsThreads / 32; ++i) t += s_w[i];
+        s_pre = t;
+    }
+    __syncthreads();
+    // this thread's words and their exclusive prefix within the tile
+    const int64_t first = (int64_t)blockIdx.x * kBitsTile + (int64_t)threadIdx.x * kBitsWords;
+    uint32_t w[kBitsWords], c[kBitsWords], local = 0;
+    load_words8(bits, first, n, w);
+#pragma unroll
+    for (int j = 0; j < kBitsWords; ++j) {
+        c[j] = __popc(w[j]);
+        local += c[j];
+    }
+    uint32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t v = lane < kBitsThreads / 32 ? s_w[lane] : 0u;
+        uint32_t vi = v;
+#pragma unroll
+        for (int o = 1; o < kBitsThreads / 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, vi, o);
+            if (lane >= o) vi += y;
+        }
+        if (lane < kBitsThreads / 32) s_w[lane] = vi - v;   // exclusive warp offsets
+    }
+    __syncthreads();
+    uint32_t run = s_pre + s_w[wid] + incl - local;
+#pragma unroll
+    for (int j = 0; j < kBitsWords; ++j) {
+        if (first + j < n) emit(first + j, run, c[j]);
+        run += c[j];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kBitsThreads - 1) {
+        if (total) *total = run;
+        if (over) *over = run > over_limit ? 1u : 0u;
+    }
 }
 
 __global__ void count_entries_kernel(const PassState *ps, const uint32_t *__restrict__ rbid, const uint32_t *vis_bits,
@@ -2501,6 +2604,20 @@ int run_compact(DevBuf &status, DevBuf &ticket, uint32_t *flags, int64_t n_cap, 
     return SPR_OK;
 }
 
+// compaction of a block bitmap of nwords words (two kernels); tsum holds
+// bits_tiles(nwords) counts
+template <class EF>
+int run_bits_compact(const uint32_t *bits, int64_t nwords, uint32_t *tsum, EF ef, uint32_t *total, cudaStream_t s,
+                     uint32_t *over = nullptr, uint32_t over_limit = 0)
+{
+    const int64_t tiles = bits_tiles(nwords);
+    bits_reduce_kernel<<<(unsigned)tiles, kBitsThreads, 0, s>>>(bits, nwords, tsum);
+    bits_emit_kernel<EF><<<(unsigned)tiles, kBitsThreads, 0, s>>>(bits, nwords, tsum, ef, total, over, over_limit);
+    count_launch(2);
+    SPR_CUDA_TRY(cudaGetLastError());
+    return SPR_OK;
+}
+
 }  // namespace spr
 
 using namespace spr;
@@ -2548,6 +2665,7 @@ struct spr_renderer {
     DevBuf tr_count, tr_taken, tr_need;
     int64_t cap_entries = 0;
     DevBuf vis_bits, act_bits, vis_wpre, ivis, iact, nbrays, obrays;
+    DevBuf bits_tsum;   // tile counts of the two bitmap compactions (active, visible)
     DevBuf lbits;   // enter bits at ray generation, alive bits at resolve (one per live position)
     int64_t nwords = 0, cap_act = 0;
     DevBuf cache, blk_slot, slot_blk, lru[2], touched, miss, victim;
@@ -2614,7 +2732,7 @@ void free_all(spr_renderer *r)
     drop_graph(r);
     DevBuf *bufs[] = {&r->state_in, &r->state_out, &r->status, &r->live[0], &r->live[1], &r->keys,
                       &r->fb_depth, &r->fb_rgba, &r->fb_block, &r->fb_cell, &r->fb_final, &r->rbid,
-                      &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre,
+                      &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre, &r->bits_tsum,
                       &r->ivis, &r->iact, &r->nbrays, &r->obrays, &r->cache, &r->blk_slot,
                       &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
                       &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
@@ -2993,18 +3111,16 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
 
     // (b) compact the marks; group the entries by visible block.  The active
     // scan (cache branch) decides whether the pass overflows the cache.
-    SPR_TRY(run_compact(r->scan_status[1], r->scan_ticket[1], flags, r->nwords, nullptr,
-                        BitsCount{r->act_bits.as<uint32_t>(), nullptr},
-                        BitsEmit{r->act_bits.as<uint32_t>(), nullptr, r->iact.as<uint32_t>(),
-                                 nullptr},
-                        ctr + C_NACT, sa, kDefaultSpinLimit, -1, ctr + C_OVERFLOW, (uint32_t)r->n_slots));
+    uint32_t *tsum = r->bits_tsum.as<uint32_t>();
+    SPR_TRY(run_bits_compact(r->act_bits.as<uint32_t>(), r->nwords, tsum,
+                             BitsEmit{r->act_bits.as<uint32_t>(), nullptr, r->iact.as<uint32_t>(), nullptr},
+                             ctr + C_NACT, sa, ctr + C_OVERFLOW, (uint32_t)r->n_slots));
     SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, sa));
     if (fork) SPR_CUDA_TRY(cudaEventRecord(ev_act, sa));
-    SPR_TRY(run_compact(r->scan_status[0], r->scan_ticket[0], flags, r->nwords, nullptr,
-                        BitsCount{r->vis_bits.as<uint32_t>(), nullptr},
-                        BitsEmit{r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(), r->ivis.as<uint32_t>(),
-                                 r->nbrays.as<uint32_t>()},
-                        ctr + C_NVIS, s));
+    SPR_TRY(run_bits_compact(r->vis_bits.as<uint32_t>(), r->nwords, tsum + bits_tiles(r->nwords),
+                             BitsEmit{r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(), r->ivis.as<uint32_t>(),
+                                      r->nbrays.as<uint32_t>()},
+                             ctr + C_NVIS, s));
     if (fork) SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_act, 0));
     count_entries_kernel<<<grid_for(cap, 256, 4), 256, 0, s>>>(
         ps, r->rbid.as<uint32_t>(), r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(),
@@ -3373,6 +3489,7 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
     }
     if ((rc = buf_alloc(r->vis_bits, 4 * r->nwords, s)) ||
         (rc = buf_alloc(r->act_bits, 4 * r->nwords, s)) || (rc = buf_alloc(r->vis_wpre, 4 * r->nwords, s)) ||
+        (rc = buf_alloc(r->bits_tsum, 8 * bits_tiles(r->nwords), s)) ||
         (rc = buf_alloc(r->blk_slot, 4 * vol->g.nblocks, s)) || (rc = buf_alloc(r->scan_ticket[0], 64, s)) ||
         (rc = buf_alloc(r->scan_ticket[1], 64, s)) || (rc = buf_alloc(r->scan_ticket[2], 64, s)) ||
         (rc = buf_alloc(r->ctr, sizeof(uint32_t) * C_COUNT, s)) ||
@@ -3847,12 +3964,12 @@ extern "C" int spr_renderer_memory(const spr_renderer *r, size_t *device_bytes)
     if (!r || !device_bytes) return set_error(SPR_ERR_INVALID_ARG, "NULL argument");
     const DevBuf *bufs[] = {&r->state_in, &r->state_out, &r->status, &r->live[0], &r->live[1], &r->keys,
                             &r->fb_depth, &r->fb_rgba, &r->fb_block, &r->fb_cell, &r->fb_final, &r->rbid,
-                            &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre,
+                            &r->erank, &r->E, &r->vis_bits, &r->act_bits, &r->vis_wpre, &r->bits_tsum,
                             &r->ivis, &r->iact, &r->nbrays, &r->obrays, &r->cache, &r->blk_slot,
                             &r->slot_blk, &r->lru[0], &r->lru[1], &r->touched, &r->miss, &r->victim,
                             &r->scan_status[0], &r->scan_status[1], &r->scan_status[2], &r->scan_ticket[0],
                             &r->scan_ticket[1], &r->scan_ticket[2], &r->ctr, &r->occ_fine, &r->occ_super,
-                            &r->ps, &r->camd, &r->lbits, &r->kray, &r->koff, &r->eray, &r->policy,
+                            &r->occ_box, &r->ps, &r->camd, &r->lbits, &r->kray, &r->koff, &r->eray, &r->policy,
                             &r->tr_count, &r->tr_taken, &r->tr_need};
     size_t n = 0;
     for (const DevBuf *b : bufs) n += b->bytes;
@@ -3876,9 +3993,9 @@ extern "C" int spr_renderer_memory_estimate(const spr_volume *vol, int width, in
     for (int a = 0; a < 3; ++a) ns *= (g.nc[a] + 3) / 4;
     const int64_t scan_items = std::max({tiled_ray_count(width, height) * n_views, slots, nwords, cap, act,
                                          (int64_t)1});
-    int64_t n = 12 * nwords + 4 * g.nblocks                        // block bitmaps, block -> slot
+    int64_t n = 12 * nwords + 8 * bits_tiles(nwords) + 4 * g.nblocks   // block bitmaps, block -> slot
                 + 57 * np + 4 * (tiled_ray_count(width, height) * n_views / 32 + 1)   // per ray, bitmap
-                + 8 * (g.ncoarse + ns) * n_views                   // brick masks
+                + (8 * (g.ncoarse + ns) + 32) * n_views            // brick masks, occupied box
                 + 269 * slots                                       // cache slots and their tables
                 + 24 * cap + 8 + 12 * act                           // entries, requests
                 + (per_ray_mode(spec_mode) ? 4 * cap + 8 * np : 0)  // per-ray counts, offsets, entry rays
