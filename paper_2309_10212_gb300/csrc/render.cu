@@ -2004,11 +2004,21 @@ __global__ void __launch_bounds__(128, 4) intersect_kernel(RT R, const uint32_t 
     const uint32_t *__restrict__ live = (ps->parity & 1) ? live1 : live0;
     const uint32_t n = ctr[C_NENT];
     const VolGeom &g = R.P.g;
+    // Entries are grouped by block in block-id order, z slowest.  When the
+    // first view looks down z (its central ray has d_z < 0), a ray's earlier
+    // blocks have the higher ids: the queue then runs from the end, so that
+    // more entries find their ray's hit already recorded and are skipped.
+    bool down;
+    {
+        const Cam &c = R.P.views[0].cam;
+        down = c.p00[2] + 0.5f * (float)R.P.W * c.du[2] + 0.5f * (float)R.P.H * c.dv[2] < 0.f;
+    }
     for (;;) {
         const uint32_t base = warp_take(&ctr[C_QISECT]);
         if (base >= n) break;
-        const uint32_t idx = base + (threadIdx.x & 31);
-        if (idx >= n) continue;
+        const uint32_t q = base + (threadIdx.x & 31);
+        if (q >= n) continue;
+        const uint32_t idx = down ? n - 1 - q : q;
         uint32_t e = E[idx];
         uint32_t b = rbid[e];
         uint32_t i, j;
