@@ -1006,8 +1006,8 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
 // path is cut at block planes of its dominant axis (the axis of largest
 // |d|; every block index along it changes monotonically): lane j owns the
 // blocks whose index along that axis lies in the j-th of SL equal parts of
-// the range from the current block to the far side of the occupied box (the
-// walk ends there).  Lane 0
+// the range from the current block to the block where the ray leaves the
+// occupied box (the walk ends there).  Lane 0
 // resumes the saved walk; lane j > 0 starts at the exact crossing time T_j
 // of its first plane, in the block containing p(T_j+) (located with the
 // exact predicates, the right-limit rule of the serial walk), unless the
@@ -1029,8 +1029,8 @@ struct SegPart {
 };
 
 // The dominant axis and this lane's part; false when the part is empty.
-// The parts end at the far side of the occupied box bx (the walk stops
-// there), never before the current block.
+// The parts end at the block where the ray leaves the occupied box bx or
+// the volume (the walk stops there), never before the current block.
 __device__ __forceinline__ bool seg_part(const Walk &w, const VolGeom &g, const int *bx, int SL, int gl, SegPart &sp)
 {
     int as = 0;
@@ -1046,8 +1046,26 @@ __device__ __forceinline__ bool seg_part(const Walk &w, const VolGeom &g, const 
     const int sg = as == 0 ? w.r.sgn[0] : (as == 1 ? w.r.sgn[1] : w.r.sgn[2]);
     const int tbq = as == 0 ? g.tb[0] : (as == 1 ? g.tb[1] : g.tb[2]);
     sp.b0 = bq;
+    // the ray leaves the box (or the volume) at T1, its first far-plane
+    // crossing; the block holding p(T1+) bounds the walk along the dominant
+    // axis (the walk's blocks before T1 lie between the current one and it)
+    Tq t1{0.f, 1.f};
+    bool have = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (w.r.sgn[a] == 0) continue;
+        const float farp = w.r.sgn[a] > 0 ? fminf((float)(4 * (bx[4 + a] + 1)), (float)(g.dims[a] - 1))
+                                           : fmaxf((float)(4 * bx[a]), 0.f);
+        const Tq tf = plane_t(w.r, a, farp);
+        if (!have || tcmp(tf, t1) < 0) {
+            t1 = tf;
+            have = true;
+        }
+    }
     const int loq = bx[as], hiq = bx[4 + as];
-    const int span = max(1, sg > 0 ? min(tbq, hiq + 1) - bq : bq - max(loq, 0) + 1);
+    const int span_box = max(1, sg > 0 ? min(tbq, hiq + 1) - bq : bq - max(loq, 0) + 1);
+    const int bend = locate_block(w.r, as, t1, tbq);
+    const int span = have ? max(1, min(span_box, (sg > 0 ? bend - bq : bq - bend) + 1)) : span_box;
     // rounded up, so that lane 0's part always holds the current block (only
     // lane 0 resumes the saved walk); later lanes may get empty parts
     sp.o0 = (int)(((int64_t)gl * span + SL - 1) / SL);
