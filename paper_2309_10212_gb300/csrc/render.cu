@@ -1544,12 +1544,18 @@ __device__ __forceinline__ uint32_t fresh_taken(const PassState *ps, const uint3
     return min(ctr[C_NMISS], n_slots - ps->fresh_lo);
 }
 
-// untouched used slots in LRU order: the first ones become victims
+// Untouched used slots in LRU order, before the assignment: the first ones
+// become victims.  Runs only when the never-used slots do not cover the
+// misses (otherwise no victim is taken and the scan is skipped).
 struct VictimCount {
     LruPair lru;
     const uint8_t *touched;
-    const uint32_t *skip;
-    __device__ bool enabled() const { return !*skip; }
+    const uint32_t *ctr;
+    uint32_t n_slots;
+    __device__ bool enabled() const
+    {
+        return !ctr[C_OVERFLOW] && ctr[C_NMISS] > fresh_taken(lru.ps, ctr, n_slots);
+    }
     __device__ uint32_t operator()(int64_t i) const { return touched[lru.cur()[i]] ? 0u : 1u; }
 };
 
@@ -1562,10 +1568,27 @@ struct VictimEmit {
     {
         if (!c) return;
         const uint32_t nf = fresh_taken(lru.ps, ctr, n_slots);
-        const uint32_t need = ctr[C_NMISS] - nf;
-        const uint32_t slot = lru.cur()[i];
-        if (pre < need) victim[nf + pre] = slot;
-        else lru.next()[pre - need] = slot;
+        if (pre < ctr[C_NMISS] - nf) victim[nf + pre] = lru.cur()[i];
+    }
+};
+
+// After the assignment (which marks the victims and the fresh slots it
+// hands out): the used slots still untouched, in LRU order, start the next
+// pass's list (the victims were the first untouched ones before it, so the
+// rest keep their order).  Off the decode's path.
+struct KeepCount {
+    LruPair lru;
+    const uint8_t *touched;
+    const uint32_t *skip;
+    __device__ bool enabled() const { return !*skip; }
+    __device__ uint32_t operator()(int64_t i) const { return touched[lru.cur()[i]] ? 0u : 1u; }
+};
+
+struct KeepEmit {
+    LruPair lru;
+    __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
+    {
+        if (c) lru.next()[pre] = lru.cur()[i];
     }
 };
 
@@ -1616,7 +1639,7 @@ struct TouchedEmit {
     __device__ void operator()(int64_t s, uint32_t pre, uint32_t c) const
     {
         if (!c) return;
-        lru.next()[ctr[C_NUNTOUCHED] - ctr[C_NEEDUSED] + pre] = (uint32_t)s;
+        lru.next()[ctr[C_NUNTOUCHED] + pre] = (uint32_t)s;
         touched[s] = 0;
     }
 };
@@ -3172,8 +3195,8 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
                                     ctr + C_OVERFLOW},
                         SelectEmit{r->iact.as<uint32_t>(), r->miss.as<uint32_t>()}, ctr + C_NMISS, sa));
     SPR_TRY(run_compact(r->scan_status[1], r->scan_ticket[1], flags, r->n_slots, &ps->n_used,
-                        VictimCount{lp, r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
-                        VictimEmit{lp, ctr, r->victim.as<uint32_t>(), (uint32_t)r->n_slots}, ctr + C_NUNTOUCHED, sa));
+                        VictimCount{lp, r->touched.as<uint8_t>(), ctr, (uint32_t)r->n_slots},
+                        VictimEmit{lp, ctr, r->victim.as<uint32_t>(), (uint32_t)r->n_slots}, nullptr, sa));
     assign_kernel<<<grid_for(r->cap_act, 256, 4), 256, 0, sa>>>(r->miss.as<uint32_t>(), r->victim.as<uint32_t>(),
                                                                r->blk_slot.as<uint32_t>(), r->slot_blk.as<uint32_t>(),
                                                                r->touched.as<uint8_t>(), ctr, ps, (uint32_t)r->n_slots);
@@ -3183,6 +3206,9 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
         SPR_CUDA_TRY(cudaEventRecord(ev_assign, sa));
         SPR_CUDA_TRY(cudaStreamWaitEvent(sl, ev_assign, 0));
     }
+    SPR_TRY(run_compact(r->scan_status[2], r->scan_ticket[2], flags, r->n_slots, &ps->n_used,
+                        KeepCount{lp, r->touched.as<uint8_t>(), ctr + C_OVERFLOW}, KeepEmit{lp}, ctr + C_NUNTOUCHED,
+                        sl));
     SPR_TRY(run_compact(r->scan_status[2], r->scan_ticket[2], flags, r->n_slots, &ps->fresh_hi,
                         TouchedCount{r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
                         TouchedEmit{r->touched.as<uint8_t>(), ctr, lp}, nullptr, sl));
