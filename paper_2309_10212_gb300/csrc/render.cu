@@ -1403,11 +1403,13 @@ __global__ void __launch_bounds__(kBitsThreads) bits_reduce_kernel(const uint32_
 }
 
 // total (and *over = total > over_limit, when over is given) from the last
-// tile's last thread
+// tile's last thread; with clear, each word is zeroed once its bits are
+// emitted (the bitmap is then all zero, as a memset would leave it)
 template <class EmitF>
-__global__ void __launch_bounds__(kBitsThreads) bits_emit_kernel(const uint32_t *__restrict__ bits, int64_t n,
+__global__ void __launch_bounds__(kBitsThreads) bits_emit_kernel(uint32_t *__restrict__ bits, int64_t n,
                                                                  const uint32_t *__restrict__ tile_sum, EmitF emit,
-                                                                 uint32_t *total, uint32_t *over, uint32_t over_limit)
+                                                                 uint32_t *total, uint32_t *over, uint32_t over_limit,
+                                                                 bool clear)
 {
     __shared__ uint32_t s_w[kBitsThreads / 32];
     __shared__ uint32_t s_pre;
@@ -1458,6 +1460,11 @@ __global__ void __launch_bounds__(kBitsThreads) bits_emit_kernel(const uint32_t 
     for (int j = 0; j < kBitsWords; ++j) {
         if (first + j < n) emit(first + j, run, c[j]);
         run += c[j];
+    }
+    if (clear) {
+#pragma unroll
+        for (int j = 0; j < kBitsWords; ++j)
+            if (w[j]) bits[first + j] = 0u;
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kBitsThreads - 1) {
         if (total) *total = run;
@@ -2658,12 +2665,13 @@ int run_compact(DevBuf &status, DevBuf &ticket, uint32_t *flags, int64_t n_cap, 
 // compaction of a block bitmap of nwords words (two kernels); tsum holds
 // bits_tiles(nwords) counts
 template <class EF>
-int run_bits_compact(const uint32_t *bits, int64_t nwords, uint32_t *tsum, EF ef, uint32_t *total, cudaStream_t s,
-                     uint32_t *over = nullptr, uint32_t over_limit = 0)
+int run_bits_compact(uint32_t *bits, int64_t nwords, uint32_t *tsum, EF ef, uint32_t *total, cudaStream_t s,
+                     uint32_t *over = nullptr, uint32_t over_limit = 0, bool clear = false)
 {
     const int64_t tiles = bits_tiles(nwords);
     bits_reduce_kernel<<<(unsigned)tiles, kBitsThreads, 0, s>>>(bits, nwords, tsum);
-    bits_emit_kernel<EF><<<(unsigned)tiles, kBitsThreads, 0, s>>>(bits, nwords, tsum, ef, total, over, over_limit);
+    bits_emit_kernel<EF><<<(unsigned)tiles, kBitsThreads, 0, s>>>(bits, nwords, tsum, ef, total, over, over_limit,
+                                                                  clear);
     count_launch(2);
     SPR_CUDA_TRY(cudaGetLastError());
     return SPR_OK;
@@ -3161,12 +3169,12 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     }
 
     // (b) compact the marks; group the entries by visible block.  The active
-    // scan (cache branch) decides whether the pass overflows the cache.
+    // scan (cache branch) decides whether the pass overflows the cache and
+    // leaves the active bitmap zero for the next attempt.
     uint32_t *tsum = r->bits_tsum.as<uint32_t>();
     SPR_TRY(run_bits_compact(r->act_bits.as<uint32_t>(), r->nwords, tsum,
                              BitsEmit{r->act_bits.as<uint32_t>(), nullptr, r->iact.as<uint32_t>(), nullptr},
-                             ctr + C_NACT, sa, ctr + C_OVERFLOW, (uint32_t)r->n_slots));
-    SPR_CUDA_TRY(cudaMemsetAsync(r->act_bits.p, 0, sizeof(uint32_t) * r->nwords, sa));
+                             ctr + C_NACT, sa, ctr + C_OVERFLOW, (uint32_t)r->n_slots, true));
     if (fork) SPR_CUDA_TRY(cudaEventRecord(ev_act, sa));
     SPR_TRY(run_bits_compact(r->vis_bits.as<uint32_t>(), r->nwords, tsum + bits_tiles(r->nwords),
                              BitsEmit{r->vis_bits.as<uint32_t>(), r->vis_wpre.as<uint32_t>(), r->ivis.as<uint32_t>(),
