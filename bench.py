@@ -58,6 +58,17 @@ def decode_bytes_per_block(rate):
     return 8 * rate + 256
 
 
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
+# the same build of that kernel on the same workload: (kernel, dims, rate) ->
+# (bytes, source).  Empty a line when the kernel changes.
+MEASURED_TRAFFIC = {
+    ("decode_list_kernel", (2048, 2048, 1920), 2): (
+        102_950_000,
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the render's two launches "
+        "(506,502 and 500,324 blocks: 104.1 and 101.8 MB); "
+        "profiles/decode_list_kernel_paper_2048x2048x1920.md"),
+}
+
 WORKLOADS = {
     "medium": dict(field="blobs", dims=(512, 512, 512), rate=2, iso=0.3, W=1280, H=720, poses=16,
                    cache_bytes=int(0.10 * 512 ** 3 * 4), spec="adaptive", k=16,
@@ -1063,6 +1074,10 @@ def measure_workload(wl, args, spr, _lib, torch, stream, rank, world, dist, loca
         "work": d["units"] + " (per-pass counters of the instrumented renders)",
         "share": round(stage[dom] / total_stage, 3),
         "timing": "CUDA-event time of the kernel's stage, %d instrumented renders of the same poses" % n_prof_r}
+    tr = MEASURED_TRAFFIC.get((d["kernel"], tuple(wl["dims"]), wl["rate"]))
+    if tr:
+        res["roofline"]["traffic"] = tr[0]
+        res["roofline"]["traffic_source"] = tr[1]
     res["stage_roofline"] = {k: {kk: v[kk] for kk in ("kernel", "achieved", "frac", "units")} | {
         "ms_per_image": round(v["ms"] / n_prof_r, 4)} for k, v in rl.items()}
     res["stage_ms_per_image"] = {k: round(v / n_prof_r, 4) for k, v in stage.items()}
