@@ -1363,19 +1363,20 @@ __device__ __forceinline__ uint32_t vis_rank(const uint32_t *bits, const uint32_
 // bits_emit_kernel adds the counts of the tiles before its own (a few
 // thousand at most, read from L2), scans its words and emits their bits in
 // order.  Same outputs as a compact_kernel over the words' popcounts.
-constexpr int kBitsThreads = 256, kBitsWords = 8;
+constexpr int kBitsThreads = 256, kBitsWords = 8;   // a multiple of 4
 constexpr int64_t kBitsTile = (int64_t)kBitsThreads * kBitsWords;   // words per tile
 
 inline int64_t bits_tiles(int64_t nwords) { return std::max<int64_t>(1, (nwords + kBitsTile - 1) / kBitsTile); }
 
-// this thread's 8 words (two 16-byte loads when all lie below n)
-__device__ __forceinline__ void load_words8(const uint32_t *bits, int64_t first, int64_t n, uint32_t w[kBitsWords])
+// this thread's kBitsWords words (16-byte loads when all lie below n)
+__device__ __forceinline__ void load_words(const uint32_t *bits, int64_t first, int64_t n, uint32_t w[kBitsWords])
 {
     if (first + kBitsWords <= n) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(bits + first);
-        const uint4 b = *reinterpret_cast<const uint4 *>(bits + first + 4);
-        w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w;
-        w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
+#pragma unroll
+        for (int q = 0; q < kBitsWords / 4; ++q) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(bits + first + 4 * q);
+            w[4 * q] = a.x, w[4 * q + 1] = a.y, w[4 * q + 2] = a.z, w[4 * q + 3] = a.w;
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < kBitsWords; ++j) w[j] = first + j < n ? bits[first + j] : 0u;
@@ -1387,7 +1388,7 @@ __global__ void __launch_bounds__(kBitsThreads) bits_reduce_kernel(const uint32_
 {
     __shared__ uint32_t s_w[kBitsThreads / 32];
     uint32_t w[kBitsWords];
-    load_words8(bits, (int64_t)blockIdx.x * kBitsTile + (int64_t)threadIdx.x * kBitsWords, n, w);
+    load_words(bits, (int64_t)blockIdx.x * kBitsTile + (int64_t)threadIdx.x * kBitsWords, n, w);
     uint32_t c = 0;
 #pragma unroll
     for (int j = 0; j < kBitsWords; ++j) c += __popc(w[j]);
@@ -1430,7 +1431,7 @@ __global__ void __launch_bounds__(kBitsThreads) bits_emit_kernel(uint32_t *__res
     // this thread's words and their exclusive prefix within the tile
     const int64_t first = (int64_t)blockIdx.x * kBitsTile + (int64_t)threadIdx.x * kBitsWords;
     uint32_t w[kBitsWords], c[kBitsWords], local = 0;
-    load_words8(bits, first, n, w);
+    load_words(bits, first, n, w);
 #pragma unroll
     for (int j = 0; j < kBitsWords; ++j) {
         c[j] = __popc(w[j]);
