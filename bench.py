@@ -64,9 +64,8 @@ def decode_bytes_per_block(rate):
 MEASURED_TRAFFIC = {
     ("decode_list_kernel", (2048, 2048, 1920), 2): (
         102_950_000,
-        "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the render's two launches "
-        "(506,502 and 500,324 blocks: 104.1 and 101.8 MB); "
-        "profiles/decode_list_kernel_paper_2048x2048x1920.md"),
+        "one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum: mean of the render's "
+        "two launches (506,502 and 500,324 blocks: 104.1 and 101.8 MB)"),
 }
 
 WORKLOADS = {
