@@ -343,6 +343,41 @@ def run_reference(args, wl):
     return 0
 
 
+def run_oracle_passes(args, wl):
+    """The oracle's progressive replay on the host cores (the CPU counterpart
+    of the renderer's pass structure): the plain raycaster over every pixel
+    with each ray's visible-block list, then the pass simulator (speculation
+    rule, LRU cache, overflow rule) from a cold cache, on pose 0.  Prints its
+    times and the passes and decodes it counts."""
+    import time
+
+    import oracle
+    oracle.build()
+    nthreads = os.cpu_count() or 1
+    _, comp = compress_volume(wl, library=False, oracle_side=True)
+    cam = pose(wl, 0)
+    W, H, dims = wl["W"], wl["H"], wl["dims"]
+    ov = oracle.Volume.on_demand(comp, dims, wl["rate"], lazy_fine=True)
+    t0 = time.perf_counter()
+    pix, off, vis = oracle.render(ov, cam, W, H, wl["iso"], lists=True)
+    t1 = time.perf_counter()
+    if wl["spec"] == "fixed":
+        spec = dict(spec_mode=oracle.SPEC_FIXED, k=wl["k"])
+    else:
+        spec = dict(spec_mode=oracle.SPEC_ADAPTIVE, k_max=wl["k"])
+    st, _ = oracle.simulate(W, H, dims, pix, off, vis, n_slots=wl["cache_bytes"] // 256, **spec)
+    t2 = time.perf_counter()
+    print(json.dumps({
+        "impl": "oracle_passes", "workload": wl["name"], "cores": nthreads,
+        "render_with_lists_ms": round(1e3 * (t1 - t0), 1), "simulate_ms": round(1e3 * (t2 - t1), 1),
+        "total_ms": round(1e3 * (t2 - t0), 1), "passes": int(len(st["n_active"])),
+        "blocks_decoded": int(st["n_decoded"].sum()), "entries": int(st["n_entries"].sum()),
+        "block_decodes_in_render": int(ov.last_decodes),
+        "note": "C oracle, FP64, blocks decoded on demand (lazy fine ranges); the simulator replays "
+                "the speculation rule, the LRU cache and the overflow rule on the rays' lists"}))
+    return 0
+
+
 def run_study(args, wl):
     """Speculation sweep (fixed k = 1..16, adaptive caps 16 and 64), resolution
     scaling (640x360, 1280x720, 1920x1080) and blocks decoded against the
@@ -1212,6 +1247,8 @@ def main():
     ap.add_argument("--learn-mod", type=int, default=16)
     ap.add_argument("--learn-samples", type=int, default=24 << 20)
     ap.add_argument("--learn-epochs", type=int, default=8)
+    ap.add_argument("--oracle-passes", action="store_true",
+                    help="time the oracle's raycaster with visible lists and its pass simulator (host cores)")
     ap.add_argument("--decode-slab", action="store_true",
                     help="instead of the bench line: the decode rate of the paper-scale field's "
                          "interface blocks (one JSON line)")
@@ -1250,6 +1287,8 @@ def main():
         wl["name"] = wl["name"].rsplit("k<=", 1)[0] + f"k<={args.k_max}" if "k<=" in wl["name"] else wl["name"]
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.oracle_passes:
+        return run_oracle_passes(args, wl)
     if args.study:
         return run_study(args, wl)
     if args.serve:
