@@ -49,3 +49,14 @@ def test_reference_arm_other_ranks_are_silent():
     lines = run(["--impl", "reference", "--workload", "small", "--steps", "1", "--warmup", "0"],
                 {"RANK": "1", "WORLD_SIZE": "2"})
     assert lines == []
+
+
+def test_oracle_passes_line():
+    """--oracle-passes times the oracle's raycaster with visible lists and its
+    pass simulator; the counts it prints are the simulator's own."""
+    lines = run(["--oracle-passes", "--workload", "small"])
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "oracle_passes" and d["cores"] >= 1
+    assert d["render_with_lists_ms"] > 0 and d["simulate_ms"] >= 0
+    assert d["passes"] >= 1 and d["blocks_decoded"] > 0 and d["entries"] > 0
