@@ -62,10 +62,6 @@ def decode_bytes_per_block(rate):
 # the same build of that kernel on the same workload: (kernel, dims, rate) ->
 # (bytes, source).  Empty a line when the kernel changes.
 MEASURED_TRAFFIC = {
-    ("decode_list_kernel", (2048, 2048, 1920), 2): (
-        102_950_000,
-        "one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum: mean of the render's "
-        "two launches (506,502 and 500,324 blocks: 104.1 and 101.8 MB)"),
 }
 
 WORKLOADS = {
@@ -919,9 +915,11 @@ def run_serve(args):
 def run_decode_slab(args):
     """Decode rate of the blocks the paper-scale render decodes: a slab of the
     2048x2048x1920 mixing layer at its interface (z = 928..959, 2 bits/value,
-    2,097,152 blocks), every block decoded in one spr_decode_blocks call,
-    timed with CUDA events (median of --steps calls, L2 written between
-    them).  Prints one JSON line."""
+    2,097,152 blocks), every block decoded in one call, timed with CUDA events
+    (median of --steps calls, L2 written between them): the plain decoder
+    (spr_decode_blocks, consecutive blocks per warp) and the renderer's
+    decoder (spr_volume_decode_blocks, blocks grouped by parse length).
+    Prints one JSON line."""
     import torch
 
     from paper_2309_10212_gb300 import build
@@ -934,26 +932,37 @@ def run_decode_slab(args):
     comp = spr.spr_encode_u8(u8, rate)
     del u8
     nb = comp.numel() // (8 * rate)
+    vol = spr.spr_create_volume((dims[0], dims[1], z1 - z0), rate, comp)
     out = torch.empty((nb, 64), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ts = []
-    for i in range(args.warmup + args.steps):
-        flush.fill_(i & 255)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        spr.spr_decode_blocks(comp, nb, rate, out=out)
-        b.record()
-        torch.cuda.synchronize()
-        if i >= args.warmup:
-            ts.append(a.elapsed_time(b))
-    ms = statistics.median(ts)
+
+    def timed(call):
+        ts = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(i & 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            call()
+            b.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
     pk = peaks()
-    gbs = nb * (8 * rate + 256) / (ms / 1e3) / 1e9
+    res = {}
+    for name, call in (("plain", lambda: spr.spr_decode_blocks(comp, nb, rate, out=out)),
+                       ("grouped", lambda: spr.spr_volume_decode_blocks(vol, out=out))):
+        ms = timed(call)
+        gbs = nb * (8 * rate + 256) / (ms / 1e3) / 1e9
+        res[name] = {"ms": round(ms, 4), "gblocks_per_s": round(nb / ms / 1e6, 3), "achieved_gbs": round(gbs, 1),
+                     "frac": round(gbs / pk["hbm_gbs"], 4)}
     print(json.dumps({"decode_slab": "mixing layer 2048x2048x1920, z %d..%d, %d bits/value" % (z0, z1 - 1, rate),
-                      "kernel": "decode_list_kernel", "blocks": nb, "ms": round(ms, 4),
-                      "gblocks_per_s": round(nb / ms / 1e6, 3), "achieved_gbs": round(gbs, 1),
-                      "peak_gbs": pk["hbm_gbs"], "frac": round(gbs / pk["hbm_gbs"], 4),
-                      "timing": "median of %d CUDA-event timed calls, L2 written before each" % len(ts)}))
+                      "blocks": nb, "peak_gbs": pk["hbm_gbs"],
+                      "plain": dict(res["plain"], kernel="decode_list_kernel", call="spr_decode_blocks"),
+                      "grouped": dict(res["grouped"], kernel="decode_sorted_kernel",
+                                      call="spr_volume_decode_blocks"),
+                      "timing": "median of %d CUDA-event timed calls, L2 written before each" % args.steps}))
     return 0
 
 
@@ -972,7 +981,7 @@ def stage_rooflines(prof_stats, stage, rate, pk):
             ("traverse", "traverse_kernel / traverse_seg_kernel", trav,
              "live rays x %d B + speculated slots x %d B + walk steps x %d B" %
              (TRAV_BYTES_PER_RAY, TRAV_BYTES_PER_SLOT, TRAV_BYTES_PER_STEP)),
-            ("decode", "decode_list_kernel", dec, "decoded blocks x %d B" % decode_bytes_per_block(rate)),
+            ("decode", "decode_sorted_kernel", dec, "decoded blocks x %d B" % decode_bytes_per_block(rate)),
             ("intersect", "intersect_kernel", isect,
              "visible blocks x %d B + entries x %d B" % (ISECT_BYTES_PER_VISIBLE, ISECT_BYTES_PER_ENTRY))):
         ms = stage[name]

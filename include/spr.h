@@ -114,6 +114,17 @@ int spr_encode_u8(const uint8_t *vol, const int32_t dims[3], int rate, uint8_t *
 int spr_decode_blocks(const uint8_t *blocks, int64_t n_blocks, int rate, const uint32_t *ids,
                       int64_t n, float *out, spr_stream stream);
 
+/* Decompress n blocks of a volume into out (device, n*64 floats, as
+ * spr_decode_blocks), the way the renderer decodes its cache misses (Sec.
+ * 3.5): the entries are grouped by the number of bit planes their parse
+ * reads (recorded by spr_create_volume) so that a warp's lanes parse alike.
+ * The values are identical to spr_decode_blocks'.  ids (device, n entries)
+ * selects the blocks, ids == NULL means blocks 0..n-1; an id beyond the
+ * volume's block count is SPR_ERR_INVALID_ARG.  n == 0 does nothing (out
+ * may then be NULL).  Synchronises `stream`. */
+int spr_volume_decode_blocks(const spr_volume *vol, const uint32_t *ids, int64_t n, float *out,
+                             spr_stream stream);
+
 /* ----------------------------------------------------------------- volume */
 typedef struct {
     int32_t dims[3];        /* voxels per axis, each in [2, 4096]              */
@@ -126,7 +137,10 @@ typedef struct {
  * blocks_on_device, else in host memory.  The library copies them, decodes
  * every block once to get its value range, and builds the fine (per block)
  * and coarse (per 4^3 blocks) macrocell grids, each range combined with the
- * +x/+y/+z neighbours' (Sec. 3.1).  Ordered on `stream`; returns after the
+ * +x/+y/+z neighbours' (Sec. 3.1).  The same pass records, one byte per
+ * block, how many bit planes the block's parse reads; the renderer's decoder
+ * groups its cache misses by that count (no counterpart in the paper; the
+ * decoded values do not depend on it).  Ordered on `stream`; returns after the
  * work is enqueued.  *out is owned by the caller (spr_destroy_volume). */
 int spr_create_volume(const spr_volume_desc *desc, const void *blocks, size_t nbytes,
                       int blocks_on_device, spr_stream stream, spr_volume **out);

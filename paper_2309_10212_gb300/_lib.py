@@ -140,6 +140,7 @@ PROTOTYPES = {
     "spr_encode_f32": ([_vp, _vp, _i32, _vp, _vp], _i32),
     "spr_encode_u8": ([_vp, _vp, _i32, _vp, _vp], _i32),
     "spr_decode_blocks": ([_vp, _i64, _i32, _vp, _i64, _vp, _vp], _i32),
+    "spr_volume_decode_blocks": ([_vp, _vp, _i64, _vp, _vp], _i32),
     "spr_create_volume": ([_vp, _vp, _sz, _i32, _vp, _vp], _i32),
     "spr_destroy_volume": ([_vp], _i32),
     "spr_volume_ranges": ([_vp, _vp, _vp, _vp], _i32),

@@ -168,6 +168,24 @@ def spr_create_volume(dims, rate: int, blocks, stream=None) -> Volume:
     return Volume(h, dims, rate)
 
 
+def spr_volume_decode_blocks(vol: Volume, ids=None, n=None, out=None, stream=None):
+    """Decompress blocks of a volume (all of them, or the CUDA uint32 `ids`)
+    into a CUDA float32 tensor of shape (n, 64), grouped by parse length the
+    way the renderer decodes its cache misses; the values equal
+    spr_decode_blocks'."""
+    torch = _torch()
+    total = vol.nblocks
+    total = total[0] * total[1] * total[2] if isinstance(total, tuple) else int(total)
+    if n is None:
+        n = total if ids is None else ids.numel()
+    if out is None:
+        out = torch.empty((n, 64), dtype=torch.float32, device="cuda" if ids is None else ids.device)
+    idp = None if ids is None else _dev_ptr(ids, torch.int32)
+    check(load().spr_volume_decode_blocks(vol.handle, idp, int(n), _dev_ptr(out, torch.float32),
+                                          _stream(stream)))
+    return out
+
+
 def spr_destroy_volume(vol: Volume):
     if vol.handle:
         check(load().spr_destroy_volume(vol.handle))

@@ -34,18 +34,22 @@ VolGeom make_geom(const int32_t dims[3], int rate)
 }
 
 // ---------------------------------------------------------------- kernels
-// raw range of each block: min/max of its decoded in-domain voxels
+// raw range of each block: min/max of its decoded in-domain voxels; and the
+// number of bit planes its parse reads
 __global__ void __launch_bounds__(kDecThreads) range_kernel(const uint8_t *__restrict__ comp,
-                                                            VolGeom g, float2 *__restrict__ raw)
+                                                            VolGeom g, float2 *__restrict__ raw,
+                                                            uint8_t *__restrict__ planes)
 {
     __shared__ uint32_t col_s[64 * kColStride];
     uint32_t *col = col_s + threadIdx.x;
     const int64_t bytes = 8 * (int64_t)g.rate;
     for (int64_t b = (int64_t)blockIdx.x * kDecThreads + threadIdx.x; b < g.nblocks;
          b += (int64_t)gridDim.x * kDecThreads) {
-        int emax = 0;
+        int emax = 0, np = 0;
         float mn = 0.0f, mx = 0.0f;
-        if (frc4::decode_block_coeffs(comp + b * bytes, g.rate, col, kColStride, &emax)) {
+        const bool nz = frc4::decode_block_coeffs(comp + b * bytes, g.rate, col, kColStride, &emax, &np);
+        planes[b] = (uint8_t)np;
+        if (nz) {
             int64_t bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / ((int64_t)g.nb[0] * g.nb[1]);
             int ex = min(4, (int)(g.dims[0] - 4 * bx));
             int ey = min(4, (int)(g.dims[1] - 4 * by));
@@ -219,6 +223,142 @@ __global__ void __launch_bounds__(kDecThreads, 6) decode_list_kernel(
     }
 }
 
+// decode_list_kernel for lists whose blocks' parse lengths are known (the
+// volume's plane counts).  A warp's lanes run the bit-plane loop together, so
+// a warp costs about the plane loop of its longest block: lanes whose blocks
+// stop after few planes wait for those that parse all 30.  Each CTA step
+// therefore takes kSortChunk list entries, counting-sorts them in shared
+// memory by their blocks' plane counts, and gives each warp 32 consecutive
+// entries of that order.  Each entry still goes to its own destination slot,
+// so the output is the same as decode_list_kernel's.  CTAs of 256 threads,
+// one entry per thread and step (the rows in dynamic shared memory, 68 KB),
+// so that a list fills the GPU with as many threads as decode_list_kernel's.
+constexpr int kSortThreads = 256;
+constexpr int kSortChunk = kSortThreads;
+constexpr size_t kSortRowBytes = sizeof(uint32_t) * kSortThreads * kRowStride;
+constexpr uint32_t kNoKey = 31;   // plane counts are 0..30
+
+__device__ __forceinline__ void decode_into_row(const uint8_t *__restrict__ comp, int64_t nblocks, int rate,
+                                                int64_t id, const frc4::RegBits &bits, uint32_t *row,
+                                                unsigned int *bad)
+{
+    int emax = 0;
+    bool nz = false;
+    if (id < nblocks) {   // the parse zeroes the row before it sets bits
+        nz = rate <= 2 ? frc4::decode_coeffs(bits, rate, row, 1, &emax)
+                       : frc4::decode_block_coeffs(comp + id * 8 * (int64_t)rate, rate, row, 1, &emax);
+    } else {
+        atomicOr(bad, 1u);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) reinterpret_cast<uint4 *>(row)[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (nz) {
+        float v[64];
+        frc4::reconstruct_row(row, emax, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            reinterpret_cast<uint4 *>(row)[q] =
+                make_uint4(__float_as_uint(v[4 * q]), __float_as_uint(v[4 * q + 1]), __float_as_uint(v[4 * q + 2]),
+                           __float_as_uint(v[4 * q + 3]));
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads, 3) decode_sorted_kernel(
+    const uint8_t *__restrict__ comp, int64_t nblocks, int rate, const uint8_t *__restrict__ planes,
+    const uint32_t *__restrict__ ids, const uint32_t *__restrict__ dst_ids, int64_t n_host, const uint32_t *n_dev,
+    const uint32_t *skip, float *__restrict__ out, unsigned int *bad)
+{
+    extern __shared__ __align__(16) uint32_t rows_s[];   // kSortThreads rows of kRowStride words
+    __shared__ uint16_t s_perm[kSortChunk];
+    __shared__ uint32_t s_off[32];
+    if (skip && *skip) return;
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    uint32_t *row = rows_s + threadIdx.x * kRowStride;
+    const uint32_t *wrows = rows_s + wid * 32 * kRowStride;
+    const int64_t bytes = 8 * (int64_t)rate;
+    constexpr int kRounds = kSortChunk / kSortThreads;
+    for (int64_t c0 = (int64_t)blockIdx.x * kSortChunk; c0 < n; c0 += (int64_t)gridDim.x * kSortChunk) {
+        const int m = n - c0 < kSortChunk ? (int)(n - c0) : kSortChunk;
+        if (threadIdx.x < 32) s_off[threadIdx.x] = 0u;
+        __syncthreads();   // the previous step's reads of s_perm and s_off are done
+        // each entry's key: its block's plane count; per-key counts
+        uint32_t key[kRounds];
+#pragma unroll
+        for (int j = 0; j < kRounds; ++j) {
+            const int l = j * kSortThreads + threadIdx.x;
+            key[j] = kNoKey;
+            if (l < m) {
+                const int64_t id = ids ? (int64_t)ids[c0 + l] : c0 + l;
+                key[j] = id < nblocks ? (uint32_t)planes[id] : 0u;
+            }
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, key[j]);
+            if (key[j] != kNoKey && (peers & below) == 0) atomicAdd(&s_off[key[j]], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        if (wid == 0) {   // exclusive offsets of the keys
+            const uint32_t v = s_off[lane];
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            s_off[lane] = incl - v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kRounds; ++j) {
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, key[j]);
+            const int leader = __ffs(peers) - 1;
+            uint32_t at = 0;
+            if (key[j] != kNoKey && lane == leader) at = atomicAdd(&s_off[key[j]], (uint32_t)__popc(peers));
+            at = __shfl_sync(0xFFFFFFFFu, at, leader);
+            if (key[j] != kNoKey) s_perm[at + __popc(peers & below)] = (uint16_t)(j * kSortThreads + threadIdx.x);
+        }
+        __syncthreads();
+        // warp wid takes sorted positions r * kSortThreads + 32 * wid + lane;
+        // every round's bitstream is loaded before the first parse
+        int64_t id[kRounds];
+        uint32_t slot[kRounds];
+        frc4::RegBits cur[kRounds];
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const int q = r * kSortThreads + wid * 32 + lane;
+            id[r] = -1;
+            slot[r] = 0u;
+            cur[r] = frc4::RegBits{0ull, 0ull};
+            if (q < m) {
+                const int64_t i = c0 + s_perm[q];
+                id[r] = ids ? (int64_t)ids[i] : i;
+                slot[r] = dst_ids ? dst_ids[i] : (uint32_t)i;
+                if (rate <= 2 && id[r] < nblocks) cur[r] = frc4::load_reg_bits(comp + id[r] * bytes, rate);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const int q0 = r * kSortThreads + wid * 32;
+            if (q0 >= m) break;   // the same for the whole warp
+            if (q0 + lane < m) decode_into_row(comp, nblocks, rate, id[r], cur[r], row, bad);
+            __syncwarp();
+            // blocks t and t + 1 of the warp per step: lanes 0-15 and 16-31
+            // each move one 16-byte quarter-row
+            const int cnt = m - q0 < 32 ? m - q0 : 32;
+            const int half = lane >> 4, qq = lane & 15;
+            for (int t = 0; t < cnt; t += 2) {
+                const int blk = t + half;
+                const uint32_t sl = __shfl_sync(0xFFFFFFFFu, slot[r], blk & 31);
+                if (blk < cnt) {
+                    const uint4 w = reinterpret_cast<const uint4 *>(wrows + blk * kRowStride)[qq];
+                    reinterpret_cast<uint4 *>(out + (int64_t)sl * 64)[qq] = w;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 int grid_for(int64_t n, int threads, int per_sm)
 {
     int64_t g = (n + threads - 1) / threads;
@@ -259,11 +399,44 @@ static int encode_impl(const T *vol, const int32_t dims[3], int rate, uint8_t *o
     return SPR_OK;
 }
 
+// The sorted decoder's dynamic shared memory (above the 48 KB default) and
+// its CTAs per SM.  spr_create_volume calls this on the creating device, so
+// that it has run before any render is captured into a graph.
+static int g_sorted_per_sm = 0;
+static int prepare_decode_sorted()
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        SPR_CUDA_TRY(cudaFuncSetAttribute(decode_sorted_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kSortRowBytes));
+        attr_set = true;
+    }
+    if (g_sorted_per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decode_sorted_kernel, kSortThreads, kSortRowBytes) !=
+                cudaSuccess ||
+            nb < 1)
+            nb = 1;
+        g_sorted_per_sm = nb * 8;
+    }
+    return SPR_OK;
+}
+
 int launch_decode_list(const uint8_t *comp, int64_t nblocks, int rate, const uint32_t *ids,
                        const uint32_t *dst, int64_t n_host, const uint32_t *n_dev,
-                       const uint32_t *skip, float *out, unsigned int *bad, cudaStream_t s)
+                       const uint32_t *skip, float *out, unsigned int *bad, cudaStream_t s,
+                       const uint8_t *planes)
 {
     if (n_host <= 0) return SPR_OK;
+    if (planes) {
+        // one sorted step of kSortChunk entries per CTA, up to 8 waves of
+        // the CTAs resident at once
+        SPR_TRY(prepare_decode_sorted());
+        decode_sorted_kernel<<<grid_for(n_host, kSortChunk, g_sorted_per_sm), kSortThreads, kSortRowBytes, s>>>(
+            comp, nblocks, rate, planes, ids, dst, n_host, n_dev, skip, out, bad);
+        SPR_CUDA_TRY(cudaGetLastError());
+        return SPR_OK;
+    }
     // kDecWaves waves of the CTAs resident at once (shared memory bound), so
     // that an SM whose CTAs finish early takes new ones: in a render the
     // decode runs beside the grouping branch, whose kernels hold SMs when it
@@ -326,6 +499,33 @@ extern "C" int spr_decode_blocks(const uint8_t *blocks, int64_t n_blocks, int ra
     return rc;
 }
 
+extern "C" int spr_volume_decode_blocks(const spr_volume *v, const uint32_t *ids, int64_t n, float *out,
+                                        spr_stream stream)
+{
+    clear_error();
+    if (!v || n < 0 || (n > 0 && !out)) return set_error(SPR_ERR_INVALID_ARG, "bad decode arguments");
+    if (!ids && n > v->g.nblocks) return set_error(SPR_ERR_INVALID_ARG, "n exceeds the block count");
+    if (n == 0) return SPR_OK;
+    cudaStream_t s = as_stream(stream);
+    DevBuf flag;
+    SPR_TRY(buf_alloc(flag, sizeof(unsigned int), s));
+    int rc = SPR_OK;
+    cudaError_t e = cudaMemsetAsync(flag.p, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) rc = set_error(SPR_ERR_CUDA, "decode: %s", cudaGetErrorString(e));
+    if (rc == SPR_OK)
+        rc = launch_decode_list(v->comp.as<uint8_t>(), v->g.nblocks, v->g.rate, ids, nullptr, n, nullptr, nullptr,
+                                out, flag.as<unsigned int>(), s, v->planes.as<uint8_t>());
+    unsigned int bad = 0;
+    if (rc == SPR_OK) {
+        e = cudaMemcpyAsync(&bad, flag.p, sizeof bad, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = set_error(SPR_ERR_CUDA, "decode: %s", cudaGetErrorString(e));
+    }
+    buf_free(flag, s);
+    if (rc == SPR_OK && bad) rc = set_error(SPR_ERR_INVALID_ARG, "a block id is out of range");
+    return rc;
+}
+
 extern "C" int spr_create_volume(const spr_volume_desc *desc, const void *blocks, size_t nbytes,
                                  int blocks_on_device, spr_stream stream, spr_volume **out)
 {
@@ -339,6 +539,9 @@ extern "C" int spr_create_volume(const spr_volume_desc *desc, const void *blocks
     if (nbytes != need)
         return set_error(SPR_ERR_INVALID_ARG, "expected %zu compressed bytes, got %zu", need, nbytes);
     cudaStream_t s = as_stream(stream);
+    SPR_CUDA_TRY(cudaFuncSetAttribute(decode_sorted_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kSortRowBytes));
+    SPR_TRY(prepare_decode_sorted());
     spr_volume *v = new (std::nothrow) spr_volume();
     if (!v) return set_error(SPR_ERR_OUT_OF_MEMORY, "host allocation failed");
     v->g = g;
@@ -350,10 +553,12 @@ extern "C" int spr_create_volume(const spr_volume_desc *desc, const void *blocks
         buf_free(v->comp, s);
         buf_free(v->fine, s);
         buf_free(v->coarse, s);
+        buf_free(v->planes, s);
         delete v;
         return code;
     };
     if ((rc = buf_alloc(v->comp, need, s)) || (rc = buf_alloc(v->fine, sizeof(float2) * g.nblocks, s)) ||
+        (rc = buf_alloc(v->planes, (size_t)g.nblocks, s)) ||
         (rc = buf_alloc(v->coarse, sizeof(float2) * g.ncoarse, s)) ||
         (rc = buf_alloc(raw, sizeof(float2) * g.nblocks, s)) ||
         (rc = buf_alloc(craw, sizeof(float2) * g.ncoarse, s)))
@@ -362,7 +567,8 @@ extern "C" int spr_create_volume(const spr_volume_desc *desc, const void *blocks
                                     blocks_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(set_error(SPR_ERR_CUDA, "copy of blocks: %s", cudaGetErrorString(e)));
     range_kernel<<<grid_for(g.nblocks, kDecThreads, 8), kDecThreads, 0, s>>>(v->comp.as<uint8_t>(), g,
-                                                                           raw.as<float2>());
+                                                                           raw.as<float2>(),
+                                                                           v->planes.as<uint8_t>());
     plus_union_kernel<<<grid_for(g.nblocks, 256, 8), 256, 0, s>>>(raw.as<float2>(), g.nb[0], g.nb[1], g.nb[2],
                                                                  v->fine.as<float2>());
     coarse_raw_kernel<<<grid_for(g.ncoarse, 256, 8), 256, 0, s>>>(raw.as<float2>(), g, craw.as<float2>());
@@ -385,6 +591,7 @@ extern "C" int spr_destroy_volume(spr_volume *v)
     buf_free(v->comp, nullptr);
     buf_free(v->fine, nullptr);
     buf_free(v->coarse, nullptr);
+    buf_free(v->planes, nullptr);
     delete v;
     return SPR_OK;
 }

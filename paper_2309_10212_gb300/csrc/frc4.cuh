@@ -87,10 +87,13 @@ __device__ __forceinline__ void set_bit_of(uint32_t *w, int p, int stride)
 
 // Parse one block.  col[k * stride] receives the negabinary value of the k-th
 // coefficient in sequency order (stride 1: col is 16-byte aligned).  Returns
-// false for an all-zero block.
+// false for an all-zero block.  With nplanes given, *nplanes receives the
+// number of bit planes parsed (0 for an all-zero block): the parse's length,
+// by which the renderer's decoder groups blocks so that a warp's lanes run
+// the plane loop alike.
 template <class Bits>
 __device__ __forceinline__ bool decode_coeffs(const Bits &bits_at, int rate, uint32_t *col, int stride,
-                                              int *emax)
+                                              int *emax, int *nplanes = nullptr)
 {
     if (stride == 1) {   // a row (16-byte aligned): vector stores
 #pragma unroll
@@ -100,11 +103,15 @@ __device__ __forceinline__ bool decode_coeffs(const Bits &bits_at, int rate, uin
         for (int i = 0; i < 64; ++i) col[i * stride] = 0u;
     }
     uint32_t h = bits_at(0, 9);
-    if (!(h & 1u)) return false;
+    if (!(h & 1u)) {
+        if (nplanes) *nplanes = 0;
+        return false;
+    }
     int e = (int)((h >> 1) & 0xFFu) - 127;
     *emax = e < -100 ? -100 : e;
     int pos = 9, budget = 64 * rate - 9, n = 0;
-    for (int p = kPlanes - 1; p >= 0 && budget > 0; --p) {
+    int p = kPlanes - 1;
+    for (; p >= 0 && budget > 0; --p) {
         // refinement bits of the significant prefix
         int m = n < budget ? n : budget;
         for (int base = 0; base < m; base += 32) {
@@ -143,15 +150,17 @@ __device__ __forceinline__ bool decode_coeffs(const Bits &bits_at, int rate, uin
             if (found) set_bit_of(col + (n - 1) * stride, p, stride);
         }
     }
+    if (nplanes) *nplanes = kPlanes - 1 - p;
     return true;
 }
 
 // decode block `blk` (8*rate bytes, 16-byte aligned when rate == 2)
 __device__ __forceinline__ bool decode_block_coeffs(const uint8_t *blk, int rate, uint32_t *col, int stride,
-                                                    int *emax)
+                                                    int *emax, int *nplanes = nullptr)
 {
-    if (rate <= 2) return decode_coeffs(load_reg_bits(blk, rate), rate, col, stride, emax);
-    return decode_coeffs(MemBits{reinterpret_cast<const uint32_t *>(blk), 2 * rate}, rate, col, stride, emax);
+    if (rate <= 2) return decode_coeffs(load_reg_bits(blk, rate), rate, col, stride, emax, nplanes);
+    return decode_coeffs(MemBits{reinterpret_cast<const uint32_t *>(blk), 2 * rate}, rate, col, stride, emax,
+                         nplanes);
 }
 
 // two-level inverse lifting on one 4-vector, wrap-around integer arithmetic

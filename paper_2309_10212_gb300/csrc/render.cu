@@ -3226,7 +3226,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     // (d) decode the misses into their slots
     SPR_TRY(launch_decode_list(r->vol->comp.as<uint8_t>(), g.nblocks, g.rate, r->miss.as<uint32_t>(),
                                r->victim.as<uint32_t>(), r->cap_act, ctr + C_NMISS, ctr + C_OVERFLOW,
-                               r->cache.as<float>(), ctr + C_BAD, sa));
+                               r->cache.as<float>(), ctr + C_BAD, sa, r->vol->planes.as<uint8_t>()));
     count_launch();
     if (events) SPR_CUDA_TRY(record(r->ev[4], s, capturing));
     if (fork) {

@@ -72,6 +72,7 @@ struct spr_volume {
     spr::DevBuf comp;     // nblocks * 8 * rate bytes
     spr::DevBuf fine;     // float2 per block
     spr::DevBuf coarse;   // float2 per coarse cell
+    spr::DevBuf planes;   // uint8 per block: bit planes its parse reads (0: all-zero block)
 };
 
 // ======================================================== device arithmetic

@@ -154,3 +154,57 @@ def test_create_volume_argument_errors(spr):
     assert e.value.status == -1
     with pytest.raises(spr.SprError):
         spr.spr_create_volume((8, 8, 8), 2, torch.zeros(15, dtype=torch.uint8, device="cuda"))
+
+
+@pytest.mark.parametrize("rate", [1, 2, 3, 8, 32])
+def test_volume_decode_grouped_by_parse_length(spr, orc, rate):
+    """spr_volume_decode_blocks (the renderer's decoder: entries grouped by
+    their blocks' plane counts in steps of 256) against the plain decoder and
+    the oracle, bit for bit: all blocks, a shuffled list with repeats and a
+    ragged length, one entry, none, and an id beyond the volume."""
+    import torch
+    dims = (37, 29, 26)
+    vol = synth.volumes.value_noise(dims, seed=rate, ref=40)
+    vol[:12] = 0.0   # all-zero blocks (plane count 0) beside rough ones
+    comp = orc.encode_volume(vol, dims, rate)
+    nb = orc.nblocks(dims)
+    n = nb[0] * nb[1] * nb[2]
+    v = spr.spr_create_volume(dims, rate, _t(comp))
+    full = spr.spr_volume_decode_blocks(v).cpu().numpy()
+    plain = spr.spr_decode_blocks(_t(comp), n, rate).cpu().numpy()
+    assert np.array_equal(full.view(np.uint32), plain.view(np.uint32))
+    bpb = 8 * rate
+    for b in range(0, n, 5):
+        assert np.array_equal(full[b].view(np.uint32), orc.decode_block(comp[b * bpb:(b + 1) * bpb], rate).view(np.uint32)), b
+    rng = np.random.default_rng(rate)
+    ids = rng.integers(0, n, size=3 * 256 + 77).astype(np.int32)
+    got = spr.spr_volume_decode_blocks(v, ids=_t(ids)).cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), plain[ids].view(np.uint32))
+    one = spr.spr_volume_decode_blocks(v, ids=_t(ids[:1])).cpu().numpy()
+    assert np.array_equal(one.view(np.uint32), plain[ids[:1]].view(np.uint32))
+    assert spr.spr_volume_decode_blocks(v, ids=_t(ids[:0])).shape == (0, 64)
+    with pytest.raises(spr.SprError):
+        spr.spr_volume_decode_blocks(v, ids=torch.tensor([3, n], dtype=torch.int32, device="cuda"))
+
+
+def test_volume_decode_mixing_layer_interface(spr, orc):
+    """The renderer's decoder on the blocks that dominate a paper-scale
+    render (the mixing layer's interface, 2 bits/value): a shuffled list of
+    300,001 of its 524,288 blocks equals the plain decoder's output, and a
+    sample equals the oracle's."""
+    dims = (2048, 2048, 1920)
+    u8 = synth.volumes.mixing_layer_slab(dims, 956, 964, synth.volumes.mixing_layer_params(3),
+                                         z_mid=960.0, device="cuda")
+    sdims = (2048, 2048, 8)
+    comp = spr.spr_encode_u8(u8, 2)
+    n = comp.numel() // 16
+    v = spr.spr_create_volume(sdims, 2, comp)
+    rng = np.random.default_rng(11)
+    ids = rng.permutation(n)[:300001].astype(np.int32)
+    got = spr.spr_volume_decode_blocks(v, ids=_t(ids)).cpu().numpy()
+    plain = spr.spr_decode_blocks(comp, n, 2, ids=_t(ids)).cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), plain.view(np.uint32))
+    c = comp.cpu().numpy()
+    for k in range(0, len(ids), 997):
+        b = int(ids[k])
+        assert np.array_equal(got[k].view(np.uint32), orc.decode_block(c[b * 16:(b + 1) * 16], 2).view(np.uint32))
