@@ -269,7 +269,12 @@ __global__ void __launch_bounds__(kSortThreads, 3) decode_sorted_kernel(
     const uint32_t *skip, float *__restrict__ out, unsigned int *bad)
 {
     extern __shared__ __align__(16) uint32_t rows_s[];   // kSortThreads rows of kRowStride words
-    __shared__ uint16_t s_perm[kSortChunk];
+    // the chunk's entries in sorted order: block id, destination slot and
+    // (rate <= 2) the bit stream, loaded before the sort by the thread that
+    // read the entry, so the parse does not wait on a second round of loads
+    __shared__ uint4 s_bits[kSortChunk];
+    __shared__ uint32_t s_id[kSortChunk];
+    __shared__ uint32_t s_slot[kSortChunk];
     __shared__ uint32_t s_off[32];
     if (skip && *skip) return;
     const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
@@ -282,16 +287,31 @@ __global__ void __launch_bounds__(kSortThreads, 3) decode_sorted_kernel(
     for (int64_t c0 = (int64_t)blockIdx.x * kSortChunk; c0 < n; c0 += (int64_t)gridDim.x * kSortChunk) {
         const int m = n - c0 < kSortChunk ? (int)(n - c0) : kSortChunk;
         if (threadIdx.x < 32) s_off[threadIdx.x] = 0u;
-        __syncthreads();   // the previous step's reads of s_perm and s_off are done
-        // each entry's key: its block's plane count; per-key counts
-        uint32_t key[kRounds];
+        __syncthreads();   // the previous step's reads of the shared arrays are done
+        // each entry: its block, slot, stream and key (the block's plane
+        // count); per-key counts
+        uint32_t key[kRounds], eid[kRounds], eslot[kRounds];
+        uint4 ebits[kRounds];
 #pragma unroll
         for (int j = 0; j < kRounds; ++j) {
             const int l = j * kSortThreads + threadIdx.x;
             key[j] = kNoKey;
+            eid[j] = 0u;
+            eslot[j] = 0u;
+            ebits[j] = make_uint4(0u, 0u, 0u, 0u);
             if (l < m) {
-                const int64_t id = ids ? (int64_t)ids[c0 + l] : c0 + l;
-                key[j] = id < nblocks ? (uint32_t)planes[id] : 0u;
+                eid[j] = ids ? ids[c0 + l] : (uint32_t)(c0 + l);
+                eslot[j] = dst_ids ? dst_ids[c0 + l] : (uint32_t)(c0 + l);
+                key[j] = 0u;
+                if ((int64_t)eid[j] < nblocks) {
+                    key[j] = planes[eid[j]];
+                    if (rate == 2)
+                        ebits[j] = __ldg(reinterpret_cast<const uint4 *>(comp + (int64_t)eid[j] * bytes));
+                    else if (rate == 1) {
+                        const uint2 h = __ldg(reinterpret_cast<const uint2 *>(comp + (int64_t)eid[j] * bytes));
+                        ebits[j] = make_uint4(h.x, h.y, 0u, 0u);
+                    }
+                }
             }
             const unsigned peers = __match_any_sync(0xFFFFFFFFu, key[j]);
             if (key[j] != kNoKey && (peers & below) == 0) atomicAdd(&s_off[key[j]], (uint32_t)__popc(peers));
@@ -315,32 +335,27 @@ __global__ void __launch_bounds__(kSortThreads, 3) decode_sorted_kernel(
             uint32_t at = 0;
             if (key[j] != kNoKey && lane == leader) at = atomicAdd(&s_off[key[j]], (uint32_t)__popc(peers));
             at = __shfl_sync(0xFFFFFFFFu, at, leader);
-            if (key[j] != kNoKey) s_perm[at + __popc(peers & below)] = (uint16_t)(j * kSortThreads + threadIdx.x);
-        }
-        __syncthreads();
-        // warp wid takes sorted positions r * kSortThreads + 32 * wid + lane;
-        // every round's bitstream is loaded before the first parse
-        int64_t id[kRounds];
-        uint32_t slot[kRounds];
-        frc4::RegBits cur[kRounds];
-#pragma unroll
-        for (int r = 0; r < kRounds; ++r) {
-            const int q = r * kSortThreads + wid * 32 + lane;
-            id[r] = -1;
-            slot[r] = 0u;
-            cur[r] = frc4::RegBits{0ull, 0ull};
-            if (q < m) {
-                const int64_t i = c0 + s_perm[q];
-                id[r] = ids ? (int64_t)ids[i] : i;
-                slot[r] = dst_ids ? dst_ids[i] : (uint32_t)i;
-                if (rate <= 2 && id[r] < nblocks) cur[r] = frc4::load_reg_bits(comp + id[r] * bytes, rate);
+            if (key[j] != kNoKey) {
+                const uint32_t pos = at + __popc(peers & below);
+                s_bits[pos] = ebits[j];
+                s_id[pos] = eid[j];
+                s_slot[pos] = eslot[j];
             }
         }
+        __syncthreads();
+        // warp wid takes sorted positions r * kSortThreads + 32 * wid + lane
 #pragma unroll
         for (int r = 0; r < kRounds; ++r) {
             const int q0 = r * kSortThreads + wid * 32;
             if (q0 >= m) break;   // the same for the whole warp
-            if (q0 + lane < m) decode_into_row(comp, nblocks, rate, id[r], cur[r], row, bad);
+            const int q = q0 + lane;
+            uint32_t slot = 0u;
+            if (q < m) {
+                const uint4 b4 = s_bits[q];
+                const frc4::RegBits bits{(uint64_t)b4.x | ((uint64_t)b4.y << 32), (uint64_t)b4.z | ((uint64_t)b4.w << 32)};
+                slot = s_slot[q];
+                decode_into_row(comp, nblocks, rate, (int64_t)s_id[q], bits, row, bad);
+            }
             __syncwarp();
             // blocks t and t + 1 of the warp per step: lanes 0-15 and 16-31
             // each move one 16-byte quarter-row
@@ -348,7 +363,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) decode_sorted_kernel(
             const int half = lane >> 4, qq = lane & 15;
             for (int t = 0; t < cnt; t += 2) {
                 const int blk = t + half;
-                const uint32_t sl = __shfl_sync(0xFFFFFFFFu, slot[r], blk & 31);
+                const uint32_t sl = __shfl_sync(0xFFFFFFFFu, slot, blk & 31);
                 if (blk < cnt) {
                     const uint4 w = reinterpret_cast<const uint4 *>(wrows + blk * kRowStride)[qq];
                     reinterpret_cast<uint4 *>(out + (int64_t)sl * 64)[qq] = w;
