@@ -1512,31 +1512,32 @@ __global__ void scatter_entries_kernel(const PassState *ps, const uint32_t *__re
 }
 
 // ------------------------------------------------------------------ cache
+// The count only reads (1 for a miss), so a thread's lookups are issued
+// together; the emit marks the hits' slots touched (a byte store, which the
+// compiler must assume may alias the tables, would otherwise order every
+// later lookup after it).
 struct LookupCount {
     const uint32_t *iact;
     const uint32_t *blk_slot;
-    uint8_t *touched;
     const uint32_t *skip;
     __device__ bool enabled() const { return !*skip; }
-    __device__ uint32_t operator()(int64_t i) const
+    __device__ uint32_t operator()(int64_t i) const { return __ldg(blk_slot + __ldg(iact + i)) == kNone ? 1u : 0u; }
+};
+
+// misses listed in order; hits' slots marked touched
+struct LookupEmit {
+    const uint32_t *iact;
+    const uint32_t *blk_slot;
+    uint8_t *touched;
+    uint32_t *miss;
+    __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
     {
-        uint32_t s = blk_slot[iact[i]];
-        if (s != kNone) {
-            touched[s] = 1;
-            return 0u;
-        }
-        return 1u;
+        const uint32_t b = __ldg(iact + i);
+        if (c) miss[pre] = b;
+        else touched[__ldg(blk_slot + b)] = 1;
     }
 };
 
-struct SelectEmit {
-    const uint32_t *src;
-    uint32_t *dst;
-    __device__ void operator()(int64_t i, uint32_t pre, uint32_t c) const
-    {
-        if (c) dst[pre] = src[i];
-    }
-};
 
 // the LRU list in use and the one being built, chosen by the pass parity
 struct LruPair {
@@ -3200,9 +3201,10 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     // (c) cache: look up, pick least recently used victims, assign
     LruPair lp{r->lru[0].as<uint32_t>(), r->lru[1].as<uint32_t>(), ps};
     SPR_TRY(run_compact(r->scan_status[1], r->scan_ticket[1], flags, r->cap_act, ctr + C_NACT,
-                        LookupCount{r->iact.as<uint32_t>(), r->blk_slot.as<uint32_t>(), r->touched.as<uint8_t>(),
-                                    ctr + C_OVERFLOW},
-                        SelectEmit{r->iact.as<uint32_t>(), r->miss.as<uint32_t>()}, ctr + C_NMISS, sa));
+                        LookupCount{r->iact.as<uint32_t>(), r->blk_slot.as<uint32_t>(), ctr + C_OVERFLOW},
+                        LookupEmit{r->iact.as<uint32_t>(), r->blk_slot.as<uint32_t>(), r->touched.as<uint8_t>(),
+                                   r->miss.as<uint32_t>()},
+                        ctr + C_NMISS, sa));
     SPR_TRY(run_compact(r->scan_status[1], r->scan_ticket[1], flags, r->n_slots, &ps->n_used,
                         VictimCount{lp, r->touched.as<uint8_t>(), ctr, (uint32_t)r->n_slots},
                         VictimEmit{lp, ctr, r->victim.as<uint32_t>(), (uint32_t)r->n_slots}, nullptr, sa));
