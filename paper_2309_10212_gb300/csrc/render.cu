@@ -29,6 +29,7 @@
 #include <new>
 #include <vector>
 
+#include "decode.cuh"
 #include "kernels.cuh"
 #include "scan.cuh"
 #include "mlp.cuh"
@@ -1601,37 +1602,42 @@ struct KeepEmit {
     }
 };
 
-__global__ void assign_kernel(const uint32_t *__restrict__ miss, uint32_t *__restrict__ victim, uint32_t *blk_slot,
-                              uint32_t *slot_blk, uint8_t *touched, uint32_t *ctr, PassState *ps, uint32_t n_slots)
-{
-    if (ctr[C_OVERFLOW]) return;
-    const uint32_t nf = fresh_taken(ps, ctr, n_slots);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+// The cache assignment of the pass's misses, done by the decoder as it reads
+// each miss (decode_sorted_kernel's slot functor), so that it takes no launch
+// of its own on the way to the decode: miss i takes never-used slot
+// fresh_lo + i while those last, else victim[i] (the least recently used
+// untouched slot); the slot's previous block loses its mapping; block and
+// slot map to each other; the slot is marked touched.
+struct AssignSlot {
+    const uint32_t *victim;
+    uint32_t *blk_slot, *slot_blk;
+    uint8_t *touched;
+    uint32_t *ctr;
+    PassState *ps;
+    uint32_t n_slots;
+    __device__ void begin() const
+    {
+        const uint32_t nf = fresh_taken(ps, ctr, n_slots);
         ps->fresh_hi = ps->fresh_lo + nf;
         ctr[C_NEEDUSED] = ctr[C_NMISS] - nf;
     }
-    const int64_t n = ctr[C_NMISS];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t s;
-        if (i < nf) {
-            s = ps->fresh_lo + (uint32_t)i;
-            victim[i] = s;
-        } else {
-            s = victim[i];
-        }
-        uint32_t old = slot_blk[s];
+    __device__ uint32_t operator()(int64_t i, uint32_t b) const
+    {
+        const uint32_t nf = fresh_taken(ps, ctr, n_slots);
+        const uint32_t s = i < nf ? ps->fresh_lo + (uint32_t)i : victim[i];
+        const uint32_t old = slot_blk[s];
         uint32_t ev = 0;
         if (old != kNone) {
             blk_slot[old] = kNone;
             ev = 1;
         }
-        uint32_t b = miss[i];
         blk_slot[b] = s;
         slot_blk[s] = b;
         touched[s] = 1;
         warp_add(&ctr[C_EVICT], ev);
+        return s;
     }
-}
+};
 
 struct TouchedCount {
     const uint8_t *touched;
@@ -3100,6 +3106,22 @@ bool coop_walks_possible(const spr_renderer *r)
     return r->coop_below > 0 && (r->seg_threads == 0 || (uint64_t)r->seg_threads < 2ull * r->coop_below);
 }
 
+// After the assignment (which marks the victims and the fresh slots it
+// hands out): the next pass's LRU list, the untouched used slots in order,
+// then the touched ones in slot order.
+int enqueue_lru_order(spr_renderer *r, const LruPair &lp, uint32_t *flags, cudaStream_t s)
+{
+    uint32_t *ctr = r->ctr.as<uint32_t>();
+    PassState *ps = r->ps.as<PassState>();
+    SPR_TRY(run_compact(r->scan_status[2], r->scan_ticket[2], flags, r->n_slots, &ps->n_used,
+                        KeepCount{lp, r->touched.as<uint8_t>(), ctr + C_OVERFLOW}, KeepEmit{lp}, ctr + C_NUNTOUCHED,
+                        s));
+    SPR_TRY(run_compact(r->scan_status[2], r->scan_ticket[2], flags, r->n_slots, &ps->fresh_hi,
+                        TouchedCount{r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
+                        TouchedEmit{r->touched.as<uint8_t>(), ctr, lp}, nullptr, s));
+    return SPR_OK;
+}
+
 int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphConditionalHandle h, int use_h,
                     bool capturing = false)
 {
@@ -3112,8 +3134,7 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     const bool fork = !events;
     cudaStream_t sa = fork ? r->aux[0] : s;   // cache branch
     cudaStream_t sl = fork ? r->aux[1] : s;   // LRU order branch
-    cudaEvent_t ev_trav = r->jev[0], ev_act = r->jev[1], ev_assign = r->jev[2], ev_dec = r->jev[3],
-                ev_lru = r->jev[4];
+    cudaEvent_t ev_trav = r->jev[0], ev_act = r->jev[1], ev_dec = r->jev[3], ev_lru = r->jev[4];
     int64_t k0 = r->launches;
     if (events) SPR_CUDA_TRY(record(r->ev[0], s, capturing));
     begin_pass_kernel<<<1, 32, 0, s>>>(ps, ctr);
@@ -3208,32 +3229,23 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     SPR_TRY(run_compact(r->scan_status[1], r->scan_ticket[1], flags, r->n_slots, &ps->n_used,
                         VictimCount{lp, r->touched.as<uint8_t>(), ctr, (uint32_t)r->n_slots},
                         VictimEmit{lp, ctr, r->victim.as<uint32_t>(), (uint32_t)r->n_slots}, nullptr, sa));
-    assign_kernel<<<grid_for(r->cap_act, 256, 4), 256, 0, sa>>>(r->miss.as<uint32_t>(), r->victim.as<uint32_t>(),
-                                                               r->blk_slot.as<uint32_t>(), r->slot_blk.as<uint32_t>(),
-                                                               r->touched.as<uint8_t>(), ctr, ps, (uint32_t)r->n_slots);
-    count_launch();
-    SPR_CUDA_TRY(cudaGetLastError());
-    if (fork) {
-        SPR_CUDA_TRY(cudaEventRecord(ev_assign, sa));
-        SPR_CUDA_TRY(cudaStreamWaitEvent(sl, ev_assign, 0));
-    }
-    SPR_TRY(run_compact(r->scan_status[2], r->scan_ticket[2], flags, r->n_slots, &ps->n_used,
-                        KeepCount{lp, r->touched.as<uint8_t>(), ctr + C_OVERFLOW}, KeepEmit{lp}, ctr + C_NUNTOUCHED,
-                        sl));
-    SPR_TRY(run_compact(r->scan_status[2], r->scan_ticket[2], flags, r->n_slots, &ps->fresh_hi,
-                        TouchedCount{r->touched.as<uint8_t>(), ctr + C_OVERFLOW},
-                        TouchedEmit{r->touched.as<uint8_t>(), ctr, lp}, nullptr, sl));
     if (events) SPR_CUDA_TRY(record(r->ev[3], s, capturing));
 
-    // (d) decode the misses into their slots
-    SPR_TRY(launch_decode_list(r->vol->comp.as<uint8_t>(), g.nblocks, g.rate, r->miss.as<uint32_t>(),
-                               r->victim.as<uint32_t>(), r->cap_act, ctr + C_NMISS, ctr + C_OVERFLOW,
-                               r->cache.as<float>(), ctr + C_BAD, sa, r->vol->planes.as<uint8_t>()));
+    // (d) decode the misses into their slots, the decoder handing out the
+    // slots (fresh ones first, then the victims) as it reads the misses
+    SPR_TRY(launch_decode_sorted(r->vol->comp.as<uint8_t>(), g.nblocks, g.rate, r->vol->planes.as<uint8_t>(),
+                                 r->miss.as<uint32_t>(),
+                                 AssignSlot{r->victim.as<uint32_t>(), r->blk_slot.as<uint32_t>(),
+                                            r->slot_blk.as<uint32_t>(), r->touched.as<uint8_t>(), ctr, ps,
+                                            (uint32_t)r->n_slots},
+                                 r->cap_act, ctr + C_NMISS, ctr + C_OVERFLOW, r->cache.as<float>(), ctr + C_BAD, sa));
     count_launch();
     if (events) SPR_CUDA_TRY(record(r->ev[4], s, capturing));
     if (fork) {
         SPR_CUDA_TRY(cudaEventRecord(ev_dec, sa));
         SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_dec, 0));
+        SPR_CUDA_TRY(cudaStreamWaitEvent(sl, ev_dec, 0));
+        SPR_TRY(enqueue_lru_order(r, lp, flags, sl));   // beside the intersection
     }
 
     // (e) intersect the entries, block by block
@@ -3263,6 +3275,8 @@ int enqueue_attempt(spr_renderer *r, cudaStream_t s, bool events, cudaGraphCondi
     if (fork) {   // the LRU order must be complete before the pass ends
         SPR_CUDA_TRY(cudaEventRecord(ev_lru, sl));
         SPR_CUDA_TRY(cudaStreamWaitEvent(s, ev_lru, 0));
+    } else {
+        SPR_TRY(enqueue_lru_order(r, lp, flags, s));
     }
     end_pass_kernel<<<1, 32, 0, s>>>(ps, ctr, r->d_recs, (uint32_t)spr_renderer::kRecCap, r->d_hps, h, use_h);
     count_launch();
@@ -3537,6 +3551,8 @@ extern "C" int spr_create_renderer(spr_volume *vol, int width, int height, spr_r
     if (!vol || !out || width < 1 || height < 1) return set_error(SPR_ERR_INVALID_ARG, "bad renderer arguments");
     *out = nullptr;
     if ((int64_t)width * height > (int64_t)1 << 28) return set_error(SPR_ERR_INVALID_ARG, "image too large");
+    // the decoder's shared-memory attribute, set here, outside any capture
+    SPR_TRY(decode_sorted_prepare<AssignSlot>(nullptr));
     spr_renderer *r = new (std::nothrow) spr_renderer();
     if (!r) return set_error(SPR_ERR_OUT_OF_MEMORY, "host allocation failed");
     r->vol = vol;
