@@ -125,24 +125,32 @@ __device__ __forceinline__ bool decode_coeffs(const Bits &bits_at, int rate, uin
         }
         pos += m;
         budget -= m;
-        // group tests and significance runs
+        // group tests and significance runs: one 32-bit read gives the test
+        // bit (bit 0) and the first 31 bits of the run after it
         while (n < 64 && budget > 0) {
-            uint32_t g = bits_at(pos, 1);
+            const uint32_t w = bits_at(pos, 32);
             ++pos;
             --budget;
-            if (!g) break;
-            int lim = 64 - n < budget ? 64 - n : budget;
-            int used = 0;
-            bool found = false;
-            while (used < lim) {
-                int cnt = lim - used < 32 ? lim - used : 32;
-                uint32_t bits = bits_at(pos + used, cnt);
-                if (bits) {
-                    used += __ffs(bits);
-                    found = true;
-                    break;
+            if (!(w & 1u)) break;
+            const int lim = 64 - n < budget ? 64 - n : budget;
+            uint32_t run = w >> 1;
+            if (lim < 31) run &= (1u << lim) - 1u;
+            int used;
+            bool found = run != 0u;
+            if (found) {
+                used = __ffs(run);
+            } else {
+                used = lim < 31 ? lim : 31;
+                while (used < lim) {   // a run longer than the window
+                    int cnt = lim - used < 32 ? lim - used : 32;
+                    uint32_t bits = bits_at(pos + used, cnt);
+                    if (bits) {
+                        used += __ffs(bits);
+                        found = true;
+                        break;
+                    }
+                    used += cnt;
                 }
-                used += cnt;
             }
             pos += used;
             budget -= used;
