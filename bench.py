@@ -62,10 +62,6 @@ def decode_bytes_per_block(rate):
 # the same build of that kernel on the same workload: (kernel, dims, rate) ->
 # (bytes, source).  Empty a line when the kernel changes.
 MEASURED_TRAFFIC = {
-    ("decode_sorted_kernel", (2048, 2048, 1920), 2): (
-        110_355_456,
-        "one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum: mean of the render's "
-        "two launches (110.8 and 109.9 MB; the decoder also writes the slot assignment)"),
 }
 
 WORKLOADS = {

@@ -172,13 +172,13 @@ __global__ void __launch_bounds__(kDecThreads, 6) decode_list_kernel(
     int64_t base = (int64_t)blockIdx.x * kDecThreads + wid * 32;
     int64_t id = dec_id(ids, base + lane, n);
     int64_t id_next = dec_id(ids, base + stride + lane, n);
-    frc4::RegBits cur{0ull, 0ull};
+    frc4::RegBits cur{0u, 0u, 0u, 0u};
     if (reg && id >= 0 && id < nblocks) cur = frc4::load_reg_bits(comp + id * bytes, rate);
     const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
     for (; base < n; base += stride) {
         const int64_t i = base + lane;
         // loads for the next items, consumed one and two iterations later
-        frc4::RegBits nxt{0ull, 0ull};
+        frc4::RegBits nxt{0u, 0u, 0u, 0u};
         if (reg && id_next >= 0 && id_next < nblocks) nxt = frc4::load_reg_bits(comp + id_next * bytes, rate);
         const int64_t id_after = dec_id(ids, base + 2 * stride + lane, n);
         const uint32_t my_slot = i < n ? (dst_ids ? dst_ids[i] : (uint32_t)i) : 0u;

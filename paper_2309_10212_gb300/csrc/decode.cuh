@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) decode_sorted_kernel(
             uint32_t slot = 0u;
             if (q < m) {
                 const uint4 b4 = s_bits[q];
-                const frc4::RegBits bits{(uint64_t)b4.x | ((uint64_t)b4.y << 32), (uint64_t)b4.z | ((uint64_t)b4.w << 32)};
+                const frc4::RegBits bits{b4.x, b4.y, b4.z, b4.w};
                 slot = s_slot[q];
                 decode_into_row(comp, nblocks, rate, (int64_t)s_id[q], bits, row, bad);
             }

@@ -49,13 +49,16 @@ struct MemBits {   // any rate: 32-bit words read through the read-only path
     }
 };
 
-struct RegBits {   // rate <= 2: the whole 64- or 128-bit stream in registers
-    uint64_t lo, hi;
+struct RegBits {   // rate <= 2: the whole 64- or 128-bit stream in registers, w0 first
+    uint32_t w0, w1, w2, w3;
+    // words pos/32 and pos/32 + 1 (pos < 128) picked by two selects per bit
+    // of the word index, then one funnel shift
     __device__ __forceinline__ uint32_t operator()(int pos, int n) const
     {
-        uint64_t v = pos < 64 ? (pos == 0 ? lo : (lo >> pos) | (hi << (64 - pos))) : (hi >> (pos - 64));
-        uint32_t x = (uint32_t)v;
-        return n >= 32 ? x : (x & ((1u << n) - 1u));
+        const bool k2 = (pos & 64) != 0, k1 = (pos & 32) != 0;
+        const uint32_t x0 = k2 ? w2 : w0, x1 = k2 ? w3 : w1, x2 = k2 ? 0u : w2;
+        const uint32_t v = __funnelshift_r(k1 ? x1 : x0, k1 ? x2 : x1, (uint32_t)pos);
+        return n >= 32 ? v : (v & ((1u << n) - 1u));
     }
 };
 
@@ -64,12 +67,10 @@ __device__ __forceinline__ RegBits load_reg_bits(const uint8_t *blk, int rate)
     RegBits b;
     if (rate == 2) {
         uint4 q = __ldg(reinterpret_cast<const uint4 *>(blk));
-        b.lo = (uint64_t)q.x | ((uint64_t)q.y << 32);
-        b.hi = (uint64_t)q.z | ((uint64_t)q.w << 32);
+        b = RegBits{q.x, q.y, q.z, q.w};
     } else {
         uint2 q = __ldg(reinterpret_cast<const uint2 *>(blk));
-        b.lo = (uint64_t)q.x | ((uint64_t)q.y << 32);
-        b.hi = 0;
+        b = RegBits{q.x, q.y, 0u, 0u};
     }
     return b;
 }
