@@ -1843,35 +1843,57 @@ __device__ __forceinline__ bool first_root(const CellF &f, float L, float &s_hit
     return false;
 }
 
-__device__ __forceinline__ uint32_t pick8(const uint32_t s[8], int k)
-{
-    uint32_t a = (k & 1) ? s[1] : s[0], b = (k & 1) ? s[3] : s[2];
-    uint32_t c = (k & 1) ? s[5] : s[4], d = (k & 1) ? s[7] : s[6];
-    uint32_t ab = (k & 2) ? b : a, cd = (k & 2) ? d : c;
-    return (k & 4) ? cd : ab;
-}
-
 // Intersect the ray with the isosurface inside block (bx,by,bz).  On a hit,
 // returns the 44 low bits of the resolve key: depth bits, local cell, grey.
 // The block's dual grid (its 4^3 voxels and the +x/+y/+z neighbours' face,
 // edge and corner voxels, 5^3 values) as the intersection reads it: local
-// corner (lx, ly, lz), each in 0..4.
+// corner (lx, ly, lz), each in 0..4, taken 8 at a time, a cell's corners.
 // GlobalCorners reads each corner from the cache slot holding it (L1-cached
 // loads); SharedCorners from a copy of the 5^3 values staged in shared memory.
 struct GlobalCorners {
     const float *cache;
     uint32_t slots[8];   // own, +x, +y, +xy, +z, +xz, +yz, +xyz
-    __device__ __forceinline__ float operator()(int lx, int ly, int lz) const
+    // the 8 corners of cell c (each 0..3), v[k] = corner (c + (k&1, k>>1&1,
+    // k>>2)): a corner lies in the +a neighbour exactly when its offset along
+    // a is 1 and c[a] == 3, so one cell's 8 slots follow from three flags
+    __device__ __forceinline__ void load8(const int c[3], float v[8]) const
     {
-        const int nsel = (lx >> 2) | ((ly >> 2) << 1) | ((lz >> 2) << 2);
-        const uint32_t slot = pick8(slots, nsel);
-        return __ldg(cache + (uint64_t)slot * 64 + (lx & 3) + 4 * (ly & 3) + 16 * (lz & 3));
+        const bool xs = c[0] == 3, ys = c[1] == 3, zs = c[2] == 3;
+        const uint32_t s000 = slots[0];
+        const uint32_t s100 = xs ? slots[1] : s000;
+        const uint32_t s010 = ys ? slots[2] : s000;
+        const uint32_t s110 = ys ? (xs ? slots[3] : slots[2]) : s100;
+        const uint32_t s001 = zs ? slots[4] : s000;
+        const uint32_t s101 = zs ? (xs ? slots[5] : slots[4]) : s100;
+        const uint32_t s011 = zs ? (ys ? slots[6] : slots[4]) : s010;
+        const uint32_t s111 = zs ? (ys ? (xs ? slots[7] : slots[6]) : (xs ? slots[5] : slots[4])) : s110;
+        const int x0 = c[0], x1 = (c[0] + 1) & 3, y0 = 4 * c[1], y1 = 4 * ((c[1] + 1) & 3), z0 = 16 * c[2],
+                  z1 = 16 * ((c[2] + 1) & 3);
+        v[0] = __ldg(cache + (uint64_t)s000 * 64 + (x0 + y0 + z0));
+        v[1] = __ldg(cache + (uint64_t)s100 * 64 + (x1 + y0 + z0));
+        v[2] = __ldg(cache + (uint64_t)s010 * 64 + (x0 + y1 + z0));
+        v[3] = __ldg(cache + (uint64_t)s110 * 64 + (x1 + y1 + z0));
+        v[4] = __ldg(cache + (uint64_t)s001 * 64 + (x0 + y0 + z1));
+        v[5] = __ldg(cache + (uint64_t)s101 * 64 + (x1 + y0 + z1));
+        v[6] = __ldg(cache + (uint64_t)s011 * 64 + (x0 + y1 + z1));
+        v[7] = __ldg(cache + (uint64_t)s111 * 64 + (x1 + y1 + z1));
     }
 };
 
 struct SharedCorners {
     const float *v;   // 125 values, x fastest
-    __device__ __forceinline__ float operator()(int lx, int ly, int lz) const { return v[lx + 5 * ly + 25 * lz]; }
+    __device__ __forceinline__ void load8(const int c[3], float out[8]) const
+    {
+        const float *p = v + c[0] + 5 * c[1] + 25 * c[2];
+        out[0] = p[0];
+        out[1] = p[1];
+        out[2] = p[5];
+        out[3] = p[6];
+        out[4] = p[25];
+        out[5] = p[26];
+        out[6] = p[30];
+        out[7] = p[31];
+    }
 };
 
 // cells per axis of block (bx, by, bz) that exist (1..4)
@@ -1986,9 +2008,9 @@ __device__ bool intersect_block(const RT &R, const Ray &r, float isov, int bx, i
         if (s1 > s0) {
             CellF f;
             int below = 0, above = 0;
+            corner.load8(c, f.v);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                f.v[k] = corner(c[0] + (k & 1), c[1] + ((k >> 1) & 1), c[2] + (k >> 2));
                 below += f.v[k] < iso;
                 above += f.v[k] > iso;
             }
