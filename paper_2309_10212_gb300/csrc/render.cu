@@ -171,6 +171,13 @@ struct Occ {
     int ts[3];   // super cells the traversal can visit: ceil(tc / 4)
 };
 
+// bit i (0..63) of a 64-bit brick mask, read from its 32-bit half
+__device__ __forceinline__ bool mask_bit(unsigned long long m, int i)
+{
+    const uint32_t h = (i & 32) ? (uint32_t)(m >> 32) : (uint32_t)m;
+    return (h >> (i & 31)) & 1u;
+}
+
 // A walk has passed the occupied box once a block index goes beyond the
 // box's last index in the walk's direction (indices change monotonically, so
 // no later block is in the box): sgn_a * b_a > lim_a with lim_a = hi_a for
@@ -722,7 +729,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
                 smask = __ldg(sm + sc);
                 cur_s = sc;
             }
-            if (!((smask >> (((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) & 1ull)) {
+            if (!mask_bit(smask, ((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) {
                 alive = skip_level(w, g, smask ? 4 : 16, smask ? g.tc : P.occ.ts);
                 continue;
             }
@@ -731,7 +738,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(Geo P, const uint32_t *__
                 fmask = __ldg(fm + c);
                 cur_c = c;
             }
-            if ((fmask >> ((b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) & 1ull) {
+            if (mask_bit(fmask, (b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) {
                 uint32_t blin = (uint32_t)b[0] + nb0 * ((uint32_t)b[1] + nb1 * (uint32_t)b[2]);
                 if (S.eray) S.eray[off + cnt] = (uint32_t)i;
                 out[cnt++] = blin;
@@ -859,7 +866,7 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
             // super mask says the cell is empty)
             const unsigned long long smask = __ldg(sm + sc);
             const unsigned long long fmask = __ldg(fm + c);
-            if (!((smask >> (((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) & 1ull)) {
+            if (!mask_bit(smask, ((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) {
                 alive = skip_level(w, g, smask ? 4 : 16, smask ? g.tc : P.occ.ts);
                 continue;
             }
@@ -938,13 +945,13 @@ __global__ void __launch_bounds__(128) traverse_coop_kernel(Geo P, const uint32_
             bool vis = false;
             int pos = 0, bb[3] = {b[0], b[1], b[2]};
             if (gl == LPR - 1) {
-                vis = (fmask >> ((b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) & 1ull;
+                vis = mask_bit(fmask, (b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3));
             } else if (interior && rep) {
                 pos = rank + 1;
                 bb[0] = nbk[0];
                 bb[1] = nbk[1];
                 bb[2] = nbk[2];
-                vis = (fmask >> ((bb[0] & 3) + 4 * (bb[1] & 3) + 16 * (bb[2] & 3))) & 1ull;
+                vis = mask_bit(fmask, (bb[0] & 3) + 4 * (bb[1] & 3) + 16 * (bb[2] & 3));
             }
             const unsigned vmask = __reduce_or_sync(full, vis ? (1u << pos) : 0u);
             const int need = ki - cnt;
@@ -1162,7 +1169,7 @@ __device__ __forceinline__ int seg_walk(Walk &w, const Geo &P, const SegPart &sp
             smask = __ldg(sm + sc);
             cur_s = sc;
         }
-        if (!((smask >> (((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) & 1ull)) {
+        if (!mask_bit(smask, ((b[0] >> 2) & 3) + 4 * ((b[1] >> 2) & 3) + 16 * ((b[2] >> 2) & 3))) {
             alive = skip_level(w, g, smask ? 4 : 16, smask ? g.tc : P.occ.ts);
             continue;
         }
@@ -1171,7 +1178,7 @@ __device__ __forceinline__ int seg_walk(Walk &w, const Geo &P, const SegPart &sp
             fmask = __ldg(fm + c);
             cur_c = c;
         }
-        if ((fmask >> ((b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) & 1ull) {
+        if (mask_bit(fmask, (b[0] & 3) + 4 * (b[1] & 3) + 16 * (b[2] & 3))) {
             const uint32_t blin = (uint32_t)b[0] + nb0 * ((uint32_t)b[1] + nb1 * (uint32_t)b[2]);
             if (MODE == 0) {
                 if (cnt < kSegBuf) {
