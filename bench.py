@@ -62,6 +62,14 @@ def decode_bytes_per_block(rate):
 # the same build of that kernel on the same workload: (kernel, dims, rate) ->
 # (bytes, source).  Empty a line when the kernel changes.
 MEASURED_TRAFFIC = {
+    ("decode_sorted_kernel", (2048, 2048, 1920), 2): (
+        110_352_640,
+        "one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum: mean of the render's "
+        "two launches (110.8 and 109.9 MB; the decoder also writes the slot assignment)"),
+    ("traverse_kernel / traverse_seg_kernel", (2048, 2048, 1920), 2): (
+        5_134_464,
+        "one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum: mean of the render's two "
+        "walking launches (traverse_kernel in pass 1: 5.81 MB; traverse_seg_kernel in pass 2: 4.46 MB)"),
 }
 
 WORKLOADS = {
