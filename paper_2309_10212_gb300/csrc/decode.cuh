@@ -174,14 +174,21 @@ __global__ void __launch_bounds__(kSortThreads, 3) decode_sorted_kernel(
 
 
 // The kernel's dynamic shared memory (above the 48 KB default) and its CTAs
-// per SM (8 waves of the resident ones), once per instantiation.  Call it
-// outside stream capture before the first launch (it sets a function
-// attribute); later calls only read the cached value.
+// per SM (8 waves of the resident ones), once per instantiation and device
+// (a function attribute holds for the device current when it is set).  Call
+// it with the device current, outside stream capture, before the first
+// launch there; later calls on that device only read the cached value.
+constexpr int kSortMaxDevices = 64;
+
 template <class SlotF>
 inline int decode_sorted_prepare(int *per_sm)
 {
-    static int cached = 0;
-    if (cached == 0) {
+    static int cached[kSortMaxDevices] = {};
+    int dev = 0;
+    SPR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kSortMaxDevices)
+        return set_error(SPR_ERR_INVALID_ARG, "device ordinal %d beyond the %d supported", dev, kSortMaxDevices);
+    if (cached[dev] == 0) {
         SPR_CUDA_TRY(cudaFuncSetAttribute(decode_sorted_kernel<SlotF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)kSortRowBytes));
         int nb = 0;
@@ -189,9 +196,9 @@ inline int decode_sorted_prepare(int *per_sm)
                                                           kSortRowBytes) != cudaSuccess ||
             nb < 1)
             nb = 1;
-        cached = nb * 8;
+        cached[dev] = nb * 8;
     }
-    if (per_sm) *per_sm = cached;
+    if (per_sm) *per_sm = cached[dev];
     return SPR_OK;
 }
 
