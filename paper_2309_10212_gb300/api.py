@@ -174,10 +174,9 @@ def spr_volume_decode_blocks(vol: Volume, ids=None, n=None, out=None, stream=Non
     way the renderer decodes its cache misses; the values equal
     spr_decode_blocks'."""
     torch = _torch()
-    total = vol.nblocks
-    total = total[0] * total[1] * total[2] if isinstance(total, tuple) else int(total)
     if n is None:
-        n = total if ids is None else ids.numel()
+        nb = vol.nblocks
+        n = nb[0] * nb[1] * nb[2] if ids is None else ids.numel()
     if out is None:
         out = torch.empty((n, 64), dtype=torch.float32, device="cuda" if ids is None else ids.device)
     idp = None if ids is None else _dev_ptr(ids, torch.int32)
