@@ -60,3 +60,28 @@ def test_oracle_passes_line():
     assert d["impl"] == "oracle_passes" and d["cores"] >= 1
     assert d["render_with_lists_ms"] > 0 and d["simulate_ms"] >= 0
     assert d["passes"] >= 1 and d["blocks_decoded"] > 0 and d["entries"] > 0
+
+
+def test_stage_rooflines_and_recorded_traffic():
+    """The rooflines' arithmetic on made-up counters (bytes per unit times
+    counts, over the stage time, against the peak), and every recorded DRAM
+    traffic figure keyed by a kernel name the rooflines report, so that the
+    line's `traffic` cannot silently become null after a rename."""
+    import bench
+    p = dict(n_processed=1000, n_entries_cap=4000, n_steps=20000, n_decoded=500, n_visible=300,
+             n_entries=900)
+    stage = {"traverse": 0.5, "decode": 0.25, "intersect": 0.125}
+    rl = bench.stage_rooflines([(None, [p, p])], stage, 2, {"hbm_gbs": 1000.0})
+    trav = 2 * (1000 * 80 + 4000 * 4 + 20000 * 8)
+    dec = 2 * 500 * (8 * 2 + 256)
+    isect = 2 * (300 * 500 + 900 * 24)
+    for name, nbytes in (("traverse", trav), ("decode", dec), ("intersect", isect)):
+        assert rl[name]["bytes"] == nbytes
+        gbs = nbytes / 1e9 / (stage[name] / 1e3)
+        assert abs(rl[name]["achieved"] - round(gbs, 1)) < 1e-9
+        assert abs(rl[name]["frac"] - round(gbs / 1000.0, 4)) < 1e-12
+    kernels = {v["kernel"] for v in rl.values()}
+    for (kernel, dims, rate), (nbytes, source) in bench.MEASURED_TRAFFIC.items():
+        assert kernel in kernels, kernel
+        assert tuple(dims) == bench.WORKLOADS["paper"]["dims"] and rate == bench.WORKLOADS["paper"]["rate"]
+        assert nbytes > 0 and "ncu" in source
