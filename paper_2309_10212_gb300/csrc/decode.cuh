@@ -16,17 +16,17 @@
 namespace spr {
 
 // decode_list_kernel (codec.cu) for lists whose blocks' parse lengths are
-// known (the volume's plane counts).  A warp's lanes run the bit-plane loop together, so
-// a warp costs about the plane loop of its longest block: lanes whose blocks
-// stop after few planes wait for those that parse all 30.  Each CTA step
-// therefore takes kSortChunk list entries, counting-sorts them in shared
-// memory by their blocks' plane counts, and gives each warp 32 consecutive
-// entries of that order.  Each entry still goes to its own destination slot,
-// slot_of(i, block) (SlotF: begin() once per launch by one thread, then
-// slot_of(i, b) once per entry), so the output is the same as
-// decode_list_kernel's.  CTAs of 256 threads,
-// one entry per thread and step (the rows in dynamic shared memory, 68 KB),
-// so that a list fills the GPU with as many threads as decode_list_kernel's.
+// known (the volume's plane counts).  A warp's lanes run the bit-plane loop
+// together, so a warp costs about the plane loop of its longest block: lanes
+// whose blocks stop after few planes wait for those that parse all 30.  Each
+// CTA step therefore takes kSortChunk list entries, counting-sorts them in
+// shared memory by their blocks' plane counts, and gives each warp 32
+// consecutive entries of that order.  Each entry still goes to its own
+// destination slot, slot_of(i, block) (SlotF: begin() once per launch by one
+// thread, then slot_of(i, b) once per entry), so the output is the same as
+// decode_list_kernel's.  CTAs of 256 threads, one entry per thread and step
+// (the rows in dynamic shared memory, 68 KB), so that a list fills the GPU
+// with as many threads as decode_list_kernel's.
 constexpr int kSortThreads = 256;
 constexpr int kSortChunk = kSortThreads;
 constexpr size_t kSortRowBytes = sizeof(uint32_t) * kSortThreads * kRowStride;
